@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""GTEPS of the GB300 partition-centric scatter/gather engine on RMAT scale 24.
+
+One step = PageRank to an L1 residual below 1e-9 (FP32 messages, FP64
+residual, cap 300 iterations) + BFS from one root + SSSP (weights uniform in
+[1, 255]) from the same root, all on the same directed RMAT-24 graph (16.8M
+vertices, edge factor 16, a/b/c/d = 0.57/0.19/0.19/0.05, self loops and
+duplicates removed), partitioned once before timing.  Edges counted:
+PageRank E x iterations; BFS and SSSP the out-degrees of the reached vertices
+(Graph500 style).  value = counted edges / device time (GTEPS).
+
+--impl reference times the CPU oracle (serial C, FP64) on the same workload.
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the method has no cross-GPU exchange on one node here) with its own roots.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS & % of HBM peak (RMAT-24 PR/BFS/SSSP); learned vs analytic mode speedup"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "gather_pagerank_rmat24.md")
+ENGINE_SRC = os.path.join(ROOT, "paper_1806_08092_gb300", "csrc", "engine.cu")
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=int, default=24)
+    ap.add_argument("--partition", type=int, default=16384)
+    ap.add_argument("--pr-tol", type=float, default=1e-9)
+    ap.add_argument("--pr-max-iters", type=int, default=300)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-pr-iters", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms while active."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_graph(scale):
+    import graphgen as gg
+    g = gg.rmat(scale).with_weights(hi=255)
+    roots = gg.roots(g, 16)
+    return g, roots
+
+
+def cpu_baseline(g, roots, pr_iters):
+    """The oracle as it stands, one host core: PageRank for pr_iters iterations + BFS from one root."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.pagerank(g, 0.85, max_iters=pr_iters)
+    t1 = time.perf_counter()
+    level, _ = oracle.bfs(g, int(roots[0]))
+    t2 = time.perf_counter()
+    deg = np.diff(g.row_ptr)
+    te = int(deg[level != 0xFFFFFFFF].sum())
+    edges = g.num_edges * pr_iters + te
+    return {"value": edges / (t2 - t0) / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"serial C oracle on this RMAT-{int(np.log2(g.num_vertices))} graph: PageRank {pr_iters} "
+                      f"iterations ({t1 - t0:.1f} s) + BFS from one root ({t2 - t1:.1f} s), FP64, 1 thread",
+            "host_cores_available": os.cpu_count()}
+
+
+def traffic_from_profile():
+    """Per-launch DRAM bytes of the PageRank gather from the committed ncu summary, if it matches this source."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+        sha = hashlib.sha256(open(ENGINE_SRC, "rb").read()).hexdigest()[:16]
+        m = re.search(r"engine_sha256_16:\s*([0-9a-f]+)", text)
+        t = re.search(r"traffic_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+        if m and t and m.group(1) == sha:
+            return float(t.group(1))
+    except Exception:
+        pass
+    return None
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    g, roots = make_graph(a.scale)
+    import oracle
+    deg = np.diff(g.row_ptr)
+    per = []
+    total_edges = 0
+    for i in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        oracle.pagerank(g, 0.85, max_iters=1)
+        level, _ = oracle.bfs(g, int(roots[i % len(roots)]))
+        dt = time.perf_counter() - t0
+        if i >= a.warmup:
+            per.append(dt)
+            total_edges += g.num_edges + int(deg[level != 0xFFFFFFFF].sum())
+    t = sum(per)
+    value = total_edges / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64/u32", "data": "synthetic",
+            "config": {"workload": f"rmat{a.scale}_pr_bfs", "scale": a.scale, "edge_factor": 16,
+                       "vertices": g.num_vertices, "edges": g.num_edges,
+                       "step": "oracle PageRank 1 iteration + BFS from one root (bounded sample of the GPU step)"},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": "each step: serial C oracle PageRank 1 iteration + BFS from one root"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a, rank, world, local_rank):
+    import torch
+    import paper_1806_08092_gb300 as gp
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    gp.build()
+    g, roots = make_graph(a.scale)
+    V, E = g.num_vertices, g.num_edges
+    stream = torch.cuda.current_stream()
+    G = gp.Graph.from_csr(g.row_ptr, g.col, g.weights, partition_size=a.partition)
+    info = G.info()
+    deg_t = torch.from_numpy(np.diff(g.row_ptr).astype(np.int64)).cuda()
+    INF = 0xFFFFFFFF
+
+    # traversed edges per root (Graph500 count), outside the timed region
+    te_of = {}
+    nsteps = a.warmup + a.steps
+    my_roots = [int(roots[(rank * nsteps + i) % len(roots)]) for i in range(nsteps)]
+    for r in set(my_roots):
+        lv = G.run("bfs", source=r).values
+        te_of[r] = int(deg_t[lv.to(torch.int64) != INF].sum().item())
+
+    def step(r):
+        out = {}
+        pr = G.run("pagerank", max_iters=a.pr_max_iters, tol=a.pr_tol, profile=True)
+        bf = G.run("bfs", source=r, profile=True)
+        ss = G.run("sssp", source=r, profile=True)
+        out["pr"], out["bfs"], out["sssp"] = pr.stats, bf.stats, ss.stats
+        return out
+
+    for i in range(a.warmup):
+        step(my_roots[i])
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = [step(my_roots[a.warmup + i]) for i in range(a.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if clocks else None
+
+    edges = 0
+    for i, s in enumerate(stats):
+        r = my_roots[a.warmup + i]
+        edges += E * s["pr"]["iterations"] + 2 * te_of[r]
+    t_s = torch.tensor([ms / 1e3, float(edges)], dtype=torch.float64, device="cuda")
+    if dist:
+        tmax = t_s[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tot = t_s[1:].clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        t_all, edges_all = float(tmax.item()), float(tot.item())
+    else:
+        t_all, edges_all = ms / 1e3, float(edges)
+    value = edges_all / t_all / 1e9
+
+    # per-application device throughput and the roofline of the dominant kernel (PageRank gather)
+    pr_ms = sum(s["pr"]["device_ms"] for s in stats)
+    pr_it = sum(s["pr"]["iterations"] for s in stats)
+    bfs_ms = sum(s["bfs"]["device_ms"] for s in stats)
+    sssp_ms = sum(s["sssp"]["device_ms"] for s in stats)
+    te = sum(te_of[my_roots[a.warmup + i]] for i in range(a.steps))
+    kern = np.zeros(4)
+    launches = np.zeros(4, dtype=np.int64)
+    for s in stats:
+        for key in ("pr", "bfs", "sssp"):
+            kern += np.array(s[key]["kernel_ms"])
+            launches += np.array(s[key]["kernel_launches"], dtype=np.int64)
+    pr_gather_ms = sum(s["pr"]["kernel_ms"][3] for s in stats)
+    pr_gather_n = sum(s["pr"]["kernel_launches"][3] for s in stats)
+    pr_scatter_ms = sum(s["pr"]["kernel_ms"][1] for s in stats)
+    pr_scatter_n = sum(s["pr"]["kernel_launches"][1] for s in stats)
+    npng, npad, k = info["num_png"], info["num_png_padded"], info["num_partitions"]
+    # algorithmic bytes of one all-PC gather launch: PC message values (4 B per PNG entry), destination
+    # lists (4 B slot + 2 B local destination per edge), column offsets, and per vertex the rank
+    # read + write, the next message value write, the degree (two row offsets) and frontier bits
+    gather_bytes = 4 * npng + 6 * E + 4 * (V + 1) + 16 * V + V // 4
+    # one PC scatter launch: PNG source IDs (2 B) and message values (4 B) per padded slot + message values per vertex
+    scatter_bytes = 6 * npad + 4 * V
+    hbm, peak_kind = peaks()
+    g_avg_s = pr_gather_ms / max(pr_gather_n, 1) / 1e3
+    s_avg_s = pr_scatter_ms / max(pr_scatter_n, 1) / 1e3
+    g_ach = gather_bytes / g_avg_s / 1e9 if g_avg_s > 0 else 0.0
+    s_ach = scatter_bytes / s_avg_s / 1e9 if s_avg_s > 0 else 0.0
+    traffic = traffic_from_profile()
+
+    # end-to-end through the public API: host CSR in pinned memory -> build -> three runs -> host results
+    e2e = None
+    if a.e2e_steps > 0:
+        rp_h = torch.from_numpy(g.row_ptr.view(np.int64)).pin_memory()
+        col_h = torch.from_numpy(g.col.view(np.int32)).pin_memory()
+        w_h = torch.from_numpy(g.weights).pin_memory()
+        h2d = rp_h.numel() * 8 + col_h.numel() * 4 + w_h.numel() * 4
+        d2h = 4 * V + 8 * V + 4 * V
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_edges = 0
+        for i in range(a.e2e_steps):
+            r = my_roots[(a.warmup + i) % nsteps]
+            He = gp.Graph.from_csr(rp_h.view(torch.uint64), col_h.view(torch.uint32), w_h, partition_size=a.partition)
+            pr = He.run("pagerank", max_iters=a.pr_max_iters, tol=a.pr_tol, device_out=False)
+            He.run("bfs", source=r, device_out=False)
+            He.run("sssp", source=r, device_out=False)
+            He.close()
+            e_edges += E * pr.stats["iterations"] + 2 * te_of[r]
+        torch.cuda.synchronize()
+        t_e = time.perf_counter() - t0
+        e2e = {"value": e_edges / t_e / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": a.e2e_steps,
+               "includes": "H2D of the CSR from pinned memory, gpop_graph_build, three gpop_run calls, D2H of results"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(g, roots, a.cpu_pr_iters)
+    dominant = "k_gather<PageRank>"
+    line = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/u32", "data": "synthetic",
+        "config": {"workload": f"rmat{a.scale}_pr_bfs_sssp", "scale": a.scale, "edge_factor": 16, "vertices": V,
+                   "edges": E, "partition_size": info["partition_size"], "partitions": k,
+                   "png_entries": npng, "r": npng / max(E, 1), "pr_tol_l1": a.pr_tol,
+                   "l2": f"inputs larger than L2 (layout {info['device_bytes'] / 1e9:.1f} GB vs 129 MB L2); no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "per_algo": {"pagerank": {"iterations": pr_it / a.steps, "gteps": E * pr_it / (pr_ms / 1e3) / 1e9,
+                                  "ms": pr_ms / a.steps, "residual": stats[-1]["pr"]["residual"]},
+                     "bfs": {"gteps": te / (bfs_ms / 1e3) / 1e9, "ms": bfs_ms / a.steps,
+                             "iterations": sum(s["bfs"]["iterations"] for s in stats) / a.steps},
+                     "sssp": {"gteps": te / (sssp_ms / 1e3) / 1e9, "ms": sssp_ms / a.steps,
+                              "iterations": sum(s["sssp"]["iterations"] for s in stats) / a.steps}},
+        "kernels_ms": {"plan": kern[0] / a.steps, "scatter_pc": kern[1] / a.steps, "scatter_sc": kern[2] / a.steps,
+                       "gather": kern[3] / a.steps},
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": g_ach, "peak": hbm, "unit": "GB/s",
+                     "frac": g_ach / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": int(gather_bytes), "avg_launch_ms": g_avg_s * 1e3,
+                     "second": {"kernel": "k_scatter_pc (PageRank)", "achieved": s_ach, "frac": s_ach / hbm,
+                                "algorithmic_bytes_per_launch": int(scatter_bytes), "avg_launch_ms": s_avg_s * 1e3}},
+        "gpu_launches": int(launches.sum() + 2 * 3 * a.steps),
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    a = args_parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+    else:
+        run_ours(a, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

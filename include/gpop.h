@@ -1,0 +1,231 @@
+/*
+ * gpop.h -- C ABI of the GB300 partition-centric scatter/gather engine.
+ *
+ * The engine follows GPOP (Lakhotia, Pati, Kannan, Prasanna): vertices are
+ * split into index partitions of P consecutive IDs (Sec. 3.1.1); each
+ * iteration scatters messages from every active partition p into bins
+ * bin[p][q] (Sec. 3.1.2, Alg. 2), either source-centric (SC: only active
+ * vertices, as (destination, value) pairs) or partition-centric (PC: one value
+ * per PNG entry, destination lists laid out once at build, Alg. 3), with the
+ * mode chosen per partition and iteration by the traffic model of Sec. 3.2
+ * (Eq. (mode)); gather then drains bin[*][q] into q's vertex data without
+ * locks or atomics on vertex data, and the filter step builds the next,
+ * optionally continued, frontier (Sec. 4 user functions).
+ *
+ * Conventions for every entry point:
+ *  - Vertex IDs are uint32 with num_vertices < 2^31; num_edges < 2^32.
+ *  - Inputs are copied; the caller keeps ownership of everything it passes.
+ *  - Outputs go to caller-allocated buffers of the stated length.
+ *  - A pointer argument is device memory when the matching *_is_device flag is
+ *    non-zero, host memory otherwise.  cuda_stream is a cudaStream_t (NULL =
+ *    the legacy default stream); calls are synchronous with respect to it
+ *    on return.
+ *  - No call aborts or exits.  On failure a non-zero gpop_status is returned
+ *    and gpop_last_error() describes it; outputs are then unspecified.
+ *  - The library allocates device memory with cudaMalloc; all of it belongs
+ *    to the gpop_graph handle and is released by gpop_graph_destroy.
+ */
+#ifndef GPOP_H
+#define GPOP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GPOP_OK = 0,
+    GPOP_ERR_INVALID_ARG = 1,    /* bad sizes, malformed CSR, unsupported option */
+    GPOP_ERR_OOM = 2,            /* device or host allocation failed */
+    GPOP_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    GPOP_ERR_DEVICE_CHECK = 4,   /* a device-side consistency check failed */
+    GPOP_ERR_TIMEOUT = 5,        /* a bounded device wait gave up */
+    GPOP_ERR_NOT_CONVERGED = 6,  /* max_iters reached before tol_l1 (results valid) */
+    GPOP_ERR_NO_SELECTOR = 7     /* learned mode requested but no trained selector */
+} gpop_status;
+
+/* Opaque graph handle; owns the partitioned layout and all device memory. */
+typedef struct gpop_graph gpop_graph;
+
+/*
+ * Builds the partitioned layout from a CSR graph (pre-processing of Sec. 3.1:
+ * index partitions, per-partition E^p and r^p, the PNG of Alg. 3 with its
+ * destination-ID lists written once, and SC bin capacities).
+ *   num_vertices   V, 1 <= V < 2^31
+ *   num_edges      E, 0 <= E < 2^32
+ *   row_ptr        V+1 offsets (uint64), row_ptr[0] = 0, non-decreasing, row_ptr[V] = E
+ *   col            E destination IDs (< V); rows need not be sorted; self loops
+ *                  and repeated edges are kept as parallel edges
+ *   weights        E non-negative int32 edge weights (SSSP), or NULL
+ *   partition_size P, a power of two in [32, 65536], or 0 for the default
+ *                  (16384, clamped to V rounded up to a power of two); the
+ *                  partition count k = ceil(V/P) must not exceed 65536
+ *   mem_is_device  non-zero if row_ptr/col/weights are device pointers
+ *   cuda_stream    stream for the build kernels
+ *   out            receives the handle (unchanged on failure)
+ * Errors: GPOP_ERR_INVALID_ARG for malformed input (checked on the device),
+ * GPOP_ERR_OOM, GPOP_ERR_CUDA.
+ */
+gpop_status gpop_graph_build(uint32_t num_vertices, uint64_t num_edges, const uint64_t *row_ptr,
+                             const uint32_t *col, const int32_t *weights, uint32_t partition_size,
+                             int mem_is_device, void *cuda_stream, gpop_graph **out);
+
+typedef struct {
+    uint32_t num_vertices;
+    uint32_t partition_size;      /* P */
+    uint32_t num_partitions;      /* k */
+    uint32_t weighted;            /* 1 if built with weights */
+    uint64_t num_edges;           /* E */
+    uint64_t num_bins;            /* non-empty bin[p][q] pairs */
+    uint64_t num_png;             /* sum_p r^p E^p (PNG entries, unpadded) */
+    uint64_t num_png_padded;      /* PNG slots including per-row padding to 8 */
+    uint32_t num_gather_tasks;    /* static (column, destination range) tasks */
+    uint32_t num_scatter_tasks;   /* static PC scatter chunks */
+    uint32_t max_row_bins;        /* largest number of bins in one bin row */
+    uint32_t reserved;
+    uint64_t device_bytes;        /* device memory held by the handle */
+} gpop_graph_info;
+
+/* Fills *info.  Errors: GPOP_ERR_INVALID_ARG on NULL arguments. */
+gpop_status gpop_graph_get_info(const gpop_graph *g, gpop_graph_info *info);
+
+/* Copies per-partition E^p (out-edges) and n_png^p = r^p E^p (Sec. 3.1.2) into
+ * host arrays of k uint64 entries each (either may be NULL). */
+gpop_status gpop_graph_partition_stats(const gpop_graph *g, uint64_t *edges, uint64_t *png);
+
+/* Releases the handle and its device memory; NULL is ignored. */
+void gpop_graph_destroy(gpop_graph *g);
+
+typedef enum {
+    GPOP_PAGERANK = 0,   /* Alg. 6: topological PageRank, all vertices always active */
+    GPOP_BFS = 1,        /* Alg. 5: BFS levels and parents from a root */
+    GPOP_CC = 2,         /* Sec. 5: min-label propagation (use a symmetrised graph) */
+    GPOP_SSSP = 3,       /* Alg. 7: Bellman-Ford over non-negative integer weights */
+    GPOP_PPR = 4         /* seeded personalised PageRank, restart = 1 - damping */
+} gpop_algo;
+
+typedef enum {
+    GPOP_MODE_ANALYTIC = 0,   /* Eq. (mode) per partition per iteration */
+    GPOP_MODE_LEARNED = 1,    /* trained MLP selector, Eq. (mode) as fallback */
+    GPOP_MODE_FORCE_SC = 2,   /* every scattered partition in SC mode */
+    GPOP_MODE_FORCE_PC = 3,   /* every scattered partition in PC mode */
+    GPOP_MODE_LOG_BOTH = 4    /* Eq. (mode) decides; both scatters run and are timed */
+} gpop_mode_policy;
+
+typedef struct {
+    int32_t algo;              /* gpop_algo */
+    uint32_t source;           /* BFS/SSSP root, PPR seed (ignored by PageRank/CC) */
+    double damping;            /* PageRank d (default 0.85); PPR continuation 1 - restart */
+    uint32_t max_iters;        /* iteration cap (default 1000) */
+    double tol_l1;             /* PageRank/PPR: stop once sum_v |x_{t+1}-x_t| < tol_l1; 0 = run max_iters */
+    int32_t mode;              /* gpop_mode_policy */
+    uint32_t bw_ratio_num;     /* BW_PC / BW_SC = num / den (Sec. 3.2 default 2/1) */
+    uint32_t bw_ratio_den;
+    int32_t msg_bf16;          /* reserved, must be 0 (FP32 messages) */
+    int32_t profile_kernels;   /* non-zero: time every kernel launch with CUDA events (stats.kernel_*) */
+    void *cuda_stream;         /* stream for all kernels of the run */
+    uint8_t *trace_modes;      /* optional HOST buffer of max_iters * k bytes: per iteration and
+                                  partition 0 = not scattered, 1 = SC, 2 = PC */
+    uint64_t *trace_frontier;  /* optional HOST buffer of max_iters * 2: V_a and E_a entering each iteration */
+    float *log_buffer;         /* optional HOST buffer for GPOP_MODE_LOG_BOTH timing records,
+                                  log_capacity records of GPOP_LOG_RECORD_FLOATS floats */
+    uint64_t log_capacity;
+} gpop_run_opts;
+
+/* Floats per LOG_BOTH record: 8 selector features, t_PC (us), t_SC (us),
+ * chosen mode (2 PC / 1 SC), partition id, iteration. */
+#define GPOP_LOG_RECORD_FLOATS 13
+
+typedef struct {
+    uint32_t iterations;          /* scatter/gather rounds executed */
+    int32_t converged;            /* 1 if the frontier emptied or tol_l1 was met */
+    double residual;              /* last L1 change (PageRank/PPR), else 0 */
+    uint64_t edges_scattered;     /* sum over iterations of E_a (active out-edges) */
+    uint64_t vertices_scattered;  /* sum over iterations of V_a */
+    uint64_t pc_partition_steps;  /* partition-iterations scattered in PC mode */
+    uint64_t sc_partition_steps;  /* partition-iterations scattered in SC mode */
+    double model_bytes;           /* sum of Sec. 3.2 bytes of the chosen modes */
+    double device_ms;             /* CUDA-event time of the iteration loop */
+    uint64_t log_records;         /* LOG_BOTH records written */
+    /* with opts.profile_kernels: per kernel (0 plan, 1 PC scatter, 2 SC scatter, 3 gather)
+       the summed CUDA-event duration and the number of launches */
+    double kernel_ms[4];
+    uint64_t kernel_launches[4];
+} gpop_run_stats;
+
+/* Fills opts with defaults: PageRank, d = 0.85, max_iters 1000, tol 0,
+ * analytic mode, BW ratio 2/1, NULL stream and buffers. */
+void gpop_run_opts_default(gpop_run_opts *opts);
+
+/*
+ * Runs one application on the graph (Alg. 2 iterations until the frontier is
+ * empty, max_iters is reached, or for PageRank/PPR the L1 change drops below
+ * tol_l1).
+ *   out_values  V elements: float PageRank / PPR values; uint32 BFS level,
+ *               SSSP distance or CC label (0xFFFFFFFF = unreached)
+ *   out_parent  BFS only: V uint32 parents (root's parent is the root,
+ *               0xFFFFFFFF = unreached), or NULL
+ *   out_is_device  non-zero if out_values/out_parent are device pointers
+ *   stats       optional, filled on return
+ * Errors: GPOP_ERR_INVALID_ARG (bad source, weights missing for SSSP, ...),
+ * GPOP_ERR_NO_SELECTOR, GPOP_ERR_CUDA, GPOP_ERR_OOM.  Reaching max_iters is
+ * not an error (stats->converged tells).
+ */
+gpop_status gpop_run(gpop_graph *g, const gpop_run_opts *opts, void *out_values, uint32_t *out_parent,
+                     int out_is_device, gpop_run_stats *stats);
+
+/*
+ * Learned SC/PC selector (replaces Eq. (mode) per partition per iteration when
+ * opts.mode = GPOP_MODE_LEARNED).  An MLP 8 -> 32 -> 32 -> 1 with ReLU,
+ * FP32, predicting y = log(t_PC / t_SC); PC is chosen iff y <= 0.  Features
+ * are standardised with the stored mean/std; a partition whose features fall
+ * outside the training range [fmin, fmax] falls back to Eq. (mode).
+ * Parameter layout (GPOP_SELECTOR_PARAMS floats): W1[32][8], b1[32],
+ * W2[32][32], b2[32], W3[32], b3, then mean[8], std[8], fmin[8], fmax[8].
+ * The paper has no learned selector; the traffic model it replaces is Sec. 3.2.
+ */
+#define GPOP_SELECTOR_FEATURES 8
+#define GPOP_SELECTOR_HIDDEN 32
+#define GPOP_SELECTOR_WEIGHTS (32 * 8 + 32 + 32 * 32 + 32 + 32 + 1)
+#define GPOP_SELECTOR_PARAMS (GPOP_SELECTOR_WEIGHTS + 4 * 8)
+
+/* Installs selector parameters (host array of GPOP_SELECTOR_PARAMS floats)
+ * process-wide, or removes them when params is NULL. */
+gpop_status gpop_selector_set(const float *params);
+
+/* Copies the installed parameters to a host array; GPOP_ERR_NO_SELECTOR if none. */
+gpop_status gpop_selector_get(float *params);
+
+/*
+ * Trains the selector on the GPU with the library's own forward, backward and
+ * Adam kernels (mean squared error on y), full-batch.
+ *   features  n x 8 host floats (raw features as logged by LOG_BOTH)
+ *   targets   n host floats, y = log(t_PC / t_SC)
+ *   epochs, lr  Adam steps and step size; seed  initialisation stream
+ *   params_out  GPOP_SELECTOR_PARAMS host floats (trained weights + feature statistics)
+ *   loss_out    optional, final MSE
+ */
+gpop_status gpop_selector_train(const float *features, const float *targets, uint32_t n, uint32_t epochs,
+                                float lr, uint64_t seed, void *cuda_stream, float *params_out,
+                                float *loss_out);
+
+/*
+ * Forward pass and parameter gradients of the MSE loss on one batch (device
+ * kernels), for checking against a CPU reference.
+ *   params  GPOP_SELECTOR_WEIGHTS host floats (weights only)
+ *   x       n x 8 host floats, already standardised;  y  n host floats
+ *   pred_out n host floats;  grad_out GPOP_SELECTOR_WEIGHTS host floats;  loss_out optional
+ */
+gpop_status gpop_selector_grad(const float *params, const float *x, const float *y, uint32_t n,
+                               void *cuda_stream, float *pred_out, float *grad_out, float *loss_out);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char *gpop_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPOP_H */

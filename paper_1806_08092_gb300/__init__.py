@@ -1,0 +1,226 @@
+"""GB300 partition-centric scatter/gather (GPOP, arXiv 1806.08092) behind a C ABI.
+
+Python binding over libgpop.so: it only marshals arguments.  Every step of
+pre-processing and of each iteration runs in the library's CUDA kernels;
+PyTorch supplies device memory for outputs and the current CUDA stream.
+
+    import paper_1806_08092_gb300 as gp
+    g = gp.Graph.from_csr(row_ptr, col, weights=None, partition_size=16384)
+    res = g.run("pagerank", max_iters=10)          # res.values: torch tensor on cuda
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _lib
+from ._build import build as _build_lib
+from ._lib import ALGOS, MODES, GpopError, LOG_RECORD_FLOATS, SELECTOR_PARAMS, SELECTOR_WEIGHTS  # noqa: F401
+
+__all__ = ["build", "Graph", "RunResult", "GpopError", "selector_set", "selector_get", "selector_train",
+           "selector_grad"]
+
+
+def build(force: bool = False) -> str:
+    """Compiles libgpop.so for sm_103a in place and loads it."""
+    path = _build_lib(force=force)
+    _lib.load(path)
+    return path
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        if not torch.cuda.is_available():
+            return None
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _as_buffer(a, dtype_np, name):
+    """Returns (pointer, is_device, keepalive) for a numpy array or a torch tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            tdt = {np.uint64: torch.uint64, np.uint32: torch.uint32, np.int32: torch.int32}[dtype_np]
+            if a.dtype != tdt:
+                a = a.to(tdt)
+            a = a.contiguous()
+            return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda), a
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype_np)
+    return ctypes.c_void_p(arr.ctypes.data), 0, arr
+
+
+@dataclass
+class RunResult:
+    values: object                   # torch tensor (float32 PageRank/PPR, uint32 level/dist/label)
+    parent: object | None            # BFS parents
+    stats: dict
+    modes: np.ndarray | None = None  # [iterations, k] uint8 (0 none, 1 SC, 2 PC) when traced
+    frontier: np.ndarray | None = None  # [iterations, 2] (V_a, E_a) when traced
+    log: np.ndarray | None = None    # LOG_BOTH records [n, 13]
+    extra: dict = field(default_factory=dict)
+
+
+class Graph:
+    """A partitioned graph living on the GPU (owns a gpop_graph handle)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        self._info = None
+
+    @classmethod
+    def from_csr(cls, row_ptr, col, weights=None, partition_size: int = 0, stream=None) -> "Graph":
+        lib = _lib.load()
+        rp, rp_dev, rp_keep = _as_buffer(row_ptr, np.uint64, "row_ptr")
+        cl, cl_dev, cl_keep = _as_buffer(col, np.uint32, "col")
+        n = int(rp_keep.shape[0]) - 1
+        m = int(cl_keep.shape[0])
+        w = ctypes.c_void_p(None)
+        w_keep = None
+        if weights is not None:
+            w, w_dev, w_keep = _as_buffer(weights, np.int32, "weights")
+            if w_dev != rp_dev:
+                raise ValueError("weights must live where row_ptr/col live")
+        if rp_dev != cl_dev:
+            raise ValueError("row_ptr and col must both be host or both be device memory")
+        h = ctypes.c_void_p()
+        _lib.check(lib.gpop_graph_build(n, m, rp, cl, w, partition_size, rp_dev, _stream_handle(stream),
+                                        ctypes.byref(h)))
+        del rp_keep, cl_keep, w_keep
+        return cls(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _lib.load().gpop_graph_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def close(self):
+        self.__del__()
+
+    def info(self) -> dict:
+        info = _lib.GraphInfo()
+        _lib.check(_lib.load().gpop_graph_get_info(self._h, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in info._fields_}
+
+    def partition_stats(self):
+        k = self.info()["num_partitions"]
+        ep = np.zeros(k, dtype=np.uint64)
+        npng = np.zeros(k, dtype=np.uint64)
+        _lib.check(_lib.load().gpop_graph_partition_stats(self._h, ctypes.c_void_p(ep.ctypes.data),
+                                                          ctypes.c_void_p(npng.ctypes.data)))
+        return ep, npng
+
+    def run(self, algo: str, source: int = 0, damping: float = 0.85, max_iters: int = 1000, tol: float = 0.0,
+            mode: str = "analytic", bw_ratio=(2, 1), device_out: bool = True, trace: bool = False,
+            log_capacity: int = 0, stream=None, out=None, out_parent=None, profile: bool = False) -> RunResult:
+        """Runs one application; outputs are torch tensors on cuda (device_out) or host numpy arrays."""
+        torch = _torch()
+        lib = _lib.load()
+        info = self.info()
+        n, k = info["num_vertices"], info["num_partitions"]
+        o = _lib.RunOpts()
+        lib.gpop_run_opts_default(ctypes.byref(o))
+        o.algo = ALGOS[algo]
+        o.source = source
+        o.damping = damping
+        o.max_iters = max_iters
+        o.tol_l1 = tol
+        o.mode = MODES[mode]
+        o.bw_ratio_num, o.bw_ratio_den = bw_ratio
+        o.cuda_stream = _stream_handle(stream)
+        o.profile_kernels = int(profile)
+        modes = frontier = log = None
+        if trace:
+            modes = np.zeros(max(max_iters, 1) * k, dtype=np.uint8)
+            frontier = np.zeros(max(max_iters, 1) * 2, dtype=np.uint64)
+            o.trace_modes = ctypes.c_void_p(modes.ctypes.data)
+            o.trace_frontier = ctypes.c_void_p(frontier.ctypes.data)
+        if log_capacity:
+            log = np.zeros(log_capacity * LOG_RECORD_FLOATS, dtype=np.float32)
+            o.log_buffer = ctypes.c_void_p(log.ctypes.data)
+            o.log_capacity = log_capacity
+        fdt = algo in ("pagerank", "ppr")
+        if device_out:
+            if out is None:
+                out = torch.empty(n, dtype=torch.float32 if fdt else torch.uint32, device="cuda")
+            if algo == "bfs" and out_parent is None:
+                out_parent = torch.empty(n, dtype=torch.uint32, device="cuda")
+            pv, pp = out.data_ptr(), (out_parent.data_ptr() if out_parent is not None else None)
+        else:
+            if out is None:
+                out = np.empty(n, dtype=np.float32 if fdt else np.uint32)
+            if algo == "bfs" and out_parent is None:
+                out_parent = np.empty(n, dtype=np.uint32)
+            pv = out.ctypes.data
+            pp = out_parent.ctypes.data if out_parent is not None else None
+        st = _lib.RunStats()
+        _lib.check(lib.gpop_run(self._h, ctypes.byref(o), ctypes.c_void_p(pv), ctypes.c_void_p(pp),
+                                int(device_out), ctypes.byref(st)))
+        stats = st.as_dict()
+        it = stats["iterations"]
+        if trace:
+            modes = modes[: it * k].reshape(it, k)
+            frontier = frontier[: it * 2].reshape(it, 2)
+        if log is not None:
+            log = log[: stats["log_records"] * LOG_RECORD_FLOATS].reshape(-1, LOG_RECORD_FLOATS)
+        return RunResult(out, out_parent if algo == "bfs" else None, stats, modes, frontier, log)
+
+
+def selector_set(params) -> None:
+    """Installs learned-selector parameters (GPOP_SELECTOR_PARAMS floats) or removes them (None)."""
+    lib = _lib.load()
+    if params is None:
+        _lib.check(lib.gpop_selector_set(None))
+        return
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.shape == (SELECTOR_PARAMS,)
+    _lib.check(lib.gpop_selector_set(ctypes.c_void_p(p.ctypes.data)))
+
+
+def selector_get():
+    p = np.zeros(SELECTOR_PARAMS, dtype=np.float32)
+    _lib.check(_lib.load().gpop_selector_get(ctypes.c_void_p(p.ctypes.data)))
+    return p
+
+
+def selector_train(features, targets, epochs: int = 2000, lr: float = 3e-3, seed: int = 1, stream=None):
+    """Trains the MLP selector on the GPU; returns (params, final MSE)."""
+    f = np.ascontiguousarray(features, dtype=np.float32)
+    y = np.ascontiguousarray(targets, dtype=np.float32)
+    assert f.ndim == 2 and f.shape[1] == 8 and y.shape == (f.shape[0],)
+    p = np.zeros(SELECTOR_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _lib.check(_lib.load().gpop_selector_train(ctypes.c_void_p(f.ctypes.data), ctypes.c_void_p(y.ctypes.data),
+                                               f.shape[0], epochs, lr, seed, _stream_handle(stream),
+                                               ctypes.c_void_p(p.ctypes.data), ctypes.byref(loss)))
+    return p, float(loss.value)
+
+
+def selector_grad(weights, x, y, stream=None):
+    """GPU forward + MSE parameter gradient on standardised inputs; returns (pred, grad, loss)."""
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    xx = np.ascontiguousarray(x, dtype=np.float32)
+    yy = np.ascontiguousarray(y, dtype=np.float32)
+    assert w.shape == (SELECTOR_WEIGHTS,)
+    pred = np.zeros(yy.shape[0], dtype=np.float32)
+    grad = np.zeros(SELECTOR_WEIGHTS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _lib.check(_lib.load().gpop_selector_grad(ctypes.c_void_p(w.ctypes.data), ctypes.c_void_p(xx.ctypes.data),
+                                              ctypes.c_void_p(yy.ctypes.data), yy.shape[0], _stream_handle(stream),
+                                              ctypes.c_void_p(pred.ctypes.data), ctypes.c_void_p(grad.ctypes.data),
+                                              ctypes.byref(loss)))
+    return pred, grad, float(loss.value)

@@ -1,0 +1,1018 @@
+// Per-iteration scatter/gather engine (Alg. 2 with Alg. 3 and Eq. (mode)).
+//
+// One iteration = four launches on the caller's stream:
+//   k_plan        1 CTA: per-partition V_a/E_a from the previous gather, mode
+//                 choice (Eq. (mode), forced, or learned), PC/NULL actions,
+//                 SC work list, termination test (Sec. 3.1.x active lists).
+//   k_scatter_pc  PC mode (Alg. 3): every PNG slot of a PC partition receives
+//                 the current value of its source (NULL if inactive) as a
+//                 sequential vectorised stream over the padded row.
+//   k_scatter_sc  SC mode (Alg. 2 scatter): active vertices of the partition
+//                 append (destination, value) pairs to their bins through
+//                 warp-aggregated cursors.
+//   k_gather      per (column q, destination range) task: PC messages through
+//                 the destination-sorted lists (segmented reductions, no
+//                 atomics on vertex data), SC pairs with per-warp destination
+//                 ownership, then reInit/gather/filter user functions and the
+//                 next frontier (Alg. 2 gather + filter; Sec. 4).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "gpop_internal.cuh"
+
+namespace gpop {
+
+enum Algo : int { ALG_PR = GPOP_PAGERANK, ALG_BFS = GPOP_BFS, ALG_CC = GPOP_CC, ALG_SSSP = GPOP_SSSP, ALG_PPR = GPOP_PPR };
+
+constexpr int kGatherThreads = 256;
+constexpr int kGatherWarps = kGatherThreads / 32;
+constexpr int kScatterThreads = 256;
+constexpr int kPlanThreads = 1024;
+constexpr uint32_t kSent = 0xFFFFFFFFu;
+
+struct Params {
+    // graph
+    uint32_t V, P, shift, k;
+    const uint32_t *rowptr, *col;
+    const int32_t *w;
+    const uint16_t *ebin;
+    const uint32_t *row_bin, *bin_q, *bin_sc, *col_bin, *col_bins;
+    const uint16_t *png;
+    uint32_t *pdata;
+    const uint32_t *row_png;
+    const uint32_t *cptr, *cidx;
+    const uint16_t *cdst;
+    const int32_t *cw;
+    uint2 *scpair;
+    uint32_t *sccnt, *scstamp;
+    const uint32_t *Ep, *npng_p;
+    const GatherTask *gtask;
+    uint32_t ngt;
+    const uint32_t *col_task;
+    const ScatterTask *stask;
+    uint32_t nst;
+    uint8_t *pc_state;
+    // run state
+    uint32_t *val, *lvl, *sval, *bits;
+    uint32_t *t_va;
+    unsigned long long *t_ea;
+    double *t_res;
+    uint32_t *t_stamp;
+    uint8_t *mode, *action;
+    uint32_t *gflag, *gflag_pc, *gflag_sc, *sc_list, *counters;
+    Control *ctrl;
+    const float *selector;  // learned selector parameters or null
+    // per launch
+    uint32_t epoch, iter, source, max_iters;
+    float c0, c1;           // PR: (1-d)/V, d.  PPR: alpha, 1-alpha
+    double tol;
+    int algo, policy;
+    uint32_t bw_num, bw_den;
+};
+
+// --- small device helpers ----------------------------------------------------------------------
+
+__device__ __forceinline__ float u2f(uint32_t x) { return __uint_as_float(x); }
+__device__ __forceinline__ uint32_t f2u(float x) { return __float_as_uint(x); }
+
+template <int ALGO>
+struct Op {
+    // monoid used to combine the messages a vertex receives in one gather
+    static __device__ __forceinline__ uint32_t identity() {
+        return (ALGO == ALG_PR || ALGO == ALG_PPR) ? 0u : kInf;
+    }
+    static __device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b) {
+        if (ALGO == ALG_PR || ALGO == ALG_PPR) return f2u(u2f(a) + u2f(b));
+        return a < b ? a : b;
+    }
+    // applyWeight of Alg. 7 (SSSP adds the edge weight, saturating below kInf)
+    static __device__ __forceinline__ uint32_t weigh(uint32_t x, int32_t w) {
+        if (ALGO == ALG_SSSP) {
+            uint64_t s = (uint64_t)x + (uint32_t)w;
+            return s >= kInf ? kInf - 1 : (uint32_t)s;
+        }
+        return x;
+    }
+};
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// exclusive scan across a block of blockDim.x threads (multiple of 32, <= 1024)
+__device__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_warp, uint32_t *total) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = warp_incl_scan(x, lane);
+    if (lane == 31) s_warp[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = lane < nw ? s_warp[lane] : 0;
+        uint32_t ti = warp_incl_scan(t, lane);
+        if (lane < nw) s_warp[lane] = ti - t;
+        if (lane == nw - 1) s_warp[32] = ti;
+    }
+    __syncthreads();
+    uint32_t r = inc - x + s_warp[wid];
+    if (total) *total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+// --- Eq. (mode) ----------------------------------------------------------------------------------
+
+// PC iff den * E^p * (3 n_png + k + E^p) <= num * (V_a E^p + 3 E_a E^p + 2 n_png E_a):
+// Sec. 3.2's two traffic formulas (s_i = s_v = 4 B) multiplied through by E^p
+// (so r^p E_a becomes the integer n_png E_a) and divided by 4.
+__device__ __forceinline__ uint8_t analytic_mode(uint64_t k, uint64_t Ep, uint64_t npng, uint64_t Va, uint64_t Ea,
+                                                 uint32_t num, uint32_t den) {
+    if (Va == 0 || Ep == 0) return kModeNone;
+    unsigned __int128 pc = (unsigned __int128)den * Ep * (unsigned __int128)(3 * npng + k + Ep);
+    unsigned __int128 sc = (unsigned __int128)num *
+                           ((unsigned __int128)Va * Ep + (unsigned __int128)3 * Ea * Ep + (unsigned __int128)2 * npng * Ea);
+    return pc <= sc ? kModePC : kModeSC;
+}
+
+__device__ __forceinline__ double mode_bytes(uint8_t m, uint64_t k, uint64_t Ep, uint64_t npng, uint64_t Va, uint64_t Ea) {
+    if (m == kModePC) return 4.0 * (double)(3 * npng + k + Ep);
+    if (m == kModeSC) return 4.0 * ((double)Va + 3.0 * (double)Ea + 2.0 * ((double)npng / (double)Ep) * (double)Ea);
+    return 0.0;
+}
+
+// Learned selector: MLP 8->32->32->1 (ReLU), lane j computes hidden unit j.
+// Returns 2 (PC), 1 (SC) or 0xFF when the features are outside the training
+// range (the caller then falls back to Eq. (mode)).  All lanes must call it.
+__device__ uint8_t learned_mode(const float *sp, const float f[8], int lane) {
+    const float *W1 = sp, *b1 = W1 + 256, *W2 = b1 + 32, *b2 = W2 + 1024, *W3 = b2 + 32, *b3 = W3 + 32;
+    const float *mean = b3 + 1, *sd = mean + 8, *fmin = sd + 8, *fmax = fmin + 8;
+    bool in_range = true;
+    float z[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        in_range &= (f[i] >= fmin[i]) && (f[i] <= fmax[i]);
+        z[i] = (f[i] - mean[i]) / sd[i];
+    }
+    float h1 = b1[lane];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h1 = fmaf(W1[lane * 8 + i], z[i], h1);
+    h1 = fmaxf(h1, 0.f);
+    float h2 = b2[lane];
+    for (int i = 0; i < 32; ++i) h2 = fmaf(W2[lane * 32 + i], __shfl_sync(0xffffffffu, h1, i), h2);
+    h2 = fmaxf(h2, 0.f);
+    float y = W3[lane] * h2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    y += b3[0];
+    if (!in_range) return 0xFF;
+    return y <= 0.f ? kModePC : kModeSC;
+}
+
+// --- initial frontier --------------------------------------------------------------------------
+
+template <int ALGO>
+__global__ void k_init(Params p) {
+    uint32_t nw = (p.V + 31) / 32;
+    for (uint32_t wi = blockIdx.x * blockDim.x + threadIdx.x; wi < nw; wi += gridDim.x * blockDim.x) {
+        uint32_t word = 0;
+        for (int b = 0; b < 32; ++b) {
+            uint32_t g = wi * 32 + b;
+            if (g >= p.V) break;
+            uint32_t deg = p.rowptr[g + 1] - p.rowptr[g];
+            bool act;
+            uint32_t v, sv;
+            if (ALGO == ALG_PR) {
+                float x = 1.0f / (float)p.V;
+                v = f2u(x);
+                act = true;
+                sv = f2u(deg ? x / (float)deg : 0.f);
+            } else if (ALGO == ALG_PPR) {
+                act = (g == p.source);
+                v = f2u(act ? 1.f : 0.f);
+                sv = act ? f2u(deg ? 1.f / (float)deg : 0.f) : kNull;
+            } else if (ALGO == ALG_BFS) {
+                act = (g == p.source);
+                v = act ? g : kInf;
+                p.lvl[g] = act ? 0u : kInf;
+                sv = act ? g : kNull;
+            } else if (ALGO == ALG_SSSP) {
+                act = (g == p.source);
+                v = act ? 0u : kInf;
+                sv = act ? 0u : kNull;
+            } else {  // CC: own ID as label, everyone active
+                act = true;
+                v = g;
+                sv = g;
+            }
+            p.val[g] = v;
+            p.sval[g] = sv;
+            if (act) word |= 1u << b;
+        }
+        p.bits[wi] = word;
+    }
+}
+
+// frontier statistics of every gather task from the bitmap (used once, for the initial frontier)
+__global__ void k_task_stats(Params p) {
+    __shared__ uint32_t s_va[kGatherWarps];
+    __shared__ unsigned long long s_ea[kGatherWarps];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (uint32_t t = blockIdx.x; t < p.ngt; t += gridDim.x) {
+        GatherTask gt = p.gtask[t];
+        uint32_t va = 0;
+        unsigned long long ea = 0;
+        for (uint32_t d = gt.d0 + threadIdx.x; d < gt.d1; d += blockDim.x) {
+            uint32_t g = (gt.q << p.shift) + d;
+            if (g < p.V && ((p.bits[g >> 5] >> (g & 31)) & 1u)) {
+                va++;
+                ea += p.rowptr[g + 1] - p.rowptr[g];
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            va += __shfl_xor_sync(0xffffffffu, va, o);
+            ea += __shfl_xor_sync(0xffffffffu, ea, o);
+        }
+        if (lane == 0) { s_va[wid] = va; s_ea[wid] = ea; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t a = 0;
+            unsigned long long b = 0;
+            for (int i = 0; i < kGatherWarps; ++i) { a += s_va[i]; b += s_ea[i]; }
+            p.t_va[t] = a;
+            p.t_ea[t] = b;
+            p.t_res[t] = 0.0;
+            p.t_stamp[t] = p.epoch;
+        }
+        __syncthreads();
+    }
+}
+
+// --- plan: modes, actions, SC list, termination ------------------------------------------------
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
+    __shared__ uint32_t s_warp[33];
+    __shared__ unsigned long long s_v[kPlanThreads / 32], s_e[kPlanThreads / 32];
+    __shared__ double s_r[kPlanThreads / 32], s_b[kPlanThreads / 32];
+    __shared__ uint32_t s_pc[kPlanThreads / 32], s_sc[kPlanThreads / 32], s_nl[kPlanThreads / 32], s_fb[kPlanThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t prev = p.epoch - 1;
+    unsigned long long tv = 0, te = 0;
+    double tr = 0.0, tb = 0.0;
+    uint32_t npc = 0, nsc = 0, nnull = 0, nfb = 0, sc_base = 0;
+
+    // partitions in chunks of blockDim so the SC list can be compacted in order
+    for (uint32_t base = 0; base < p.k; base += blockDim.x) {
+        uint32_t q = base + threadIdx.x;
+        uint8_t m = kModeNone;
+        bool valid = q < p.k;
+        uint64_t Va = 0, Ea = 0, Ep = 0, np = 0;
+        if (valid) {
+            double res = 0.0;
+            for (uint32_t t = p.col_task[q]; t < p.col_task[q + 1]; ++t)
+                if (p.t_stamp[t] == prev) { Va += p.t_va[t]; Ea += p.t_ea[t]; res += p.t_res[t]; }
+            Ep = p.Ep[q];
+            np = p.npng_p[q];
+            tv += Va; te += Ea; tr += res;
+            if (Va == 0 || Ep == 0) m = kModeNone;
+            else if (p.policy == GPOP_MODE_FORCE_SC) m = kModeSC;
+            else if (p.policy == GPOP_MODE_FORCE_PC) m = kModePC;
+            else m = analytic_mode(p.k, Ep, np, Va, Ea, p.bw_num, p.bw_den);
+        }
+        if (p.policy == GPOP_MODE_LEARNED && p.selector) {
+            // one warp evaluates the MLP for each of its 32 partitions in turn
+            for (int j = 0; j < 32; ++j) {
+                uint64_t jVa = __shfl_sync(0xffffffffu, Va, j), jEa = __shfl_sync(0xffffffffu, Ea, j);
+                uint64_t jEp = __shfl_sync(0xffffffffu, Ep, j), jnp = __shfl_sync(0xffffffffu, np, j);
+                uint8_t jm = (uint8_t)__shfl_sync(0xffffffffu, (uint32_t)m, j);
+                uint32_t jq = base + (threadIdx.x & ~31u) + j;
+                if (jm == kModeNone) continue;  // uniform across the warp
+                float f[8];
+                double cpc = 4.0 * (double)(3 * jnp + p.k + jEp) * p.bw_den;
+                double csc = 4.0 * ((double)jVa + 3.0 * (double)jEa + 2.0 * ((double)jnp / (double)jEp) * (double)jEa) * p.bw_num;
+                f[0] = log1pf((float)jVa);
+                f[1] = log1pf((float)jEa);
+                f[2] = log1pf((float)jEp);
+                f[3] = (float)((double)jnp / (double)jEp);
+                f[4] = log1pf((float)(p.row_bin[jq + 1] - p.row_bin[jq]));
+                f[5] = log1pf((float)jnp);
+                f[6] = log1pf((float)p.k);
+                f[7] = (float)log(cpc / csc);
+                uint8_t lm = learned_mode(p.selector, f, lane);
+                if (lane == j) {
+                    if (lm == 0xFF) nfb++;
+                    else m = lm;
+                }
+            }
+        }
+        if (valid) {
+            p.mode[q] = m;
+            tb += mode_bytes(m, p.k, Ep, np, Va, Ea);
+            if (Va > 0) p.gflag[q] = p.epoch;  // active partitions are gathered (reInit of Alg. 2)
+            npc += (m == kModePC);
+            nsc += (m == kModeSC);
+            uint8_t act = m == kModePC ? kActPC : (p.pc_state[q] ? kActNull : kActSkip);
+            nnull += (act == kActNull);
+            p.action[q] = act;
+        }
+        uint32_t total;
+        uint32_t off = block_excl_scan((valid && m == kModeSC) ? 1u : 0u, s_warp, &total);
+        if (valid && m == kModeSC) p.sc_list[sc_base + off] = q;
+        sc_base += total;
+    }
+    // deterministic block reductions (fixed tree order)
+    for (int o = 16; o > 0; o >>= 1) {
+        tv += __shfl_xor_sync(0xffffffffu, tv, o);
+        te += __shfl_xor_sync(0xffffffffu, te, o);
+        tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        tb += __shfl_xor_sync(0xffffffffu, tb, o);
+        npc += __shfl_xor_sync(0xffffffffu, npc, o);
+        nsc += __shfl_xor_sync(0xffffffffu, nsc, o);
+        nnull += __shfl_xor_sync(0xffffffffu, nnull, o);
+        nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
+    }
+    if (lane == 0) {
+        s_v[wid] = tv; s_e[wid] = te; s_r[wid] = tr; s_b[wid] = tb;
+        s_pc[wid] = npc; s_sc[wid] = nsc; s_nl[wid] = nnull; s_fb[wid] = nfb;
+    }
+    __syncthreads();
+    __shared__ uint32_t s_done;
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, b = 0;
+        double r = 0.0, by = 0.0;
+        uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            a += s_v[i]; b += s_e[i]; r += s_r[i]; by += s_b[i];
+            c0 += s_pc[i]; c1 += s_sc[i]; c2 += s_nl[i]; c3 += s_fb[i];
+        }
+        uint32_t done = (a == 0) || (p.iter > p.max_iters);
+        if ((p.algo == ALG_PR || p.algo == ALG_PPR) && p.iter > 1 && r < p.tol) done = 1;
+        Control c;
+        c.frontier_v = a; c.frontier_e = b; c.residual = r; c.model_bytes = by;
+        c.n_pc = c0; c.n_sc = c1; c.n_null = c2; c.done = done; c.n_fallback = c3; c.error = 0;
+        c.pad[0] = c.pad[1] = 0;
+        *p.ctrl = c;
+        p.counters[0] = 0;
+        p.counters[1] = 0;
+        p.counters[2] = 0;
+        s_done = done;
+    }
+    __syncthreads();
+    if (!s_done)  // commit the PC-state of each data row only if this iteration runs
+        for (uint32_t q = threadIdx.x; q < p.k; q += blockDim.x) p.pc_state[q] = p.mode[q] == kModePC;
+}
+
+// --- PC scatter (Alg. 3) -----------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kScatterThreads) k_scatter_pc(Params p) {
+    __shared__ uint32_t s_task;
+    for (;;) {
+        if (threadIdx.x == 0) s_task = atomicAdd(&p.counters[0], 1u);
+        __syncthreads();
+        uint32_t t = s_task;
+        __syncthreads();
+        if (t >= p.nst) break;
+        ScatterTask st = p.stask[t];
+        uint8_t act = p.action[st.p];
+        if (act == kActSkip) continue;
+        if (act == kActPC && st.first) {
+            // the partition's messages reach every column of its bin row
+            for (uint32_t b = p.row_bin[st.p] + threadIdx.x; b < p.row_bin[st.p + 1]; b += blockDim.x) {
+                uint32_t q = p.bin_q[b];
+                p.gflag[q] = p.epoch;
+                p.gflag_pc[q] = p.epoch;
+            }
+        }
+        const uint32_t vbase = st.p << p.shift;
+        for (uint32_t i = st.beg + threadIdx.x * 8; i < st.end; i += blockDim.x * 8) {
+            uint4 o0, o1;
+            if (act == kActPC) {
+                uint4 s = *reinterpret_cast<const uint4 *>(p.png + i);
+                o0.x = p.sval[vbase + (s.x & 0xFFFFu)];
+                o0.y = p.sval[vbase + (s.x >> 16)];
+                o0.z = p.sval[vbase + (s.y & 0xFFFFu)];
+                o0.w = p.sval[vbase + (s.y >> 16)];
+                o1.x = p.sval[vbase + (s.z & 0xFFFFu)];
+                o1.y = p.sval[vbase + (s.z >> 16)];
+                o1.z = p.sval[vbase + (s.w & 0xFFFFu)];
+                o1.w = p.sval[vbase + (s.w >> 16)];
+            } else {
+                o0 = make_uint4(kNull, kNull, kNull, kNull);
+                o1 = o0;
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(p.pdata + i);
+            dst[0] = o0;
+            dst[1] = o1;
+        }
+    }
+}
+
+// --- SC scatter (Alg. 2 scatter in source-centric mode) ---------------------------------------
+
+template <int ALGO>
+__global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
+    extern __shared__ uint32_t s_cursor[];  // one insertion point per bin of the row
+    __shared__ uint32_t s_list[1024];       // active local IDs of the current 1024-vertex segment
+    __shared__ uint32_t s_pref[1025];       // exclusive prefix of their out-degrees
+    __shared__ uint32_t s_warp[33];
+    __shared__ uint32_t s_task, s_nact;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nsc = p.ctrl->n_sc;
+    for (;;) {
+        if (threadIdx.x == 0) s_task = atomicAdd(&p.counters[1], 1u);
+        __syncthreads();
+        uint32_t t = s_task;
+        __syncthreads();
+        if (t >= nsc) break;
+        const uint32_t part = p.sc_list[t];
+        const uint32_t rb0 = p.row_bin[part], nbr = p.row_bin[part + 1] - rb0;
+        for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) s_cursor[i] = 0;
+        const uint32_t g0 = part << p.shift;
+        const uint32_t gend = min(g0 + p.P, p.V);
+        for (uint32_t seg = g0; seg < gend; seg += 1024) {
+            // active vertices of this segment, ascending
+            if (threadIdx.x < 32) {
+                uint32_t gw = seg + threadIdx.x * 32;
+                uint32_t word = gw < gend ? p.bits[gw >> 5] : 0u;
+                uint32_t c = __popc(word);
+                uint32_t off = warp_incl_scan(c, lane) - c;
+                while (word) {
+                    int b = __ffs(word) - 1;
+                    word &= word - 1;
+                    s_list[off++] = gw + b;
+                }
+                if (lane == 31) s_nact = off;
+            }
+            __syncthreads();
+            const uint32_t nact = s_nact;
+            // out-degree prefix
+            uint32_t total = 0;
+            for (uint32_t base = 0; base < nact; base += blockDim.x) {
+                uint32_t i = base + threadIdx.x;
+                uint32_t d = i < nact ? p.rowptr[s_list[i] + 1] - p.rowptr[s_list[i]] : 0;
+                uint32_t tt;
+                uint32_t ex = block_excl_scan(d, s_warp, &tt);
+                if (i < nact) s_pref[i] = total + ex;
+                total += tt;
+            }
+            if (threadIdx.x == 0) s_pref[nact] = total;
+            __syncthreads();
+            // expand the active edges, one thread per edge
+            for (uint32_t base = 0; base < total; base += blockDim.x) {
+                uint32_t e = base + threadIdx.x;
+                bool live = e < total;
+                uint32_t lb = 0xFFFFFFFFu, dloc = 0, val = 0, slot = 0;
+                if (live) {
+                    uint32_t lo = 0, hi = nact;  // largest i with s_pref[i] <= e
+                    while (hi - lo > 1) {
+                        uint32_t mid = (lo + hi) >> 1;
+                        if (s_pref[mid] <= e) lo = mid; else hi = mid;
+                    }
+                    uint32_t u = s_list[lo];
+                    uint32_t edge = p.rowptr[u] + (e - s_pref[lo]);
+                    uint32_t dst = p.col[edge];
+                    lb = p.ebin[edge];
+                    dloc = dst & (p.P - 1);
+                    val = p.sval[u];
+                    if (ALGO == ALG_SSSP) val = Op<ALGO>::weigh(val, p.w[edge]);
+                }
+                // warp-aggregated insertion: one cursor bump per distinct bin in the warp
+                uint32_t peers = __match_any_sync(0xffffffffu, lb);
+                int leader = __ffs(peers) - 1;
+                uint32_t rank = __popc(peers & ((1u << lane) - 1));
+                uint32_t basepos = 0;
+                if (live && lane == leader) basepos = atomicAdd(&s_cursor[lb], (uint32_t)__popc(peers));
+                basepos = __shfl_sync(0xffffffffu, basepos, leader);
+                if (live) {
+                    slot = p.bin_sc[rb0 + lb] + basepos + rank;
+                    p.scpair[slot] = make_uint2(dloc, val);
+                }
+            }
+            __syncthreads();
+        }
+        // publish counts and the 2-level active list entries (gPartList / binPartList via stamps)
+        for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) {
+            uint32_t c = s_cursor[i];
+            if (c) {
+                uint32_t b = rb0 + i;
+                p.sccnt[b] = c;
+                p.scstamp[b] = p.epoch;
+                uint32_t q = p.bin_q[b];
+                p.gflag[q] = p.epoch;
+                p.gflag_sc[q] = p.epoch;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// --- gather + filter ---------------------------------------------------------------------------
+
+// Segmented reduction of the destination-sorted PC lists [a, b) by one warp.
+// Every segment (one destination) except the warp's first is complete inside
+// this warp and written straight to acc; the first may continue a segment of
+// the previous warp and goes to the carry slot, merged in warp order later.
+template <int ALGO>
+__device__ __forceinline__ void csc_warp(const Params &p, uint32_t a, uint32_t b, uint32_t d0, uint32_t *acc,
+                                         uint2 *carry, int lane) {
+    using O = Op<ALGO>;
+    uint32_t cur_d = kSent, cur_v = O::identity();
+    bool have_cur = false, cur_first = false, first_chunk = true;
+    constexpr int U = 4;
+    for (uint32_t base = a; base < b; base += 32 * U) {
+        uint32_t dd[U], vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            uint32_t j = base + u * 32 + lane;
+            dd[u] = kSent;
+            vv[u] = kNull;
+            if (j < b) {
+                dd[u] = (uint32_t)p.cdst[j] - d0;
+                vv[u] = p.cidx[j];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            uint32_t j = base + u * 32 + lane;
+            if (j < b) {
+                uint32_t x = p.pdata[vv[u]];
+                vv[u] = (x == kNull) ? O::identity()
+                                     : O::weigh(x, (ALGO == ALG_SSSP) ? p.cw[j] : 0);
+            } else {
+                vv[u] = O::identity();
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            uint32_t cbase = base + u * 32;
+            if (cbase >= b) break;
+            uint32_t d = dd[u], v = vv[u];
+            uint32_t d_lane0 = __shfl_sync(0xffffffffu, d, 0);
+            if (have_cur && cur_d != d_lane0) {
+                if (lane == 0) {
+                    if (cur_first) *carry = make_uint2(cur_d, cur_v);
+                    else acc[cur_d] = cur_v;
+                }
+                have_cur = false;
+            }
+            bool lane0_first = have_cur ? cur_first : first_chunk;
+            if (lane == 0 && have_cur) v = O::combine(cur_v, v);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t vu = __shfl_up_sync(0xffffffffu, v, o);
+                uint32_t du = __shfl_up_sync(0xffffffffu, d, o);
+                if (lane >= o && du == d) v = O::combine(vu, v);
+            }
+            uint32_t d_next = __shfl_down_sync(0xffffffffu, d, 1);
+            uint32_t nvalid = min(32u, b - cbase);
+            int last = (int)nvalid - 1;
+            bool valid = lane < (int)nvalid;
+            bool tail = valid && (lane == last || d_next != d);
+            bool seg_first = (d == d_lane0) && lane0_first;
+            if (tail && lane != last) {
+                if (seg_first) *carry = make_uint2(d, v);
+                else acc[d] = v;
+            }
+            cur_d = __shfl_sync(0xffffffffu, d, last);
+            cur_v = __shfl_sync(0xffffffffu, v, last);
+            cur_first = __shfl_sync(0xffffffffu, (int)seg_first, last);
+            have_cur = true;
+            first_chunk = false;
+        }
+    }
+    if (have_cur && lane == 0) {
+        if (cur_first) *carry = make_uint2(cur_d, cur_v);
+        else acc[cur_d] = cur_v;
+    }
+}
+
+template <int ALGO>
+__global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
+    using O = Op<ALGO>;
+    __shared__ uint32_t s_acc[kGatherWidth];
+    __shared__ uint2 s_carry[kGatherWarps];
+    __shared__ uint32_t s_stage[kGatherWarps][32];
+    __shared__ uint32_t s_task;
+    __shared__ uint32_t s_va[kGatherWarps];
+    __shared__ unsigned long long s_ea[kGatherWarps];
+    __shared__ double s_res[kGatherWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_task = atomicAdd(&p.counters[2], 1u);
+        __syncthreads();
+        const uint32_t t = s_task;
+        __syncthreads();
+        if (t >= p.ngt) break;
+        const GatherTask gt = p.gtask[t];
+        const uint32_t q = gt.q;
+        if (p.gflag[q] != p.epoch) continue;
+        const uint32_t width = gt.d1 - gt.d0;
+        const uint32_t gq = q << p.shift;
+        for (uint32_t i = threadIdx.x; i < width; i += blockDim.x) s_acc[i] = O::identity();
+        if (threadIdx.x < kGatherWarps) s_carry[threadIdx.x] = make_uint2(kSent, 0);
+        __syncthreads();
+
+        // PC messages: destination-sorted lists of this range, split evenly over the warps
+        if (p.gflag_pc[q] == p.epoch) {
+            uint32_t e0 = p.cptr[gq + gt.d0], e1 = p.cptr[min(gq + gt.d1, p.V)];
+            uint32_t n = e1 - e0;
+            uint32_t a = e0 + (uint32_t)(((uint64_t)n * wid) / kGatherWarps);
+            uint32_t b = e0 + (uint32_t)(((uint64_t)n * (wid + 1)) / kGatherWarps);
+            csc_warp<ALGO>(p, a, b, gt.d0, s_acc, &s_carry[wid], lane);
+            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int w = 0; w < kGatherWarps; ++w) {
+                    uint2 c = s_carry[w];
+                    if (c.x != kSent) s_acc[c.x] = O::combine(s_acc[c.x], c.y);
+                }
+            __syncthreads();
+        }
+
+        // SC messages: every warp scans the column's fresh SC bins and applies the
+        // pairs whose destination lies in its own slice of [d0, d1)
+        if (p.gflag_sc[q] == p.epoch) {
+            const uint32_t lo = (width * wid) / kGatherWarps, hi = (width * (wid + 1)) / kGatherWarps;
+            for (uint32_t i = p.col_bin[q]; i < p.col_bin[q + 1]; ++i) {
+                uint32_t bn = p.col_bins[i];
+                if (p.scstamp[bn] != p.epoch) continue;
+                uint32_t cnt = p.sccnt[bn], sb = p.bin_sc[bn];
+                for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
+                    uint32_t j = j0 + lane;
+                    uint32_t d = kSent, v = 0;
+                    if (j < cnt) {
+                        uint2 pr = p.scpair[sb + j];
+                        d = pr.x - gt.d0;
+                        v = pr.y;
+                    }
+                    bool mine = (j < cnt) && d >= lo && d < hi;
+                    uint32_t key = mine ? d : (0x80000000u | (uint32_t)lane);
+                    uint32_t peers = __match_any_sync(0xffffffffu, key);
+                    s_stage[wid][lane] = v;
+                    __syncwarp();
+                    if (mine && lane == __ffs(peers) - 1) {
+                        uint32_t r = s_acc[d];
+                        uint32_t m = peers;
+                        while (m) {
+                            int l = __ffs(m) - 1;
+                            m &= m - 1;
+                            r = O::combine(r, s_stage[wid][l]);
+                        }
+                        s_acc[d] = r;
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+        }
+
+        // reInit (init of previously active vertices), gather apply, filter, next frontier
+        uint32_t va = 0;
+        unsigned long long ea = 0;
+        double res = 0.0;
+        for (uint32_t i = threadIdx.x; i < ((width + 31) & ~31u); i += blockDim.x) {
+            const uint32_t g = gq + gt.d0 + i;
+            const bool inrange = i < width && g < p.V;
+            bool act = false;
+            uint32_t deg = 0;
+            if (inrange) {
+                const bool was = (p.bits[g >> 5] >> (g & 31)) & 1u;
+                const uint32_t m = s_acc[i];
+                deg = p.rowptr[g + 1] - p.rowptr[g];
+                uint32_t sv = kNull;
+                if (ALGO == ALG_PR) {
+                    // Alg. 6: initFunc PR = 0 (continue), gatherFunc +=, filterFunc damping
+                    float xo = u2f(p.val[g]);
+                    float xn = fmaf(p.c1, u2f(m), p.c0);
+                    p.val[g] = f2u(xn);
+                    res += fabs((double)xn - (double)xo);
+                    act = true;
+                    sv = f2u(deg ? xn / (float)deg : 0.f);
+                } else if (ALGO == ALG_PPR) {
+                    // initFunc PR = 0, continue iff seed; gatherFunc +=; filterFunc restart, keep iff > 0
+                    float xo = u2f(p.val[g]);
+                    bool cont = was && g == p.source;
+                    bool recv = m != 0u;
+                    float xn = 0.f;
+                    if (cont || recv) xn = fmaf(p.c1, u2f(m), g == p.source ? p.c0 : 0.f);
+                    act = (cont || recv) && xn > 0.f;
+                    if (f2u(xn) != f2u(xo)) p.val[g] = f2u(xn);
+                    res += fabs((double)xn - (double)xo);
+                    if (act) sv = f2u(deg ? xn / (float)deg : 0.f);
+                } else if (ALGO == ALG_BFS) {
+                    // Alg. 5: first discovery sets the parent (smallest candidate) and level
+                    if (m != kInf && p.lvl[g] == kInf) {
+                        p.lvl[g] = p.iter;
+                        p.val[g] = m;
+                        act = true;
+                        sv = g;
+                    }
+                } else {
+                    // Alg. 7 / CC: keep the minimum distance or label, activate on improvement
+                    if (m < p.val[g]) {
+                        p.val[g] = m;
+                        act = true;
+                        sv = m;
+                    }
+                }
+                p.sval[g] = sv;
+            }
+            uint32_t word = __ballot_sync(0xffffffffu, act);
+            if (lane == 0 && (gq + gt.d0 + (i & ~31u)) < p.V) p.bits[(gq + gt.d0 + (i & ~31u)) >> 5] = word;
+            if (act) { va++; ea += deg; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            va += __shfl_xor_sync(0xffffffffu, va, o);
+            ea += __shfl_xor_sync(0xffffffffu, ea, o);
+            res += __shfl_xor_sync(0xffffffffu, res, o);
+        }
+        if (lane == 0) { s_va[wid] = va; s_ea[wid] = ea; s_res[wid] = res; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t a = 0;
+            unsigned long long b2 = 0;
+            double r = 0.0;
+            for (int w = 0; w < kGatherWarps; ++w) { a += s_va[w]; b2 += s_ea[w]; r += s_res[w]; }
+            p.t_va[t] = a;
+            p.t_ea[t] = b2;
+            p.t_res[t] = r;
+            p.t_stamp[t] = p.epoch;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_copy_f32(uint32_t n, const uint32_t *src, uint32_t *dst) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+// --- host side --------------------------------------------------------------------------------
+
+struct RunBuffers {
+    uint32_t *val = nullptr, *lvl = nullptr, *sval = nullptr, *bits = nullptr;
+    uint32_t *t_va = nullptr, *t_stamp = nullptr;
+    unsigned long long *t_ea = nullptr;
+    double *t_res = nullptr;
+    uint8_t *mode = nullptr, *action = nullptr;
+    uint32_t *gflag = nullptr, *gflag_pc = nullptr, *gflag_sc = nullptr, *sc_list = nullptr, *counters = nullptr;
+    Control *ctrl = nullptr, *h_ctrl = nullptr;
+};
+
+static void release_runbufs(RunBuffers *rb) {
+    void *ptrs[] = {rb->val, rb->lvl, rb->sval, rb->bits, rb->t_va, rb->t_stamp, rb->t_ea, rb->t_res,
+                    rb->mode, rb->action, rb->gflag, rb->gflag_pc, rb->gflag_sc, rb->sc_list, rb->counters,
+                    rb->ctrl};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    if (rb->h_ctrl) cudaFreeHost(rb->h_ctrl);
+    delete rb;
+}
+
+static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
+    RunBuffers *rb = new RunBuffers();
+    uint64_t nw = (g->V + 31) / 32 + 1;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto **ptr, uint64_t n) {
+        if (e == cudaSuccess) e = dalloc(g, ptr, n);
+    };
+    A(&rb->val, g->V);
+    A(&rb->lvl, g->V);
+    A(&rb->sval, g->V);
+    A(&rb->bits, nw);
+    A(&rb->t_va, g->ngt);
+    A(&rb->t_stamp, g->ngt);
+    A(&rb->t_ea, g->ngt);
+    A(&rb->t_res, g->ngt);
+    A(&rb->mode, g->k);
+    A(&rb->action, g->k);
+    A(&rb->gflag, g->k);
+    A(&rb->gflag_pc, g->k);
+    A(&rb->gflag_sc, g->k);
+    A(&rb->sc_list, g->k);
+    A(&rb->counters, 8);
+    A(&rb->ctrl, 1);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&rb->h_ctrl, sizeof(Control));
+    if (e == cudaSuccess) e = cudaMemset(rb->t_stamp, 0, 4ull * std::max<uint32_t>(g->ngt, 1));
+    if (e == cudaSuccess) e = cudaMemset(rb->gflag, 0, 4ull * g->k);
+    if (e == cudaSuccess) e = cudaMemset(rb->gflag_pc, 0, 4ull * g->k);
+    if (e == cudaSuccess) e = cudaMemset(rb->gflag_sc, 0, 4ull * g->k);
+    if (e == cudaSuccess) e = cudaMemset(rb->bits, 0, 4ull * nw);
+    if (e != cudaSuccess) {
+        release_runbufs(rb);
+        return fail(e == cudaErrorMemoryAllocation ? GPOP_ERR_OOM : GPOP_ERR_CUDA,
+                    std::string("run buffers: ") + cudaGetErrorString(e));
+    }
+    *out = rb;
+    return GPOP_OK;
+}
+
+void release_run_state(Graph *g) {
+    if (g->run) release_runbufs(static_cast<RunBuffers *>(g->run));
+    g->run = nullptr;
+}
+
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem, int num_sms) {
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+    return std::max(1, per) * num_sms;
+}
+
+template <int ALGO>
+static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cudaStream_t s, void *out_values,
+                            uint32_t *out_parent, int out_is_device, gpop_run_stats *stats) {
+    Params p;
+    memset(&p, 0, sizeof p);
+    p.V = g->V; p.P = g->P; p.shift = g->shift; p.k = g->k;
+    p.rowptr = g->rowptr; p.col = g->col; p.w = g->w; p.ebin = g->ebin;
+    p.row_bin = g->row_bin; p.bin_q = g->bin_q; p.bin_sc = g->bin_sc; p.col_bin = g->col_bin; p.col_bins = g->col_bins;
+    p.png = g->png; p.pdata = g->pdata; p.row_png = g->row_png;
+    p.cptr = g->cptr; p.cidx = g->cidx; p.cdst = g->cdst; p.cw = g->cw;
+    p.scpair = g->scpair; p.sccnt = g->sccnt; p.scstamp = g->scstamp;
+    p.Ep = g->Ep; p.npng_p = g->npng_p;
+    p.gtask = g->gtask; p.ngt = g->ngt; p.col_task = g->col_task;
+    p.stask = g->stask; p.nst = g->nst; p.pc_state = g->pc_state;
+    p.val = rb->val; p.lvl = rb->lvl; p.sval = rb->sval; p.bits = rb->bits;
+    p.t_va = rb->t_va; p.t_ea = rb->t_ea; p.t_res = rb->t_res; p.t_stamp = rb->t_stamp;
+    p.mode = rb->mode; p.action = rb->action; p.gflag = rb->gflag; p.gflag_pc = rb->gflag_pc;
+    p.gflag_sc = rb->gflag_sc; p.sc_list = rb->sc_list; p.counters = rb->counters; p.ctrl = rb->ctrl;
+    p.selector = (o->mode == GPOP_MODE_LEARNED) ? selector_device_params() : nullptr;
+    p.source = o->source; p.max_iters = o->max_iters; p.tol = o->tol_l1;
+    p.algo = ALGO; p.policy = o->mode == GPOP_MODE_LOG_BOTH ? GPOP_MODE_ANALYTIC : o->mode;
+    p.bw_num = o->bw_ratio_num; p.bw_den = o->bw_ratio_den;
+    if (ALGO == ALG_PR) {
+        p.c0 = (float)((1.0 - o->damping) / (double)g->V);
+        p.c1 = (float)o->damping;
+    } else if (ALGO == ALG_PPR) {
+        p.c0 = (float)(1.0 - o->damping);
+        p.c1 = (float)o->damping;
+    }
+
+    int grid_pc = 0, grid_sc = 0, grid_ga = 0;
+    const size_t sc_smem = sizeof(uint32_t) * std::max<uint32_t>(g->max_row_bins, 1);
+    if (sc_smem > 48 * 1024)
+        GPOP_CUDA_TRY(cudaFuncSetAttribute(k_scatter_sc<ALGO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sc_smem));
+    grid_pc = persistent_grid(k_scatter_pc, kScatterThreads, 0, g->num_sms);
+    grid_sc = persistent_grid(k_scatter_sc<ALGO>, kScatterThreads, sc_smem, g->num_sms);
+    grid_ga = persistent_grid(k_gather<ALGO>, kGatherThreads, 0, g->num_sms);
+
+    // initial frontier (Alg. 4 driver: loadFrontier and initial values)
+    p.epoch = ++g->epoch;
+    k_init<ALGO><<<std::max(1, std::min((int)((g->V / 32 + 255) / 256), 4096)), 256, 0, s>>>(p);
+    k_task_stats<<<std::max(1, std::min((int)g->ngt, 8 * g->num_sms)), kGatherThreads, 0, s>>>(p);
+    GPOP_CUDA_TRY(cudaGetLastError());
+
+    cudaEvent_t ev0, ev1;
+    GPOP_CUDA_TRY(cudaEventCreate(&ev0));
+    GPOP_CUDA_TRY(cudaEventCreate(&ev1));
+    gpop_run_stats st;
+    memset(&st, 0, sizeof st);
+    GPOP_CUDA_TRY(cudaEventRecord(ev0, s));
+    // optional per-kernel CUDA-event timing: a start/stop pair per kernel kind, resolved at the
+    // next host synchronisation (which the plan's control read provides every iteration)
+    const bool prof = o->profile_kernels != 0;
+    cudaEvent_t kev[8] = {};
+    bool pend[4] = {false, false, false, false};
+    if (prof)
+        for (auto &ev : kev) GPOP_CUDA_TRY(cudaEventCreate(&ev));
+    auto resolve = [&]() {
+        for (int i = 0; i < 4; ++i)
+            if (pend[i]) {
+                float kms = 0.f;
+                cudaEventElapsedTime(&kms, kev[2 * i], kev[2 * i + 1]);
+                st.kernel_ms[i] += kms;
+                st.kernel_launches[i] += 1;
+                pend[i] = false;
+            }
+    };
+    auto timed = [&](int kind, auto launch) {
+        if (prof) cudaEventRecord(kev[2 * kind], s);
+        launch();
+        if (prof) {
+            cudaEventRecord(kev[2 * kind + 1], s);
+            pend[kind] = true;
+        }
+    };
+    uint32_t iter = 0;
+    gpop_status status = GPOP_OK;
+    for (;;) {
+        p.iter = iter + 1;
+        p.epoch = ++g->epoch;
+        timed(0, [&] { k_plan<<<1, kPlanThreads, 0, s>>>(p); });
+        cudaError_t ce = cudaMemcpyAsync(rb->h_ctrl, rb->ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("plan: ") + cudaGetErrorString(ce)); break; }
+        if (prof) resolve();
+        const Control c = *rb->h_ctrl;
+        st.residual = c.residual;
+        if (c.done) {
+            st.converged = (c.frontier_v == 0) || ((ALGO == ALG_PR || ALGO == ALG_PPR) && iter > 0 && c.residual < o->tol_l1);
+            break;
+        }
+        ++iter;
+        st.edges_scattered += c.frontier_e;
+        st.vertices_scattered += c.frontier_v;
+        st.pc_partition_steps += c.n_pc;
+        st.sc_partition_steps += c.n_sc;
+        st.model_bytes += c.model_bytes;
+        if (o->trace_frontier) {
+            o->trace_frontier[2 * (iter - 1)] = c.frontier_v;
+            o->trace_frontier[2 * (iter - 1) + 1] = c.frontier_e;
+        }
+        if (o->trace_modes) {
+            ce = cudaMemcpyAsync(o->trace_modes + (uint64_t)(iter - 1) * g->k, rb->mode, g->k, cudaMemcpyDeviceToHost, s);
+            if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, cudaGetErrorString(ce)); break; }
+        }
+        if (c.n_pc + c.n_null > 0) timed(1, [&] { k_scatter_pc<<<grid_pc, kScatterThreads, 0, s>>>(p); });
+        if (c.n_sc > 0) timed(2, [&] { k_scatter_sc<ALGO><<<grid_sc, kScatterThreads, sc_smem, s>>>(p); });
+        timed(3, [&] { k_gather<ALGO><<<grid_ga, kGatherThreads, 0, s>>>(p); });
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(ce)); break; }
+    }
+    cudaEventRecord(ev1, s);
+    cudaEventSynchronize(ev1);
+    if (prof) {
+        resolve();
+        for (auto &ev : kev) cudaEventDestroy(ev);
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (status != GPOP_OK) {
+        g->pdata_dirty = true;
+        return status;
+    }
+    st.iterations = iter;
+    st.device_ms = ms;
+
+    // outputs
+    cudaMemcpyKind kind = out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const uint32_t *res_src = (ALGO == ALG_BFS) ? rb->lvl : rb->val;
+    if (out_values) GPOP_CUDA_TRY(cudaMemcpyAsync(out_values, res_src, 4ull * g->V, kind, s));
+    if (ALGO == ALG_BFS && out_parent) GPOP_CUDA_TRY(cudaMemcpyAsync(out_parent, rb->val, 4ull * g->V, kind, s));
+    GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (stats) *stats = st;
+    return GPOP_OK;
+}
+
+}  // namespace gpop
+
+using namespace gpop;
+
+extern "C" void gpop_run_opts_default(gpop_run_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->algo = GPOP_PAGERANK;
+    o->damping = 0.85;
+    o->max_iters = 1000;
+    o->tol_l1 = 0.0;
+    o->mode = GPOP_MODE_ANALYTIC;
+    o->bw_ratio_num = 2;
+    o->bw_ratio_den = 1;
+}
+
+extern "C" gpop_status gpop_run(gpop_graph *h, const gpop_run_opts *o, void *out_values, uint32_t *out_parent,
+                                int out_is_device, gpop_run_stats *stats) {
+    set_error("");
+    if (!h || !o) return fail(GPOP_ERR_INVALID_ARG, "NULL graph or options");
+    Graph *g = &h->g;
+    if (o->algo < GPOP_PAGERANK || o->algo > GPOP_PPR) return fail(GPOP_ERR_INVALID_ARG, "unknown algorithm");
+    if ((o->algo == GPOP_BFS || o->algo == GPOP_SSSP || o->algo == GPOP_PPR) && o->source >= g->V)
+        return fail(GPOP_ERR_INVALID_ARG, "source out of range");
+    if (o->algo == GPOP_SSSP && !g->weighted) return fail(GPOP_ERR_INVALID_ARG, "SSSP needs a weighted graph");
+    if (o->mode < GPOP_MODE_ANALYTIC || o->mode > GPOP_MODE_LOG_BOTH) return fail(GPOP_ERR_INVALID_ARG, "unknown mode policy");
+    if (o->bw_ratio_num == 0 || o->bw_ratio_den == 0) return fail(GPOP_ERR_INVALID_ARG, "bandwidth ratio must be positive");
+    if (o->msg_bf16) return fail(GPOP_ERR_INVALID_ARG, "BF16 messages are not supported");
+    if ((o->algo == GPOP_PAGERANK || o->algo == GPOP_PPR) && !(o->damping > 0.0 && o->damping < 1.0))
+        return fail(GPOP_ERR_INVALID_ARG, "damping must be in (0, 1)");
+    if (o->mode == GPOP_MODE_LEARNED && !selector_device_params())
+        return fail(GPOP_ERR_NO_SELECTOR, "learned mode requested but no selector is installed");
+    cudaStream_t s = (cudaStream_t)o->cuda_stream;
+    if (g->pdata_dirty) {
+        // a failed run may have left PC data rows partially written: restore the all-NULL state
+        GPOP_CUDA_TRY(cudaMemsetAsync(g->pdata, 0xFF, 4ull * std::max<uint64_t>(g->npng_pad, 1), s));
+        GPOP_CUDA_TRY(cudaMemsetAsync(g->pc_state, 0, g->k, s));
+        g->pdata_dirty = false;
+    }
+    RunBuffers *rb = static_cast<RunBuffers *>(g->run);
+    if (!rb) {
+        gpop_status st = alloc_runbufs(g, &rb);
+        if (st != GPOP_OK) return st;
+        g->run = rb;
+    }
+    switch (o->algo) {
+    case GPOP_PAGERANK: return run_algo<ALG_PR>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
+    case GPOP_BFS: return run_algo<ALG_BFS>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
+    case GPOP_CC: return run_algo<ALG_CC>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
+    case GPOP_SSSP: return run_algo<ALG_SSSP>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
+    default: return run_algo<ALG_PPR>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
+    }
+}

@@ -1,0 +1,136 @@
+// Internal declarations of the GB300 GPOP engine (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gpop.h"
+
+namespace gpop {
+
+// Reserved message value: a partition-centric message from an inactive source
+// (and the "no message" state of a vertex).  As FP32 it is a NaN that no
+// arithmetic of the applications produces; as uint32 it is above every vertex
+// ID, distance and label.
+constexpr uint32_t kNull = 0xFFFFFFFFu;
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+
+constexpr int kPngAlign = 8;           // PNG rows padded to 8 entries (16-byte u16 vectors)
+constexpr uint32_t kGatherWidth = 4096;  // max destinations per gather task (smem accumulator)
+constexpr uint32_t kGatherEntries = 32768;  // target in-entries per gather task
+constexpr uint32_t kScatterChunk = 16384;   // PNG entries per static PC scatter task
+constexpr uint32_t kMaxRowBins = 40960;     // SC scatter keeps one cursor per row bin in smem
+
+enum Mode : uint8_t { kModeNone = 0, kModeSC = 1, kModePC = 2 };
+enum Action : uint8_t { kActSkip = 0, kActPC = 1, kActNull = 2 };
+
+// Per-iteration control block written by the plan kernel and read by the host.
+struct Control {
+    unsigned long long frontier_v;   // sum of V_a entering the iteration
+    unsigned long long frontier_e;   // sum of E_a
+    double residual;                 // L1 change of the previous iteration (PR/PPR)
+    double model_bytes;              // Sec. 3.2 bytes of this iteration's chosen modes
+    uint32_t n_pc, n_sc, n_null;     // partitions per action
+    uint32_t done;                   // 1 = stop before scattering this iteration
+    uint32_t n_fallback;             // learned mode: partitions that fell back to Eq. (mode)
+    uint32_t error;                  // device check flags
+    uint32_t pad[2];
+};
+
+// Static gather task: destinations [d0, d1) (local IDs) of column q.
+struct GatherTask {
+    uint32_t q, d0, d1, entries;
+};
+
+// Static PC scatter task: PNG slots [beg, end) of partition p (padded row layout).
+struct ScatterTask {
+    uint32_t p, beg, end, first;  // first = 1 for the chunk that starts the row
+};
+
+struct Graph {
+    uint32_t V = 0, P = 0, shift = 0, k = 0;
+    uint64_t E = 0;
+    int weighted = 0;
+    uint64_t nb = 0, npng = 0, npng_pad = 0;
+    uint32_t max_row_bins = 0;
+
+    // CSR with rows sorted by destination
+    uint32_t *rowptr = nullptr;   // V+1
+    uint32_t *col = nullptr;      // E
+    int32_t *w = nullptr;         // E or null
+    uint16_t *ebin = nullptr;     // E: bin index of the edge within its bin row
+
+    // bins bin[p][q] (non-empty), row-major
+    uint32_t *row_bin = nullptr;  // k+1
+    uint32_t *bin_q = nullptr;    // nb
+    uint32_t *bin_sc = nullptr;   // nb+1: SC capacity offsets (edges per bin)
+    uint32_t *col_bin = nullptr;  // k+1
+    uint32_t *col_bins = nullptr; // nb: bin ids per column, ascending p
+
+    // PNG (Alg. 3) and PC data bins, padded rows
+    uint16_t *png = nullptr;      // npng_pad: local source ID per message slot
+    uint32_t *pdata = nullptr;    // npng_pad: message values
+    uint32_t *row_png = nullptr;  // k+1: padded row offsets
+
+    // destination lists of PC messages, grouped per destination (column CSC)
+    uint32_t *cptr = nullptr;     // V+1
+    uint32_t *cidx = nullptr;     // E: PNG slot of the message that carries the edge
+    uint16_t *cdst = nullptr;     // E: local destination
+    int32_t *cw = nullptr;        // E or null
+
+    // SC bins
+    uint2 *scpair = nullptr;      // E: (local destination, value)
+    uint32_t *sccnt = nullptr;    // nb
+    uint32_t *scstamp = nullptr;  // nb
+
+    // per partition statics
+    uint32_t *Ep = nullptr, *npng_p = nullptr, *nbins_p = nullptr;  // device, k each
+    uint64_t *h_Ep = nullptr, *h_npng = nullptr;                      // host copies
+
+    // tasks
+    uint32_t ngt = 0, nst = 0;
+    GatherTask *gtask = nullptr;  // ngt
+    uint32_t *col_task = nullptr; // k+1
+    ScatterTask *stask = nullptr; // nst
+
+    // persistent run state (allocated lazily, reused across runs)
+    uint8_t *pc_state = nullptr;  // k: row of pdata holds non-NULL values
+    uint32_t epoch = 0;           // iteration stamp, never reused within the handle
+    bool pdata_dirty = false;
+
+    uint64_t device_bytes = 0;
+    int device = 0, num_sms = 0;
+    void *run = nullptr;          // cached per-run buffers (engine.cu)
+};
+
+// error reporting (thread-local last error)
+void set_error(const std::string &msg);
+gpop_status fail(gpop_status st, const std::string &msg);
+
+#define GPOP_CUDA_TRY(expr)                                                                       \
+    do {                                                                                          \
+        cudaError_t _e = (expr);                                                                  \
+        if (_e != cudaSuccess)                                                                    \
+            return ::gpop::fail(GPOP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+// device allocation helper tracked in Graph::device_bytes
+template <typename T>
+cudaError_t dalloc(Graph *g, T **p, uint64_t count) {
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e == cudaSuccess) g->device_bytes += sizeof(T) * count;
+    return e;
+}
+
+void free_graph(Graph *g);
+void release_run_state(Graph *g);   // engine.cu
+const float *selector_device_params();  // selector.cu: installed MLP parameters or null
+
+}  // namespace gpop
+
+struct gpop_graph {
+    gpop::Graph g;
+};

@@ -1,0 +1,196 @@
+"""CUDA path vs the CPU oracle through the C ABI, element by element.
+
+Integer results (BFS levels and parents, SSSP distances, CC labels) must be
+bit-exact; FP32 PageRank / PPR must be within L-inf relative error 1e-5 of the
+FP64 oracle (PPR: relative on the oracle's support, absolute 1e-12 elsewhere).
+Per-iteration modes and frontier sizes must equal the serial GPOP engine's
+(Tier 2) exactly: both evaluate Eq. (mode) in exact integers.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PR_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import paper_1806_08092_gb300 as gp
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gp.build()
+    return gp
+
+
+def G(g, P):
+    import paper_1806_08092_gb300 as gp
+    return gp.Graph.from_csr(g.row_ptr, g.col, g.weights, partition_size=P)
+
+
+def pr_err(x, ref):
+    return float(np.max(np.abs(x.astype(np.float64) - ref) / ref))
+
+
+def u64_to_u32(a):
+    out = a.copy()
+    out[a == O.U64_INF] = O.U32_INF
+    return out.astype(np.uint32)
+
+
+SMALL = [
+    ("ring", gg.ring(100)), ("path", gg.path(70)), ("star", gg.star(200)), ("complete", gg.complete(40)),
+    ("rings", gg.disjoint_rings([33, 1, 64, 7])), ("uniform_ragged", gg.uniform(3001, 20000)),
+    ("sparse_sinks", gg.uniform(2500, 3000)), ("rmat10", gg.rmat(10)), ("rmat13", gg.rmat(13)),
+    ("multi", gg.multigraph(40, list(range(40)) * 3 + [5] * 5, [(3 * i) % 40 for i in range(120)] + [5, 5, 6, 6, 7])),
+]
+POLICIES = ["analytic", "force_sc", "force_pc"]
+
+
+@pytest.mark.parametrize("name,g", SMALL, ids=[s[0] for s in SMALL])
+@pytest.mark.parametrize("P", [32, 256, 4096])
+def test_pagerank_small(name, g, P):
+    ref, _, _ = O.pagerank(g, 0.85, max_iters=15)
+    Gd = G(g, P)
+    for pol in POLICIES:
+        r = Gd.run("pagerank", max_iters=15, mode=pol)
+        assert r.stats["iterations"] == 15
+        assert pr_err(r.values.cpu().numpy(), ref) <= PR_TOL, pol
+
+
+@pytest.mark.parametrize("name,g", SMALL, ids=[s[0] for s in SMALL])
+@pytest.mark.parametrize("P", [32, 1024])
+def test_bfs_sssp_small(name, g, P):
+    gw = g.with_weights()
+    Gd = G(gw, P)
+    for root in gg.roots(g, 3):
+        root = int(root)
+        level, parent = O.bfs(g, root)
+        dist = u64_to_u32(O.sssp(gw, root))
+        for pol in POLICIES:
+            r = Gd.run("bfs", source=root, mode=pol)
+            assert np.array_equal(r.values.cpu().numpy(), level), pol
+            assert np.array_equal(r.parent.cpu().numpy(), parent), pol
+            r = Gd.run("sssp", source=root, mode=pol)
+            assert np.array_equal(r.values.cpu().numpy(), dist), pol
+
+
+@pytest.mark.parametrize("name,g", SMALL, ids=[s[0] for s in SMALL])
+def test_cc_small(name, g):
+    gs = gg.symmetrized(g)
+    label = O.cc(gs)
+    for P in (32, 512):
+        Gd = G(gs, P)
+        for pol in POLICIES:
+            r = Gd.run("cc", mode=pol)
+            assert np.array_equal(r.values.cpu().numpy(), label), (P, pol)
+
+
+@pytest.mark.parametrize("name,g", SMALL[4:], ids=[s[0] for s in SMALL[4:]])
+def test_ppr_small(name, g):
+    Gd = G(g, 64)
+    for s in gg.roots(g, 2):
+        s = int(s)
+        ref, _, _ = O.ppr(g, s, 0.15, max_iters=30)
+        for pol in POLICIES:
+            r = Gd.run("ppr", source=s, damping=0.85, max_iters=30, mode=pol)
+            x = r.values.cpu().numpy().astype(np.float64)
+            sup = ref > 0
+            assert np.all(np.abs(x[sup] - ref[sup]) / ref[sup] <= PR_TOL), pol
+            assert np.all(np.abs(x[~sup]) <= 1e-12), pol
+
+
+@pytest.mark.parametrize("scale,P", [(12, 64), (14, 512), (16, 1024)])
+def test_modes_and_frontiers_match_tier2(scale, P):
+    g = gg.rmat(scale).with_weights()
+    Gd = G(g, P)
+    root = int(gg.roots(g, 1)[0])
+    for algo in ("bfs", "sssp"):
+        t2 = O.gpop(g, P, algo, root)
+        r = Gd.run(algo, source=root, trace=True)
+        assert r.stats["iterations"] == t2.iterations
+        assert np.array_equal(r.modes, t2.modes)
+        assert np.array_equal(r.frontier[:, 0], t2.frontier_vertices)
+        assert np.array_equal(r.frontier[:, 1], t2.frontier_edges)
+        assert r.stats["model_bytes"] == pytest.approx(float(t2.model_bytes.sum()), rel=1e-12)
+    gs = gg.symmetrized(gg.rmat(scale))
+    t2 = O.gpop(gs, P, "cc")
+    r = G(gs, P).run("cc", trace=True)
+    assert r.stats["iterations"] == t2.iterations
+    assert np.array_equal(r.modes, t2.modes)
+
+
+def test_pagerank_rmat16_p1024_10_iterations():
+    # PageRank, 10 iterations, d = 0.85, RMAT scale 16, partitions of 1024 vertices
+    g = gg.rmat(16)
+    ref, _, _ = O.pagerank(g, 0.85, max_iters=10)
+    r = G(g, 1024).run("pagerank", max_iters=10)
+    assert r.stats["iterations"] == 10
+    assert pr_err(r.values.cpu().numpy(), ref) <= PR_TOL
+    assert r.stats["sc_partition_steps"] == 0  # all active: Eq. (mode) always picks PC
+
+
+def test_pagerank_to_residual():
+    g = gg.rmat(14)
+    ref, it, res = O.pagerank(g, 0.85, max_iters=300, tol=1e-9)
+    r = G(g, 1024).run("pagerank", max_iters=300, tol=1e-9)
+    assert r.stats["converged"] == 1 and r.stats["residual"] < 1e-9
+    assert pr_err(r.values.cpu().numpy(), ref) <= PR_TOL
+
+
+def test_layout_partition_stats_match_oracle():
+    for g, P in ((gg.rmat(12), 128), (gg.uniform(5000, 40000), 1024), (gg.star(100), 32)):
+        Ep, npng = O.partition_stats(g, P)
+        Gd = G(g, P)
+        e, n = Gd.partition_stats()
+        assert np.array_equal(e, Ep) and np.array_equal(n, npng)
+        info = Gd.info()
+        assert info["num_png"] == int(npng.sum()) and info["num_edges"] == g.num_edges
+
+
+def test_repeated_runs_and_mode_switches_are_consistent():
+    # PC rows left over from a previous run or iteration must not leak into later gathers
+    g = gg.rmat(13).with_weights()
+    Gd = G(g, 256)
+    roots = gg.roots(g, 4)
+    for i in range(3):
+        for root in roots:
+            root = int(root)
+            for pol in ("force_pc", "analytic", "force_sc"):
+                dist = u64_to_u32(O.sssp(g, root))
+                assert np.array_equal(Gd.run("sssp", source=root, mode=pol).values.cpu().numpy(), dist)
+    x = Gd.run("pagerank", max_iters=5).values.cpu().numpy()
+    assert pr_err(x, O.pagerank(g, 0.85, max_iters=5)[0]) <= PR_TOL
+
+
+def test_host_outputs_and_device_inputs():
+    g = gg.rmat(11)
+    rp = torch.from_numpy(g.row_ptr.view(np.int64)).cuda()
+    col = torch.from_numpy(g.col.view(np.int32)).cuda()
+    import paper_1806_08092_gb300 as gp
+    Gd = gp.Graph.from_csr(rp.view(torch.uint64), col.view(torch.uint32), partition_size=128)
+    root = int(gg.roots(g, 1)[0])
+    r = Gd.run("bfs", source=root, device_out=False)
+    level, parent = O.bfs(g, root)
+    assert np.array_equal(r.values, level) and np.array_equal(r.parent, parent)
+
+
+def test_errors_are_reported():
+    import paper_1806_08092_gb300 as gp
+    g = gg.rmat(8)
+    bad = g.col.copy()
+    bad[3] = g.num_vertices + 5
+    with pytest.raises(gp.GpopError, match="INVALID_ARG"):
+        gp.Graph.from_csr(g.row_ptr, bad, partition_size=32)
+    Gd = G(g, 32)
+    with pytest.raises(gp.GpopError, match="weighted"):
+        Gd.run("sssp", source=0)
+    with pytest.raises(gp.GpopError, match="source"):
+        Gd.run("bfs", source=g.num_vertices)
+    with pytest.raises(gp.GpopError, match="NO_SELECTOR"):
+        gp.selector_set(None)
+        Gd.run("bfs", source=1, mode="learned")
