@@ -86,6 +86,9 @@ typedef struct {
     uint32_t max_row_bins;        /* largest number of bins in one bin row */
     uint32_t reserved;
     uint64_t device_bytes;        /* device memory held by the handle */
+    uint64_t num_heavy_entries;   /* in-entries of destinations reduced in fixed segments */
+    uint32_t num_heavy_vertices;  /* destinations with more than 1024 in-entries */
+    uint32_t num_heavy_segments;
 } gpop_graph_info;
 
 /* Fills *info.  Errors: GPOP_ERR_INVALID_ARG on NULL arguments. */
@@ -149,10 +152,10 @@ typedef struct {
     double model_bytes;           /* sum of Sec. 3.2 bytes of the chosen modes */
     double device_ms;             /* CUDA-event time of the iteration loop */
     uint64_t log_records;         /* LOG_BOTH records written */
-    /* with opts.profile_kernels: per kernel (0 plan, 1 PC scatter, 2 SC scatter, 3 gather)
-       the summed CUDA-event duration and the number of launches */
-    double kernel_ms[4];
-    uint64_t kernel_launches[4];
+    /* with opts.profile_kernels: per kernel (0 plan, 1 PC scatter, 2 SC scatter, 3 gather,
+       4 heavy-destination gather) the summed CUDA-event duration and the number of launches */
+    double kernel_ms[5];
+    uint64_t kernel_launches[5];
 } gpop_run_stats;
 
 /* Fills opts with defaults: PageRank, d = 0.85, max_iters 1000, tol 0,

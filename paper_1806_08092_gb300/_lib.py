@@ -31,7 +31,9 @@ class GraphInfo(ctypes.Structure):
                 ("num_edges", ctypes.c_uint64), ("num_bins", ctypes.c_uint64), ("num_png", ctypes.c_uint64),
                 ("num_png_padded", ctypes.c_uint64), ("num_gather_tasks", ctypes.c_uint32),
                 ("num_scatter_tasks", ctypes.c_uint32), ("max_row_bins", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64)]
+                ("reserved", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64),
+                ("num_heavy_entries", ctypes.c_uint64), ("num_heavy_vertices", ctypes.c_uint32),
+                ("num_heavy_segments", ctypes.c_uint32)]
 
 
 class RunOpts(ctypes.Structure):
@@ -48,7 +50,7 @@ class RunStats(ctypes.Structure):
                 ("edges_scattered", ctypes.c_uint64), ("vertices_scattered", ctypes.c_uint64),
                 ("pc_partition_steps", ctypes.c_uint64), ("sc_partition_steps", ctypes.c_uint64),
                 ("model_bytes", ctypes.c_double), ("device_ms", ctypes.c_double), ("log_records", ctypes.c_uint64),
-                ("kernel_ms", ctypes.c_double * 4), ("kernel_launches", ctypes.c_uint64 * 4)]
+                ("kernel_ms", ctypes.c_double * 5), ("kernel_launches", ctypes.c_uint64 * 5)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

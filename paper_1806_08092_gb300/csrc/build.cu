@@ -27,7 +27,8 @@ void free_graph(Graph *g) {
     void *ptrs[] = {g->rowptr, g->col, g->w, g->ebin, g->row_bin, g->bin_q, g->bin_sc, g->col_bin,
                     g->col_bins, g->png, g->pdata, g->row_png, g->cptr, g->cidx, g->cdst, g->cw,
                     g->scpair, g->sccnt, g->scstamp, g->Ep, g->npng_p, g->nbins_p, g->gtask,
-                    g->col_task, g->stask, g->pc_state};
+                    g->col_task, g->stask, g->pc_state, g->hidx, g->hw, g->hseg, g->hpart, g->task_hptr,
+                    g->task_heavy};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete[] g->h_Ep;
@@ -191,7 +192,18 @@ __global__ void k_unpack_csc(uint64_t E, uint32_t P, const uint64_t *key, uint32
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < E; i += stride) {
         uint64_t x = key[i];
         cidx[i] = (uint32_t)x;
-        cdst[i] = (uint16_t)((x >> 32) & (P - 1));
+        if (cdst) cdst[i] = (uint16_t)((x >> 32) & (P - 1));
+    }
+}
+
+// splits the destination-sorted entries into light and heavy destinations
+__global__ void k_heavy_flags(uint64_t E, const uint64_t *key, const uint32_t *indeg, uint32_t heavy, uint8_t *fl,
+                              uint8_t *fh) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < E; i += stride) {
+        bool h = indeg[(uint32_t)(key[i] >> 32)] > heavy;
+        fl[i] = !h;
+        fh[i] = h;
     }
 }
 
@@ -216,14 +228,6 @@ __global__ void k_part_edges(uint32_t k, uint32_t V, uint32_t shift, const uint3
         uint64_t a = (uint64_t)p << shift, b = (uint64_t)(p + 1) << shift;
         if (b > V) b = V;
         Ep[p] = rowptr[b] - rowptr[a];
-    }
-}
-
-__global__ void k_block_counts(uint32_t V, const uint32_t *cptr, uint32_t *cnt) {
-    uint32_t nblk = (V + 31) / 32;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nblk; i += gridDim.x * blockDim.x) {
-        uint32_t a = i * 32, b = a + 32 < V ? a + 32 : V;
-        cnt[i] = cptr[b] - cptr[a];
     }
 }
 
@@ -426,34 +430,98 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         return cub::DeviceScan::ExclusiveSum(tmp, bytes, edges_bin, g->bin_sc, g->nb + 1, s);
     }));
 
-    // 6. destination lists grouped per destination vertex (column CSC over PNG slots)
+    // 6. destination lists grouped per destination vertex (column CSC over PNG slots).  A destination
+    //    with more than kHeavy in-entries keeps its entries in a separate list cut into segments of at
+    //    most kHeavySeg entries, reduced by their own warps so that no single task serialises a hub.
     GPOP_CUDA_TRY(dalloc(g, &g->cptr, (uint64_t)V + 1));
     GPOP_CUDA_TRY(dalloc(g, &g->cidx, E));
     GPOP_CUDA_TRY(dalloc(g, &g->cdst, E));
     if (g->weighted) GPOP_CUDA_TRY(dalloc(g, &g->cw, E));
+    std::vector<uint32_t> hin(V);
     {
-        uint32_t *indeg;
+        uint32_t *indeg, *light;
         GPOP_CUDA_TRY(t.alloc(&indeg, (uint64_t)V + 1));
+        GPOP_CUDA_TRY(t.alloc(&light, (uint64_t)V + 1));
         GPOP_CUDA_TRY(cudaMemsetAsync(indeg, 0, 4ull * (V + 1), s));
         if (E) k_indegree<<<blocks_for(E), kThreads, 0, s>>>(E, g->col, indeg);
+        GPOP_CUDA_TRY(cudaMemcpyAsync(hin.data(), indeg, 4ull * V, cudaMemcpyDeviceToHost, s));
+        GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+        std::vector<uint32_t> hlight(V + 1, 0);
+        uint64_t nheavy_entries = 0;
+        for (uint32_t v = 0; v < V; ++v) {
+            if (hin[v] > kHeavy) {
+                g->h_hv.push_back(v);
+                nheavy_entries += hin[v];
+            } else {
+                hlight[v] = hin[v];
+            }
+        }
+        GPOP_CUDA_TRY(cudaMemcpyAsync(light, hlight.data(), 4ull * (V + 1), cudaMemcpyHostToDevice, s));
         GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-            return cub::DeviceScan::ExclusiveSum(tmp, bytes, indeg, g->cptr, (uint64_t)V + 1, s);
+            return cub::DeviceScan::ExclusiveSum(tmp, bytes, light, g->cptr, (uint64_t)V + 1, s);
         }));
+        g->nheavy = nheavy_entries;
+        GPOP_CUDA_TRY(dalloc(g, &g->hidx, nheavy_entries));
+        if (g->weighted) GPOP_CUDA_TRY(dalloc(g, &g->hw, nheavy_entries));
         if (E) {
-            uint64_t *ck2;
+            uint64_t *ck2, *ckl, *ckh;
+            int32_t *cw2 = nullptr;
+            uint8_t *fl, *fh;
+            uint32_t *d_cnt;
             GPOP_CUDA_TRY(t.alloc(&ck2, E));
+            GPOP_CUDA_TRY(t.alloc(&ckl, E));
+            GPOP_CUDA_TRY(t.alloc(&ckh, nheavy_entries));
+            GPOP_CUDA_TRY(t.alloc(&fl, E));
+            GPOP_CUDA_TRY(t.alloc(&fh, E));
+            GPOP_CUDA_TRY(t.alloc(&d_cnt, 2));
             int end_bit = 32 + bits_for(V);
             if (g->weighted) {
+                GPOP_CUDA_TRY(t.alloc(&cw2, E));
                 GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-                    return cub::DeviceRadixSort::SortPairs(tmp, bytes, ckey, ck2, g->w, g->cw, E, 0, end_bit, s);
+                    return cub::DeviceRadixSort::SortPairs(tmp, bytes, ckey, ck2, g->w, cw2, E, 0, end_bit, s);
                 }));
             } else {
                 GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
                     return cub::DeviceRadixSort::SortKeys(tmp, bytes, ckey, ck2, E, 0, end_bit, s);
                 }));
             }
-            k_unpack_csc<<<blocks_for(E), kThreads, 0, s>>>(E, P, ck2, g->cidx, g->cdst);
+            k_heavy_flags<<<blocks_for(E), kThreads, 0, s>>>(E, ck2, indeg, kHeavy, fl, fh);
+            GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+                return cub::DeviceSelect::Flagged(tmp, bytes, ck2, fl, ckl, d_cnt, (int64_t)E, s);
+            }));
+            GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+                return cub::DeviceSelect::Flagged(tmp, bytes, ck2, fh, ckh, d_cnt + 1, (int64_t)E, s);
+            }));
+            if (g->weighted) {
+                GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+                    return cub::DeviceSelect::Flagged(tmp, bytes, cw2, fl, g->cw, d_cnt, (int64_t)E, s);
+                }));
+                GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+                    return cub::DeviceSelect::Flagged(tmp, bytes, cw2, fh, g->hw, d_cnt + 1, (int64_t)E, s);
+                }));
+            }
+            uint64_t nlight = E - nheavy_entries;
+            if (nlight) k_unpack_csc<<<blocks_for(nlight), kThreads, 0, s>>>(nlight, P, ckl, g->cidx, g->cdst);
+            if (nheavy_entries)
+                k_unpack_csc<<<blocks_for(nheavy_entries), kThreads, 0, s>>>(nheavy_entries, P, ckh, g->hidx, nullptr);
         }
+        // heavy destinations: contiguous entry ranges in destination order, cut into segments
+        uint64_t off = 0;
+        std::vector<uint4> segs;
+        for (size_t i = 0; i < g->h_hv.size(); ++i) {
+            uint32_t v = g->h_hv[i];
+            g->h_hseg0.push_back((uint32_t)segs.size());
+            for (uint64_t b = 0; b < hin[v]; b += kHeavySeg)
+                segs.push_back(make_uint4(v, (uint32_t)(off + b), (uint32_t)std::min<uint64_t>(off + b + kHeavySeg, off + hin[v]), 0));
+            off += hin[v];
+        }
+        g->h_hseg0.push_back((uint32_t)segs.size());
+        g->nseg = (uint32_t)segs.size();
+        GPOP_CUDA_TRY(dalloc(g, &g->hseg, g->nseg));
+        GPOP_CUDA_TRY(dalloc(g, &g->hpart, g->nseg));
+        if (g->nseg)
+            GPOP_CUDA_TRY(cudaMemcpyAsync(g->hseg, segs.data(), sizeof(uint4) * segs.size(), cudaMemcpyHostToDevice, s));
+        GPOP_CUDA_TRY(cudaStreamSynchronize(s));
     }
 
     // 7. bins per column in ascending source partition
@@ -490,13 +558,9 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
 
     // 9. static gather tasks: destination ranges of <= kGatherWidth vertices, ~kGatherEntries in-entries
     uint32_t nblk = (V + 31) / 32;
-    std::vector<uint32_t> hcnt(nblk);
-    {
-        uint32_t *cnt;
-        GPOP_CUDA_TRY(t.alloc(&cnt, nblk));
-        k_block_counts<<<blocks_for(nblk), kThreads, 0, s>>>(V, g->cptr, cnt);
-        GPOP_CUDA_TRY(cudaMemcpyAsync(hcnt.data(), cnt, 4ull * nblk, cudaMemcpyDeviceToHost, s));
-    }
+    std::vector<uint32_t> hcnt(nblk, 0);  // light in-entries per block of 32 destinations
+    for (uint32_t v = 0; v < V; ++v)
+        if (hin[v] <= kHeavy) hcnt[v / 32] += hin[v];
     GPOP_CUDA_TRY(cudaStreamSynchronize(s));
     g->h_Ep = new uint64_t[k];
     g->h_npng = new uint64_t[k];
@@ -526,6 +590,27 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
     }
     col_task[k] = (uint32_t)gt.size();
     g->ngt = (uint32_t)gt.size();
+    // heavy destinations of every task: (local destination, first segment, segment count)
+    {
+        std::vector<uint32_t> thp(g->ngt + 1, 0);
+        std::vector<uint4> th;
+        size_t hi = 0;
+        for (uint32_t ti = 0; ti < g->ngt; ++ti) {
+            thp[ti] = (uint32_t)th.size();
+            uint64_t lo = ((uint64_t)gt[ti].q << shift) + gt[ti].d0, up = ((uint64_t)gt[ti].q << shift) + gt[ti].d1;
+            while (hi < g->h_hv.size() && g->h_hv[hi] < lo) ++hi;
+            for (size_t j = hi; j < g->h_hv.size() && g->h_hv[j] < up; ++j)
+                th.push_back(make_uint4((uint32_t)(g->h_hv[j] - ((uint64_t)gt[ti].q << shift) - gt[ti].d0),
+                                        g->h_hseg0[j], g->h_hseg0[j + 1] - g->h_hseg0[j], 0));
+        }
+        thp[g->ngt] = (uint32_t)th.size();
+        GPOP_CUDA_TRY(dalloc(g, &g->task_hptr, (uint64_t)g->ngt + 1));
+        GPOP_CUDA_TRY(dalloc(g, &g->task_heavy, th.size()));
+        GPOP_CUDA_TRY(cudaMemcpyAsync(g->task_hptr, thp.data(), 4ull * (g->ngt + 1), cudaMemcpyHostToDevice, s));
+        if (!th.empty())
+            GPOP_CUDA_TRY(cudaMemcpyAsync(g->task_heavy, th.data(), sizeof(uint4) * th.size(), cudaMemcpyHostToDevice, s));
+        GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+    }
     GPOP_CUDA_TRY(dalloc(g, &g->gtask, g->ngt));
     GPOP_CUDA_TRY(dalloc(g, &g->col_task, (uint64_t)k + 1));
     GPOP_CUDA_TRY(cudaMemcpyAsync(g->gtask, gt.data(), sizeof(GatherTask) * gt.size(), cudaMemcpyHostToDevice, s));
@@ -604,6 +689,9 @@ extern "C" gpop_status gpop_graph_get_info(const gpop_graph *h, gpop_graph_info 
     info->num_scatter_tasks = g.nst;
     info->max_row_bins = g.max_row_bins;
     info->device_bytes = g.device_bytes;
+    info->num_heavy_vertices = (uint32_t)g.h_hv.size();
+    info->num_heavy_segments = g.nseg;
+    info->num_heavy_entries = g.nheavy;
     return GPOP_OK;
 }
 

@@ -50,6 +50,14 @@ struct Params {
     const int32_t *cw;
     uint2 *scpair;
     uint32_t *sccnt, *scstamp;
+    uint32_t *col_sc_cnt, *col_sc_list;  // per column: fresh SC bins of this iteration
+    const uint32_t *hidx;
+    const int32_t *hw;
+    const uint4 *hseg;
+    uint32_t *hpart;
+    uint32_t nseg;
+    const uint32_t *task_hptr;
+    const uint4 *task_heavy;
     const uint32_t *Ep, *npng_p;
     const GatherTask *gtask;
     uint32_t ngt;
@@ -67,6 +75,17 @@ struct Params {
     uint32_t *gflag, *gflag_pc, *gflag_sc, *sc_list, *counters;
     Control *ctrl;
     const float *selector;  // learned selector parameters or null
+    // work lists / timing used by the SC scatter and by the LOG_BOTH shadow launches
+    const uint32_t *list;        // partitions for k_scatter_sc
+    const uint32_t *list_count;  // number of entries in list
+    uint32_t counter_slot;       // which counters[] entry the launch consumes
+    uint32_t dry;                // shadow launch: do not publish bins or flags
+    unsigned long long *t_task;  // per-task CTA durations (ns) or null
+    uint32_t *all_list;          // LOG_BOTH: every partition scattered this iteration
+    float *feat;                 // LOG_BOTH: per-partition selector features [k][8]
+    uint32_t *part_va;           // LOG_BOTH: V_a per partition
+    unsigned long long *part_ea; // LOG_BOTH: E_a per partition
+    uint32_t log_both;
     // per launch
     uint32_t epoch, iter, source, max_iters;
     float c0, c1;           // PR: (1-d)/V, d.  PPR: alpha, 1-alpha
@@ -146,6 +165,29 @@ __device__ __forceinline__ double mode_bytes(uint8_t m, uint64_t k, uint64_t Ep,
     if (m == kModePC) return 4.0 * (double)(3 * npng + k + Ep);
     if (m == kModeSC) return 4.0 * ((double)Va + 3.0 * (double)Ea + 2.0 * ((double)npng / (double)Ep) * (double)Ea);
     return 0.0;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Selector features of one partition in one iteration (shared by logging and inference):
+// log1p V_a, log1p E_a, log1p E^p, r^p, log1p(bins in the row), log1p n_png, log1p k,
+// and the log of Eq. (mode)'s cost ratio (PC cost / BW_PC over SC cost / BW_SC).
+__device__ __forceinline__ void partition_features(uint64_t Va, uint64_t Ea, uint64_t Ep, uint64_t np, uint32_t k,
+                                                   uint32_t row_bins, uint32_t num, uint32_t den, float f[8]) {
+    double cpc = 4.0 * (double)(3 * np + k + Ep) * den;
+    double csc = 4.0 * ((double)Va + 3.0 * (double)Ea + 2.0 * ((double)np / (double)Ep) * (double)Ea) * num;
+    f[0] = log1pf((float)Va);
+    f[1] = log1pf((float)Ea);
+    f[2] = log1pf((float)Ep);
+    f[3] = (float)((double)np / (double)Ep);
+    f[4] = log1pf((float)row_bins);
+    f[5] = log1pf((float)np);
+    f[6] = log1pf((float)k);
+    f[7] = (float)log(cpc / csc);
 }
 
 // Learned selector: MLP 8->32->32->1 (ReLU), lane j computes hidden unit j.
@@ -268,12 +310,14 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
     double tr = 0.0, tb = 0.0;
     uint32_t npc = 0, nsc = 0, nnull = 0, nfb = 0, sc_base = 0;
 
+    uint32_t all_base = 0;
     // partitions in chunks of blockDim so the SC list can be compacted in order
     for (uint32_t base = 0; base < p.k; base += blockDim.x) {
         uint32_t q = base + threadIdx.x;
         uint8_t m = kModeNone;
         bool valid = q < p.k;
         uint64_t Va = 0, Ea = 0, Ep = 0, np = 0;
+        float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (valid) {
             double res = 0.0;
             for (uint32_t t = p.col_task[q]; t < p.col_task[q + 1]; ++t)
@@ -285,27 +329,23 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
             else if (p.policy == GPOP_MODE_FORCE_SC) m = kModeSC;
             else if (p.policy == GPOP_MODE_FORCE_PC) m = kModePC;
             else m = analytic_mode(p.k, Ep, np, Va, Ea, p.bw_num, p.bw_den);
+            if (m != kModeNone && (p.log_both || p.selector))
+                partition_features(Va, Ea, Ep, np, p.k, p.row_bin[q + 1] - p.row_bin[q], p.bw_num, p.bw_den, f);
+            if (p.log_both) {
+                for (int i = 0; i < 8; ++i) p.feat[(uint64_t)q * 8 + i] = f[i];
+                p.part_va[q] = (uint32_t)Va;
+                p.part_ea[q] = Ea;
+            }
         }
         if (p.policy == GPOP_MODE_LEARNED && p.selector) {
-            // one warp evaluates the MLP for each of its 32 partitions in turn
+            // one warp evaluates the MLP for each of its 32 partitions in turn (uniform loop)
             for (int j = 0; j < 32; ++j) {
-                uint64_t jVa = __shfl_sync(0xffffffffu, Va, j), jEa = __shfl_sync(0xffffffffu, Ea, j);
-                uint64_t jEp = __shfl_sync(0xffffffffu, Ep, j), jnp = __shfl_sync(0xffffffffu, np, j);
                 uint8_t jm = (uint8_t)__shfl_sync(0xffffffffu, (uint32_t)m, j);
-                uint32_t jq = base + (threadIdx.x & ~31u) + j;
-                if (jm == kModeNone) continue;  // uniform across the warp
-                float f[8];
-                double cpc = 4.0 * (double)(3 * jnp + p.k + jEp) * p.bw_den;
-                double csc = 4.0 * ((double)jVa + 3.0 * (double)jEa + 2.0 * ((double)jnp / (double)jEp) * (double)jEa) * p.bw_num;
-                f[0] = log1pf((float)jVa);
-                f[1] = log1pf((float)jEa);
-                f[2] = log1pf((float)jEp);
-                f[3] = (float)((double)jnp / (double)jEp);
-                f[4] = log1pf((float)(p.row_bin[jq + 1] - p.row_bin[jq]));
-                f[5] = log1pf((float)jnp);
-                f[6] = log1pf((float)p.k);
-                f[7] = (float)log(cpc / csc);
-                uint8_t lm = learned_mode(p.selector, f, lane);
+                float fj[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) fj[i] = __shfl_sync(0xffffffffu, f[i], j);
+                if (jm == kModeNone) continue;
+                uint8_t lm = learned_mode(p.selector, fj, lane);
                 if (lane == j) {
                     if (lm == 0xFF) nfb++;
                     else m = lm;
@@ -314,6 +354,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         }
         if (valid) {
             p.mode[q] = m;
+            p.col_sc_cnt[q] = 0;
             tb += mode_bytes(m, p.k, Ep, np, Va, Ea);
             if (Va > 0) p.gflag[q] = p.epoch;  // active partitions are gathered (reInit of Alg. 2)
             npc += (m == kModePC);
@@ -326,6 +367,11 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         uint32_t off = block_excl_scan((valid && m == kModeSC) ? 1u : 0u, s_warp, &total);
         if (valid && m == kModeSC) p.sc_list[sc_base + off] = q;
         sc_base += total;
+        if (p.log_both) {
+            uint32_t off2 = block_excl_scan((valid && m != kModeNone) ? 1u : 0u, s_warp, &total);
+            if (valid && m != kModeNone) p.all_list[all_base + off2] = q;
+            all_base += total;
+        }
     }
     // deterministic block reductions (fixed tree order)
     for (int o = 16; o > 0; o >>= 1) {
@@ -359,9 +405,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         c.n_pc = c0; c.n_sc = c1; c.n_null = c2; c.done = done; c.n_fallback = c3; c.error = 0;
         c.pad[0] = c.pad[1] = 0;
         *p.ctrl = c;
-        p.counters[0] = 0;
-        p.counters[1] = 0;
-        p.counters[2] = 0;
+        for (int i = 0; i < 8; ++i) p.counters[i] = 0;
+        p.counters[7] = all_base;  // LOG_BOTH: size of all_list
         s_done = done;
     }
     __syncthreads();
@@ -373,16 +418,20 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
 
 __global__ void __launch_bounds__(kScatterThreads) k_scatter_pc(Params p) {
     __shared__ uint32_t s_task;
+    __shared__ unsigned long long s_t0;
     for (;;) {
-        if (threadIdx.x == 0) s_task = atomicAdd(&p.counters[0], 1u);
+        if (threadIdx.x == 0) s_task = atomicAdd(&p.counters[p.counter_slot], 1u);
         __syncthreads();
         uint32_t t = s_task;
         __syncthreads();
         if (t >= p.nst) break;
         ScatterTask st = p.stask[t];
-        uint8_t act = p.action[st.p];
+        // a shadow launch (LOG_BOTH) scatters every partition picked for this iteration into a
+        // private buffer, to time PC mode where Eq. (mode) chose SC
+        uint8_t act = p.dry ? (p.mode[st.p] != kModeNone ? kActPC : kActSkip) : p.action[st.p];
         if (act == kActSkip) continue;
-        if (act == kActPC && st.first) {
+        if (p.t_task && threadIdx.x == 0) s_t0 = globaltimer();
+        if (act == kActPC && st.first && !p.dry) {
             // the partition's messages reach every column of its bin row
             for (uint32_t b = p.row_bin[st.p] + threadIdx.x; b < p.row_bin[st.p + 1]; b += blockDim.x) {
                 uint32_t q = p.bin_q[b];
@@ -411,6 +460,10 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_pc(Params p) {
             dst[0] = o0;
             dst[1] = o1;
         }
+        if (p.t_task) {
+            __syncthreads();
+            if (threadIdx.x == 0) p.t_task[t] = globaltimer() - s_t0;
+        }
     }
 }
 
@@ -423,15 +476,17 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
     __shared__ uint32_t s_pref[1025];       // exclusive prefix of their out-degrees
     __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_task, s_nact;
+    __shared__ unsigned long long s_t0;
     const int lane = threadIdx.x & 31;
-    const uint32_t nsc = p.ctrl->n_sc;
+    const uint32_t nsc = *p.list_count;
     for (;;) {
-        if (threadIdx.x == 0) s_task = atomicAdd(&p.counters[1], 1u);
+        if (threadIdx.x == 0) s_task = atomicAdd(&p.counters[p.counter_slot], 1u);
         __syncthreads();
         uint32_t t = s_task;
         __syncthreads();
         if (t >= nsc) break;
-        const uint32_t part = p.sc_list[t];
+        const uint32_t part = p.list[t];
+        if (p.t_task && threadIdx.x == 0) s_t0 = globaltimer();
         const uint32_t rb0 = p.row_bin[part], nbr = p.row_bin[part + 1] - rb0;
         for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) s_cursor[i] = 0;
         const uint32_t g0 = part << p.shift;
@@ -500,16 +555,20 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
         // publish counts and the 2-level active list entries (gPartList / binPartList via stamps)
         for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) {
             uint32_t c = s_cursor[i];
-            if (c) {
+            if (c && !p.dry) {
                 uint32_t b = rb0 + i;
                 p.sccnt[b] = c;
                 p.scstamp[b] = p.epoch;
                 uint32_t q = p.bin_q[b];
                 p.gflag[q] = p.epoch;
                 p.gflag_sc[q] = p.epoch;
+                // binPartList[q]: append this bin to the column's list of fresh SC bins
+                uint32_t pos = atomicAdd(&p.col_sc_cnt[q], 1u);
+                p.col_sc_list[p.col_bin[q] + pos] = b;
             }
         }
         __syncthreads();
+        if (p.t_task && threadIdx.x == 0) p.t_task[part] = globaltimer() - s_t0;
     }
 }
 
@@ -593,6 +652,43 @@ __device__ __forceinline__ void csc_warp(const Params &p, uint32_t a, uint32_t b
     }
 }
 
+// Heavy destinations (more than kHeavy PC in-entries): one warp reduces one fixed-size segment of a
+// destination's entries; the gather task owning the destination combines the segment results in
+// segment order.  Lane l accumulates entries l, l+32, ... in order and a fixed xor tree combines the
+// lanes, so the result does not depend on scheduling.
+template <int ALGO>
+__global__ void __launch_bounds__(kGatherThreads) k_gather_heavy(Params p) {
+    using O = Op<ALGO>;
+    const int lane = threadIdx.x & 31;
+    const uint32_t wglobal = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t sg = wglobal; sg < p.nseg; sg += nwarps) {
+        const uint4 s = p.hseg[sg];
+        if (p.gflag_pc[s.x >> p.shift] != p.epoch) continue;
+        uint32_t acc = O::identity();
+        constexpr int U = 4;
+        for (uint32_t j0 = s.y; j0 < s.z; j0 += 32 * U) {
+            uint32_t idx[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                uint32_t j = j0 + u * 32 + lane;
+                idx[u] = j < s.z ? p.hidx[j] : kSent;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (idx[u] != kSent) {
+                    uint32_t x = p.pdata[idx[u]];
+                    if (x != kNull)
+                        acc = O::combine(acc, O::weigh(x, (ALGO == ALG_SSSP) ? p.hw[j0 + u * 32 + lane] : 0));
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = O::combine(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+        if (lane == 0) p.hpart[sg] = acc;
+    }
+}
+
 template <int ALGO>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
     using O = Op<ALGO>;
@@ -613,6 +709,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
         const GatherTask gt = p.gtask[t];
         const uint32_t q = gt.q;
         if (p.gflag[q] != p.epoch) continue;
+        unsigned long long t0 = (p.t_task && threadIdx.x == 0) ? globaltimer() : 0ull;
         const uint32_t width = gt.d1 - gt.d0;
         const uint32_t gq = q << p.shift;
         for (uint32_t i = threadIdx.x; i < width; i += blockDim.x) s_acc[i] = O::identity();
@@ -632,16 +729,23 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                     uint2 c = s_carry[w];
                     if (c.x != kSent) s_acc[c.x] = O::combine(s_acc[c.x], c.y);
                 }
+            // heavy destinations of this range: their segment partials, in segment order
+            for (uint32_t h = p.task_hptr[t] + threadIdx.x; h < p.task_hptr[t + 1]; h += blockDim.x) {
+                uint4 hd = p.task_heavy[h];
+                uint32_t r = O::identity();
+                for (uint32_t sgi = 0; sgi < hd.z; ++sgi) r = O::combine(r, p.hpart[hd.y + sgi]);
+                s_acc[hd.x] = r;
+            }
             __syncthreads();
         }
 
-        // SC messages: every warp scans the column's fresh SC bins and applies the
-        // pairs whose destination lies in its own slice of [d0, d1)
+        // SC messages: every warp walks the column's fresh SC bins (binPartList) and applies
+        // the pairs whose destination lies in its own slice of [d0, d1)
         if (p.gflag_sc[q] == p.epoch) {
             const uint32_t lo = (width * wid) / kGatherWarps, hi = (width * (wid + 1)) / kGatherWarps;
-            for (uint32_t i = p.col_bin[q]; i < p.col_bin[q + 1]; ++i) {
-                uint32_t bn = p.col_bins[i];
-                if (p.scstamp[bn] != p.epoch) continue;
+            const uint32_t nfresh = p.col_sc_cnt[q], lbase = p.col_bin[q];
+            for (uint32_t i = 0; i < nfresh; ++i) {
+                uint32_t bn = p.col_sc_list[lbase + i];
                 uint32_t cnt = p.sccnt[bn], sb = p.bin_sc[bn];
                 for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
                     uint32_t j = j0 + lane;
@@ -743,6 +847,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
             p.t_ea[t] = b2;
             p.t_res[t] = r;
             p.t_stamp[t] = p.epoch;
+            if (p.t_task) p.t_task[t] = globaltimer() - t0;
         }
         __syncthreads();
     }
@@ -761,13 +866,19 @@ struct RunBuffers {
     double *t_res = nullptr;
     uint8_t *mode = nullptr, *action = nullptr;
     uint32_t *gflag = nullptr, *gflag_pc = nullptr, *gflag_sc = nullptr, *sc_list = nullptr, *counters = nullptr;
+    uint32_t *col_sc_cnt = nullptr, *col_sc_list = nullptr;
     Control *ctrl = nullptr, *h_ctrl = nullptr;
+    // LOG_BOTH only (allocated on first use)
+    uint32_t *shadow = nullptr, *all_list = nullptr, *part_va = nullptr;
+    unsigned long long *part_ea = nullptr, *t_pc = nullptr, *t_sc = nullptr, *t_ga = nullptr;
+    float *feat = nullptr;
 };
 
 static void release_runbufs(RunBuffers *rb) {
     void *ptrs[] = {rb->val, rb->lvl, rb->sval, rb->bits, rb->t_va, rb->t_stamp, rb->t_ea, rb->t_res,
                     rb->mode, rb->action, rb->gflag, rb->gflag_pc, rb->gflag_sc, rb->sc_list, rb->counters,
-                    rb->ctrl};
+                    rb->ctrl, rb->col_sc_cnt, rb->col_sc_list, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_ga,
+                    rb->feat};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (rb->h_ctrl) cudaFreeHost(rb->h_ctrl);
@@ -796,6 +907,8 @@ static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
     A(&rb->gflag_sc, g->k);
     A(&rb->sc_list, g->k);
     A(&rb->counters, 8);
+    A(&rb->col_sc_cnt, g->k);
+    A(&rb->col_sc_list, g->nb);
     A(&rb->ctrl, 1);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&rb->h_ctrl, sizeof(Control));
     if (e == cudaSuccess) e = cudaMemset(rb->t_stamp, 0, 4ull * std::max<uint32_t>(g->ngt, 1));
@@ -824,6 +937,55 @@ static int persistent_grid(K kernel, int threads, size_t smem, int num_sms) {
     return std::max(1, per) * num_sms;
 }
 
+// LOG_BOTH: turns this iteration's per-task CTA durations into one record per scattered partition:
+// 8 features, t_PC and t_SC in CTA-microseconds (scatter of that mode + that mode's share of the
+// gather, attributed by gather bytes at the iteration's measured gather time per byte), the mode
+// Eq. (mode) chose, the partition and the iteration.
+static gpop_status log_iteration(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cudaStream_t s, uint32_t iter,
+                                 gpop_run_stats *st) {
+    const uint32_t k = g->k;
+    std::vector<float> feat(8ull * k);
+    std::vector<uint32_t> va(k);
+    std::vector<unsigned long long> ea(k), tpc(g->nst), tsc(k), tga(g->ngt);
+    std::vector<uint8_t> mode(k);
+    std::vector<ScatterTask> stask(g->nst);
+    GPOP_CUDA_TRY(cudaMemcpyAsync(feat.data(), rb->feat, 4ull * 8 * k, cudaMemcpyDeviceToHost, s));
+    GPOP_CUDA_TRY(cudaMemcpyAsync(va.data(), rb->part_va, 4ull * k, cudaMemcpyDeviceToHost, s));
+    GPOP_CUDA_TRY(cudaMemcpyAsync(ea.data(), rb->part_ea, 8ull * k, cudaMemcpyDeviceToHost, s));
+    GPOP_CUDA_TRY(cudaMemcpyAsync(mode.data(), rb->mode, k, cudaMemcpyDeviceToHost, s));
+    if (g->nst) {
+        GPOP_CUDA_TRY(cudaMemcpyAsync(tpc.data(), rb->t_pc, 8ull * g->nst, cudaMemcpyDeviceToHost, s));
+        GPOP_CUDA_TRY(cudaMemcpyAsync(stask.data(), g->stask, sizeof(ScatterTask) * g->nst, cudaMemcpyDeviceToHost, s));
+    }
+    GPOP_CUDA_TRY(cudaMemcpyAsync(tsc.data(), rb->t_sc, 8ull * k, cudaMemcpyDeviceToHost, s));
+    GPOP_CUDA_TRY(cudaMemcpyAsync(tga.data(), rb->t_ga, 8ull * g->ngt, cudaMemcpyDeviceToHost, s));
+    GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<double> pc_ns(k, 0.0);
+    for (uint32_t t = 0; t < g->nst; ++t)
+        if (mode[stask[t].p] != kModeNone) pc_ns[stask[t].p] += (double)tpc[t];
+    double ga_ns = 0.0, ga_bytes = 0.0;
+    for (uint32_t t = 0; t < g->ngt; ++t) ga_ns += (double)tga[t];
+    auto gb = [&](uint32_t q, int m) {
+        return m == kModePC ? 4.0 * (double)g->h_npng[q] + 6.0 * (double)g->h_Ep[q] : 8.0 * (double)ea[q];
+    };
+    for (uint32_t q = 0; q < k; ++q)
+        if (mode[q] != kModeNone) ga_bytes += gb(q, mode[q]);
+    const double nspb = ga_bytes > 0 ? ga_ns / ga_bytes : 0.0;
+    for (uint32_t q = 0; q < k; ++q) {
+        if (mode[q] == kModeNone || st->log_records >= o->log_capacity) continue;
+        float *r = o->log_buffer + st->log_records * GPOP_LOG_RECORD_FLOATS;
+        for (int i = 0; i < 8; ++i) r[i] = feat[8ull * q + i];
+        r[8] = (float)((pc_ns[q] + nspb * gb(q, kModePC)) / 1e3);
+        r[9] = (float)(((double)tsc[q] + nspb * gb(q, kModeSC)) / 1e3);
+        r[10] = (float)mode[q];
+        r[11] = (float)q;
+        r[12] = (float)iter;
+        st->log_records++;
+    }
+    (void)va;
+    return GPOP_OK;
+}
+
 template <int ALGO>
 static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cudaStream_t s, void *out_values,
                             uint32_t *out_parent, int out_is_device, gpop_run_stats *stats) {
@@ -835,6 +997,9 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     p.png = g->png; p.pdata = g->pdata; p.row_png = g->row_png;
     p.cptr = g->cptr; p.cidx = g->cidx; p.cdst = g->cdst; p.cw = g->cw;
     p.scpair = g->scpair; p.sccnt = g->sccnt; p.scstamp = g->scstamp;
+    p.col_sc_cnt = rb->col_sc_cnt; p.col_sc_list = rb->col_sc_list;
+    p.hidx = g->hidx; p.hw = g->hw; p.hseg = g->hseg; p.hpart = g->hpart; p.nseg = g->nseg;
+    p.task_hptr = g->task_hptr; p.task_heavy = g->task_heavy;
     p.Ep = g->Ep; p.npng_p = g->npng_p;
     p.gtask = g->gtask; p.ngt = g->ngt; p.col_task = g->col_task;
     p.stask = g->stask; p.nst = g->nst; p.pc_state = g->pc_state;
@@ -843,6 +1008,24 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     p.mode = rb->mode; p.action = rb->action; p.gflag = rb->gflag; p.gflag_pc = rb->gflag_pc;
     p.gflag_sc = rb->gflag_sc; p.sc_list = rb->sc_list; p.counters = rb->counters; p.ctrl = rb->ctrl;
     p.selector = (o->mode == GPOP_MODE_LEARNED) ? selector_device_params() : nullptr;
+    p.list = rb->sc_list; p.list_count = &rb->ctrl->n_sc; p.counter_slot = 0; p.dry = 0; p.t_task = nullptr;
+    p.log_both = o->mode == GPOP_MODE_LOG_BOTH && o->log_buffer && o->log_capacity;
+    if (p.log_both && !rb->shadow) {
+        cudaError_t ae = cudaSuccess;
+        auto A = [&](auto **ptr, uint64_t n) {
+            if (ae == cudaSuccess) ae = dalloc(g, ptr, n);
+        };
+        A(&rb->shadow, g->npng_pad);
+        A(&rb->all_list, g->k);
+        A(&rb->part_va, g->k);
+        A(&rb->part_ea, g->k);
+        A(&rb->t_pc, g->nst);
+        A(&rb->t_sc, g->k);
+        A(&rb->t_ga, g->ngt);
+        A(&rb->feat, 8ull * g->k);
+        if (ae != cudaSuccess) return fail(GPOP_ERR_OOM, std::string("LOG_BOTH buffers: ") + cudaGetErrorString(ae));
+    }
+    p.all_list = rb->all_list; p.feat = rb->feat; p.part_va = rb->part_va; p.part_ea = rb->part_ea;
     p.source = o->source; p.max_iters = o->max_iters; p.tol = o->tol_l1;
     p.algo = ALGO; p.policy = o->mode == GPOP_MODE_LOG_BOTH ? GPOP_MODE_ANALYTIC : o->mode;
     p.bw_num = o->bw_ratio_num; p.bw_den = o->bw_ratio_den;
@@ -862,6 +1045,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     grid_pc = persistent_grid(k_scatter_pc, kScatterThreads, 0, g->num_sms);
     grid_sc = persistent_grid(k_scatter_sc<ALGO>, kScatterThreads, sc_smem, g->num_sms);
     grid_ga = persistent_grid(k_gather<ALGO>, kGatherThreads, 0, g->num_sms);
+    const int grid_gh = persistent_grid(k_gather_heavy<ALGO>, kGatherThreads, 0, g->num_sms);
 
     // initial frontier (Alg. 4 driver: loadFrontier and initial values)
     p.epoch = ++g->epoch;
@@ -878,12 +1062,12 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     // optional per-kernel CUDA-event timing: a start/stop pair per kernel kind, resolved at the
     // next host synchronisation (which the plan's control read provides every iteration)
     const bool prof = o->profile_kernels != 0;
-    cudaEvent_t kev[8] = {};
-    bool pend[4] = {false, false, false, false};
+    cudaEvent_t kev[10] = {};
+    bool pend[5] = {false, false, false, false, false};
     if (prof)
         for (auto &ev : kev) GPOP_CUDA_TRY(cudaEventCreate(&ev));
     auto resolve = [&]() {
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 5; ++i)
             if (pend[i]) {
                 float kms = 0.f;
                 cudaEventElapsedTime(&kms, kev[2 * i], kev[2 * i + 1]);
@@ -930,11 +1114,32 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
             ce = cudaMemcpyAsync(o->trace_modes + (uint64_t)(iter - 1) * g->k, rb->mode, g->k, cudaMemcpyDeviceToHost, s);
             if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, cudaGetErrorString(ce)); break; }
         }
+        if (p.log_both) {
+            // time both modes for every partition picked this iteration (shadow launches first:
+            // the real SC scatter below rewrites the same bins with the same pairs)
+            cudaMemsetAsync(rb->t_ga, 0, 8ull * g->ngt, s);
+            Params q1 = p;
+            q1.pdata = rb->shadow; q1.dry = 1; q1.counter_slot = 3; q1.t_task = rb->t_pc;
+            k_scatter_pc<<<grid_pc, kScatterThreads, 0, s>>>(q1);
+            Params q2 = p;
+            q2.dry = 1; q2.counter_slot = 4; q2.list = rb->all_list; q2.list_count = &rb->counters[7];
+            q2.t_task = rb->t_sc;
+            k_scatter_sc<ALGO><<<grid_sc, kScatterThreads, sc_smem, s>>>(q2);
+        }
+        Params ps = p;
+        ps.counter_slot = 1;
+        Params pg = p;
+        pg.t_task = p.log_both ? rb->t_ga : nullptr;
         if (c.n_pc + c.n_null > 0) timed(1, [&] { k_scatter_pc<<<grid_pc, kScatterThreads, 0, s>>>(p); });
-        if (c.n_sc > 0) timed(2, [&] { k_scatter_sc<ALGO><<<grid_sc, kScatterThreads, sc_smem, s>>>(p); });
-        timed(3, [&] { k_gather<ALGO><<<grid_ga, kGatherThreads, 0, s>>>(p); });
+        if (c.n_sc > 0) timed(2, [&] { k_scatter_sc<ALGO><<<grid_sc, kScatterThreads, sc_smem, s>>>(ps); });
+        if (c.n_pc > 0 && g->nseg > 0) timed(4, [&] { k_gather_heavy<ALGO><<<grid_gh, kGatherThreads, 0, s>>>(p); });
+        timed(3, [&] { k_gather<ALGO><<<grid_ga, kGatherThreads, 0, s>>>(pg); });
         ce = cudaGetLastError();
         if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(ce)); break; }
+        if (p.log_both) {
+            status = log_iteration(g, rb, o, s, iter, &st);
+            if (status != GPOP_OK) break;
+        }
     }
     cudaEventRecord(ev1, s);
     cudaEventSynchronize(ev1);

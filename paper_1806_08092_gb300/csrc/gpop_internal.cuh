@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/gpop.h"
 
@@ -22,6 +23,8 @@ constexpr uint32_t kGatherWidth = 4096;  // max destinations per gather task (sm
 constexpr uint32_t kGatherEntries = 32768;  // target in-entries per gather task
 constexpr uint32_t kScatterChunk = 16384;   // PNG entries per static PC scatter task
 constexpr uint32_t kMaxRowBins = 40960;     // SC scatter keeps one cursor per row bin in smem
+constexpr uint32_t kHeavy = 1024;           // destinations with more in-entries are reduced in segments
+constexpr uint32_t kHeavySeg = 2048;        // in-entries per heavy segment (one warp each)
 
 enum Mode : uint8_t { kModeNone = 0, kModeSC = 1, kModePC = 2 };
 enum Action : uint8_t { kActSkip = 0, kActPC = 1, kActNull = 2 };
@@ -79,6 +82,18 @@ struct Graph {
     uint32_t *cidx = nullptr;     // E: PNG slot of the message that carries the edge
     uint16_t *cdst = nullptr;     // E: local destination
     int32_t *cw = nullptr;        // E or null
+
+    // heavy destinations (more than kHeavy in-entries): entries in destination order, cut into
+    // segments (destination, begin, end) whose partial results the owning gather task merges
+    uint32_t *hidx = nullptr;     // heavy entries: PNG slot
+    int32_t *hw = nullptr;        // heavy entries: weight or null
+    uint4 *hseg = nullptr;        // nseg segments
+    uint32_t *hpart = nullptr;    // nseg partial results
+    uint32_t nseg = 0;
+    uint64_t nheavy = 0;          // heavy in-entries
+    uint32_t *task_hptr = nullptr;  // ngt+1 offsets into task_heavy
+    uint4 *task_heavy = nullptr;    // (local destination, first segment, segment count)
+    std::vector<uint32_t> h_hv, h_hseg0;  // host: heavy destinations and their first segment
 
     // SC bins
     uint2 *scpair = nullptr;      // E: (local destination, value)
