@@ -267,13 +267,13 @@ def run_ours(a, rank, world, local_rank):
     el = E - eh
     # Algorithmic bytes per launch of an all-PC PageRank iteration (every vertex active):
     #  PC scatter: PNG source IDs (2 B) + message values (4 B) per padded slot, one message value per vertex;
-    #  gather (light destinations): PNG slot (4 B) + local destination (2 B) per entry, column offsets,
-    #    per vertex rank read + write, next message value, two row offsets, frontier bits, and the message
-    #    values (4 B per PNG entry) in proportion to the entries it reads;
+    #  gather (light destinations): PNG slot (4 B) per entry, column offsets, per vertex rank read +
+    #    write, next message value, two row offsets, frontier bits, and the message values (4 B per PNG
+    #    entry) in proportion to the entries it reads;
     #  heavy-destination gather: PNG slot (4 B) per entry plus its share of the message values.
     per_kernel_bytes = {
         1: 6 * npad + 4 * V,
-        3: 6 * el + 4 * (V + 1) + 16 * V + V // 4 + 4 * npng * el / max(E, 1),
+        3: 4 * el + 4 * (V + 1) + 16 * V + V // 4 + 4 * npng * el / max(E, 1),
         4: 4 * eh + 4 * npng * eh / max(E, 1),
     }
     names = {1: "k_scatter_pc", 3: "k_gather", 4: "k_gather_heavy"}

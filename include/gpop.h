@@ -87,7 +87,7 @@ typedef struct {
     uint32_t reserved;
     uint64_t device_bytes;        /* device memory held by the handle */
     uint64_t num_heavy_entries;   /* in-entries of destinations reduced in fixed segments */
-    uint32_t num_heavy_vertices;  /* destinations with more than 1024 in-entries */
+    uint32_t num_heavy_vertices;  /* destinations with more than 256 in-entries */
     uint32_t num_heavy_segments;
 } gpop_graph_info;
 

@@ -24,9 +24,10 @@ gpop_status fail(gpop_status st, const std::string &msg) {
 
 void free_graph(Graph *g) {
     release_run_state(g);
-    void *ptrs[] = {g->rowptr, g->col, g->w, g->ebin, g->row_bin, g->bin_q, g->bin_sc, g->col_bin,
-                    g->col_bins, g->png, g->pdata, g->row_png, g->cptr, g->cidx, g->cdst, g->cw,
-                    g->scpair, g->sccnt, g->scstamp, g->Ep, g->npng_p, g->nbins_p, g->gtask,
+    void *ptrs[] = {g->rowptr, g->col, g->w, g->esub, g->row_bin, g->bin_q, g->col_bin,
+                    g->col_bins, g->png, g->pdata, g->row_png, g->cptr, g->cidx, g->cw,
+                    g->scpair, g->sccnt, g->sub_cap, g->sub_task, g->row_sub, g->task_sub_ptr,
+                    g->Ep, g->npng_p, g->nbins_p, g->gtask,
                     g->col_task, g->stask, g->pc_state, g->hidx, g->hw, g->hseg, g->hpart, g->task_hptr,
                     g->task_heavy};
     for (void *p : ptrs)
@@ -165,19 +166,44 @@ __global__ void k_place_msgs(uint64_t nmsg, uint32_t shift, uint32_t k, const ui
 }
 
 // every edge inherits the slot and bin of its message head
-__global__ void k_edge_msg(uint64_t E, uint32_t shift, const uint32_t *src, const uint32_t *head_of,
-                           const uint32_t *slot_of_head, const uint32_t *bin_of_head, const uint32_t *row_bin,
-                           const uint32_t *col, uint32_t *slot_e, uint32_t *bin_e, uint16_t *ebin,
-                           uint32_t *edges_per_bin, uint64_t *ckey) {
+__global__ void k_edge_msg(uint64_t E, const uint32_t *head_of, const uint32_t *slot_of_head, const uint32_t *col,
+                           uint64_t *ckey) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E; e += stride)
+        ckey[e] = ((uint64_t)col[e] << 32) | slot_of_head[head_of[e]];  // destination-major column lists
+}
+
+// SC bins are (source partition p, gather task t) pairs: key (p << 32) | t per edge
+__global__ void k_sub_keys(uint64_t E, uint32_t shift, const uint32_t *src, const uint32_t *col,
+                           const uint32_t *task_of, uint64_t *key) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E; e += stride)
+        key[e] = ((uint64_t)(src[e] >> shift) << 32) | task_of[col[e]];
+}
+
+__global__ void k_sub_split(uint64_t nsub, const uint64_t *ukey, uint32_t *sub_task, uint32_t *row_hist,
+                            uint32_t *task_hist) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < nsub; s += stride) {
+        uint32_t tsk = (uint32_t)ukey[s];
+        sub_task[s] = tsk;
+        atomicAdd(&row_hist[(uint32_t)(ukey[s] >> 32)], 1u);
+        atomicAdd(&task_hist[tsk], 1u);
+    }
+}
+
+// index of every edge's SC bin within its bin row (binary search of its task in the row)
+__global__ void k_edge_sub(uint64_t E, uint32_t shift, const uint32_t *src, const uint32_t *col,
+                           const uint32_t *task_of, const uint32_t *row_sub, const uint32_t *sub_task, uint16_t *esub) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E; e += stride) {
-        uint32_t h = head_of[e];
-        uint32_t slot = slot_of_head[h], b = bin_of_head[h];
-        slot_e[e] = slot;
-        bin_e[e] = b;
-        ebin[e] = (uint16_t)(b - row_bin[src[e] >> shift]);
-        atomicAdd(&edges_per_bin[b], 1u);
-        ckey[e] = ((uint64_t)col[e] << 32) | slot;  // destination-major order for the column lists
+        uint32_t p = src[e] >> shift, tsk = task_of[col[e]];
+        uint32_t lo = row_sub[p], hi = row_sub[p + 1];  // sub_task[lo..hi) ascending, contains tsk
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (sub_task[mid] <= tsk) lo = mid; else hi = mid;
+        }
+        esub[e] = (uint16_t)(lo - row_sub[p]);
     }
 }
 
@@ -408,34 +434,23 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         k_place_msgs<<<blocks_for(nmsg), kThreads, 0, s>>>(nmsg, shift, k, skey, shead, binscan, row_msg, g->row_png,
                                                            g->png, slot_of_head, bin_of_head, g->bin_q);
 
-    // 5. per-edge message slot and bin; SC capacities; keys of the column lists
-    GPOP_CUDA_TRY(dalloc(g, &g->ebin, E));
-    GPOP_CUDA_TRY(dalloc(g, &g->bin_sc, g->nb + 1));
-    uint32_t *head_of, *slot_e, *bin_e, *edges_bin;
+    // 5. per-edge message slot (keys of the column lists)
+    uint32_t *head_of;
     uint64_t *ckey;
     GPOP_CUDA_TRY(t.alloc(&head_of, E));
-    GPOP_CUDA_TRY(t.alloc(&slot_e, E));
-    GPOP_CUDA_TRY(t.alloc(&bin_e, E));
-    GPOP_CUDA_TRY(t.alloc(&edges_bin, g->nb + 1));
     GPOP_CUDA_TRY(t.alloc(&ckey, E));
-    GPOP_CUDA_TRY(cudaMemsetAsync(edges_bin, 0, 4ull * (g->nb + 1), s));
     if (E) {
         GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
             return cub::DeviceScan::InclusiveScan(tmp, bytes, head_idx, head_of, MaxOp(), E, s);
         }));
-        k_edge_msg<<<blocks_for(E), kThreads, 0, s>>>(E, shift, src, head_of, slot_of_head, bin_of_head, g->row_bin,
-                                                      g->col, slot_e, bin_e, g->ebin, edges_bin, ckey);
+        k_edge_msg<<<blocks_for(E), kThreads, 0, s>>>(E, head_of, slot_of_head, g->col, ckey);
     }
-    GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-        return cub::DeviceScan::ExclusiveSum(tmp, bytes, edges_bin, g->bin_sc, g->nb + 1, s);
-    }));
 
     // 6. destination lists grouped per destination vertex (column CSC over PNG slots).  A destination
     //    with more than kHeavy in-entries keeps its entries in a separate list cut into segments of at
     //    most kHeavySeg entries, reduced by their own warps so that no single task serialises a hub.
     GPOP_CUDA_TRY(dalloc(g, &g->cptr, (uint64_t)V + 1));
     GPOP_CUDA_TRY(dalloc(g, &g->cidx, E));
-    GPOP_CUDA_TRY(dalloc(g, &g->cdst, E));
     if (g->weighted) GPOP_CUDA_TRY(dalloc(g, &g->cw, E));
     std::vector<uint32_t> hin(V);
     {
@@ -501,7 +516,7 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
                 }));
             }
             uint64_t nlight = E - nheavy_entries;
-            if (nlight) k_unpack_csc<<<blocks_for(nlight), kThreads, 0, s>>>(nlight, P, ckl, g->cidx, g->cdst);
+            if (nlight) k_unpack_csc<<<blocks_for(nlight), kThreads, 0, s>>>(nlight, P, ckl, g->cidx, nullptr);
             if (nheavy_entries)
                 k_unpack_csc<<<blocks_for(nheavy_entries), kThreads, 0, s>>>(nheavy_entries, P, ckh, g->hidx, nullptr);
         }
@@ -626,11 +641,72 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
     if (g->nst)
         GPOP_CUDA_TRY(cudaMemcpyAsync(g->stask, st.data(), sizeof(ScatterTask) * st.size(), cudaMemcpyHostToDevice, s));
 
-    // 11. SC bins and persistent state
+    // 11. SC bins at gather-task granularity: bin (p, t) receives the SC pairs from partition p to the
+    //     destinations of gather task t (capacity = edges p -> t), so each gather task reads only its own
+    {
+        std::vector<uint32_t> task_of(V);
+        for (uint32_t ti = 0; ti < g->ngt; ++ti) {
+            uint64_t lo = ((uint64_t)gt[ti].q << shift) + gt[ti].d0;
+            uint64_t hi = std::min<uint64_t>(((uint64_t)gt[ti].q << shift) + gt[ti].d1, V);
+            for (uint64_t v = lo; v < hi; ++v) task_of[v] = ti;
+        }
+        uint32_t *d_task_of, *row_hist, *task_hist, *d_nsub;
+        uint64_t *skey, *skey2, *ukey;
+        uint32_t *counts;
+        GPOP_CUDA_TRY(t.alloc(&d_task_of, V));
+        GPOP_CUDA_TRY(t.alloc(&row_hist, (uint64_t)k + 1));
+        GPOP_CUDA_TRY(t.alloc(&task_hist, (uint64_t)g->ngt + 1));
+        GPOP_CUDA_TRY(t.alloc(&d_nsub, 1));
+        GPOP_CUDA_TRY(t.alloc(&skey, E));
+        GPOP_CUDA_TRY(t.alloc(&skey2, E));
+        GPOP_CUDA_TRY(t.alloc(&ukey, E));
+        GPOP_CUDA_TRY(t.alloc(&counts, E + 1));
+        GPOP_CUDA_TRY(cudaMemcpyAsync(d_task_of, task_of.data(), 4ull * V, cudaMemcpyHostToDevice, s));
+        GPOP_CUDA_TRY(cudaMemsetAsync(row_hist, 0, 4ull * (k + 1), s));
+        GPOP_CUDA_TRY(cudaMemsetAsync(task_hist, 0, 4ull * (g->ngt + 1), s));
+        GPOP_CUDA_TRY(cudaMemsetAsync(d_nsub, 0, 4, s));
+        uint32_t nsub = 0;
+        if (E) {
+            k_sub_keys<<<blocks_for(E), kThreads, 0, s>>>(E, shift, src, g->col, d_task_of, skey);
+            GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+                return cub::DeviceRadixSort::SortKeys(tmp, bytes, skey, skey2, E, 0, 32 + bits_for(k), s);
+            }));
+            GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+                return cub::DeviceRunLengthEncode::Encode(tmp, bytes, skey2, ukey, counts, d_nsub, (int64_t)E, s);
+            }));
+            GPOP_CUDA_TRY(cudaMemcpyAsync(&nsub, d_nsub, 4, cudaMemcpyDeviceToHost, s));
+            GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        g->nsub = nsub;
+        GPOP_CUDA_TRY(dalloc(g, &g->sub_cap, (uint64_t)nsub + 1));
+        GPOP_CUDA_TRY(dalloc(g, &g->sub_task, nsub));
+        GPOP_CUDA_TRY(dalloc(g, &g->row_sub, (uint64_t)k + 1));
+        GPOP_CUDA_TRY(dalloc(g, &g->task_sub_ptr, (uint64_t)g->ngt + 1));
+        GPOP_CUDA_TRY(dalloc(g, &g->esub, E));
+        GPOP_CUDA_TRY(cudaMemsetAsync(counts + nsub, 0, 4, s));
+        GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+            return cub::DeviceScan::ExclusiveSum(tmp, bytes, counts, g->sub_cap, (uint64_t)nsub + 1, s);
+        }));
+        if (nsub) k_sub_split<<<blocks_for(nsub), kThreads, 0, s>>>(nsub, ukey, g->sub_task, row_hist, task_hist);
+        GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+            return cub::DeviceScan::ExclusiveSum(tmp, bytes, row_hist, g->row_sub, (uint64_t)k + 1, s);
+        }));
+        GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+            return cub::DeviceScan::ExclusiveSum(tmp, bytes, task_hist, g->task_sub_ptr, (uint64_t)g->ngt + 1, s);
+        }));
+        std::vector<uint32_t> hrow(k);
+        GPOP_CUDA_TRY(cudaMemcpyAsync(hrow.data(), row_hist, 4ull * k, cudaMemcpyDeviceToHost, s));
+        GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+        g->max_row_subs = 0;
+        for (uint32_t p = 0; p < k; ++p) g->max_row_subs = std::max(g->max_row_subs, hrow[p]);
+        if (g->max_row_subs > kMaxRowBins)
+            return fail(GPOP_ERR_INVALID_ARG, "a partition sends SC messages to more gather tasks than the SC "
+                                              "scatter supports; use a larger partition size");
+        if (E) k_edge_sub<<<blocks_for(E), kThreads, 0, s>>>(E, shift, src, g->col, d_task_of, g->row_sub,
+                                                             g->sub_task, g->esub);
+    }
     GPOP_CUDA_TRY(dalloc(g, &g->scpair, E));
-    GPOP_CUDA_TRY(dalloc(g, &g->sccnt, g->nb));
-    GPOP_CUDA_TRY(dalloc(g, &g->scstamp, g->nb));
-    GPOP_CUDA_TRY(cudaMemsetAsync(g->scstamp, 0, 4ull * std::max<uint64_t>(g->nb, 1), s));
+    GPOP_CUDA_TRY(dalloc(g, &g->sccnt, g->nsub));
     GPOP_CUDA_TRY(dalloc(g, &g->pc_state, k));
     GPOP_CUDA_TRY(cudaMemsetAsync(g->pc_state, 0, k, s));
     GPOP_CUDA_TRY(cudaStreamSynchronize(s));

@@ -34,23 +34,24 @@ constexpr int kGatherWarps = kGatherThreads / 32;
 constexpr int kScatterThreads = 256;
 constexpr int kPlanThreads = 1024;
 constexpr uint32_t kSent = 0xFFFFFFFFu;
+constexpr int kTile = 2048;  // PC entries staged in shared memory per gather round
 
 struct Params {
     // graph
     uint32_t V, P, shift, k;
     const uint32_t *rowptr, *col;
     const int32_t *w;
-    const uint16_t *ebin;
-    const uint32_t *row_bin, *bin_q, *bin_sc, *col_bin, *col_bins;
+    const uint16_t *esub;
+    const uint32_t *row_bin, *bin_q, *col_bin, *col_bins;
+    const uint32_t *sub_cap, *sub_task, *row_sub, *task_sub_ptr;
     const uint16_t *png;
     uint32_t *pdata;
     const uint32_t *row_png;
     const uint32_t *cptr, *cidx;
-    const uint16_t *cdst;
     const int32_t *cw;
     uint2 *scpair;
-    uint32_t *sccnt, *scstamp;
-    uint32_t *col_sc_cnt, *col_sc_list;  // per column: fresh SC bins of this iteration
+    uint32_t *sccnt;
+    uint32_t *task_sc_cnt, *task_sc_list;  // per gather task: fresh SC bins of this iteration
     const uint32_t *hidx;
     const int32_t *hw;
     const uint4 *hseg;
@@ -72,7 +73,7 @@ struct Params {
     double *t_res;
     uint32_t *t_stamp;
     uint8_t *mode, *action;
-    uint32_t *gflag, *gflag_pc, *gflag_sc, *sc_list, *counters;
+    uint32_t *gflag, *gflag_pc, *sc_list, *counters;
     Control *ctrl;
     const float *selector;  // learned selector parameters or null
     // work lists / timing used by the SC scatter and by the LOG_BOTH shadow launches
@@ -354,7 +355,6 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         }
         if (valid) {
             p.mode[q] = m;
-            p.col_sc_cnt[q] = 0;
             tb += mode_bytes(m, p.k, Ep, np, Va, Ea);
             if (Va > 0) p.gflag[q] = p.epoch;  // active partitions are gathered (reInit of Alg. 2)
             npc += (m == kModePC);
@@ -410,8 +410,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         s_done = done;
     }
     __syncthreads();
-    if (!s_done)  // commit the PC-state of each data row only if this iteration runs
+    if (!s_done) {  // commit the PC-state of each data row only if this iteration runs
         for (uint32_t q = threadIdx.x; q < p.k; q += blockDim.x) p.pc_state[q] = p.mode[q] == kModePC;
+        for (uint32_t t = threadIdx.x; t < p.ngt; t += blockDim.x) p.task_sc_cnt[t] = 0;
+    }
 }
 
 // --- PC scatter (Alg. 3) -----------------------------------------------------------------------
@@ -487,7 +489,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
         if (t >= nsc) break;
         const uint32_t part = p.list[t];
         if (p.t_task && threadIdx.x == 0) s_t0 = globaltimer();
-        const uint32_t rb0 = p.row_bin[part], nbr = p.row_bin[part + 1] - rb0;
+        const uint32_t rb0 = p.row_sub[part], nbr = p.row_sub[part + 1] - rb0;
         for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) s_cursor[i] = 0;
         const uint32_t g0 = part << p.shift;
         const uint32_t gend = min(g0 + p.P, p.V);
@@ -533,7 +535,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
                     uint32_t u = s_list[lo];
                     uint32_t edge = p.rowptr[u] + (e - s_pref[lo]);
                     uint32_t dst = p.col[edge];
-                    lb = p.ebin[edge];
+                    lb = p.esub[edge];
                     dloc = dst & (p.P - 1);
                     val = p.sval[u];
                     if (ALGO == ALG_SSSP) val = Op<ALGO>::weigh(val, p.w[edge]);
@@ -546,25 +548,23 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
                 if (live && lane == leader) basepos = atomicAdd(&s_cursor[lb], (uint32_t)__popc(peers));
                 basepos = __shfl_sync(0xffffffffu, basepos, leader);
                 if (live) {
-                    slot = p.bin_sc[rb0 + lb] + basepos + rank;
+                    slot = p.sub_cap[rb0 + lb] + basepos + rank;
                     p.scpair[slot] = make_uint2(dloc, val);
                 }
             }
             __syncthreads();
         }
-        // publish counts and the 2-level active list entries (gPartList / binPartList via stamps)
+        // publish counts and the 2-level active list (gPartList = gflag, binPartList = the gather
+        // task's list of fresh SC bins)
         for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) {
             uint32_t c = s_cursor[i];
             if (c && !p.dry) {
                 uint32_t b = rb0 + i;
                 p.sccnt[b] = c;
-                p.scstamp[b] = p.epoch;
-                uint32_t q = p.bin_q[b];
-                p.gflag[q] = p.epoch;
-                p.gflag_sc[q] = p.epoch;
-                // binPartList[q]: append this bin to the column's list of fresh SC bins
-                uint32_t pos = atomicAdd(&p.col_sc_cnt[q], 1u);
-                p.col_sc_list[p.col_bin[q] + pos] = b;
+                uint32_t tsk = p.sub_task[b];
+                p.gflag[p.gtask[tsk].q] = p.epoch;
+                uint32_t pos = atomicAdd(&p.task_sc_cnt[tsk], 1u);
+                p.task_sc_list[p.task_sub_ptr[tsk] + pos] = b;
             }
         }
         __syncthreads();
@@ -573,84 +573,6 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
 }
 
 // --- gather + filter ---------------------------------------------------------------------------
-
-// Segmented reduction of the destination-sorted PC lists [a, b) by one warp.
-// Every segment (one destination) except the warp's first is complete inside
-// this warp and written straight to acc; the first may continue a segment of
-// the previous warp and goes to the carry slot, merged in warp order later.
-template <int ALGO>
-__device__ __forceinline__ void csc_warp(const Params &p, uint32_t a, uint32_t b, uint32_t d0, uint32_t *acc,
-                                         uint2 *carry, int lane) {
-    using O = Op<ALGO>;
-    uint32_t cur_d = kSent, cur_v = O::identity();
-    bool have_cur = false, cur_first = false, first_chunk = true;
-    constexpr int U = 4;
-    for (uint32_t base = a; base < b; base += 32 * U) {
-        uint32_t dd[U], vv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            uint32_t j = base + u * 32 + lane;
-            dd[u] = kSent;
-            vv[u] = kNull;
-            if (j < b) {
-                dd[u] = (uint32_t)p.cdst[j] - d0;
-                vv[u] = p.cidx[j];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            uint32_t j = base + u * 32 + lane;
-            if (j < b) {
-                uint32_t x = p.pdata[vv[u]];
-                vv[u] = (x == kNull) ? O::identity()
-                                     : O::weigh(x, (ALGO == ALG_SSSP) ? p.cw[j] : 0);
-            } else {
-                vv[u] = O::identity();
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            uint32_t cbase = base + u * 32;
-            if (cbase >= b) break;
-            uint32_t d = dd[u], v = vv[u];
-            uint32_t d_lane0 = __shfl_sync(0xffffffffu, d, 0);
-            if (have_cur && cur_d != d_lane0) {
-                if (lane == 0) {
-                    if (cur_first) *carry = make_uint2(cur_d, cur_v);
-                    else acc[cur_d] = cur_v;
-                }
-                have_cur = false;
-            }
-            bool lane0_first = have_cur ? cur_first : first_chunk;
-            if (lane == 0 && have_cur) v = O::combine(cur_v, v);
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t vu = __shfl_up_sync(0xffffffffu, v, o);
-                uint32_t du = __shfl_up_sync(0xffffffffu, d, o);
-                if (lane >= o && du == d) v = O::combine(vu, v);
-            }
-            uint32_t d_next = __shfl_down_sync(0xffffffffu, d, 1);
-            uint32_t nvalid = min(32u, b - cbase);
-            int last = (int)nvalid - 1;
-            bool valid = lane < (int)nvalid;
-            bool tail = valid && (lane == last || d_next != d);
-            bool seg_first = (d == d_lane0) && lane0_first;
-            if (tail && lane != last) {
-                if (seg_first) *carry = make_uint2(d, v);
-                else acc[d] = v;
-            }
-            cur_d = __shfl_sync(0xffffffffu, d, last);
-            cur_v = __shfl_sync(0xffffffffu, v, last);
-            cur_first = __shfl_sync(0xffffffffu, (int)seg_first, last);
-            have_cur = true;
-            first_chunk = false;
-        }
-    }
-    if (have_cur && lane == 0) {
-        if (cur_first) *carry = make_uint2(cur_d, cur_v);
-        else acc[cur_d] = cur_v;
-    }
-}
 
 // Heavy destinations (more than kHeavy PC in-entries): one warp reduces one fixed-size segment of a
 // destination's entries; the gather task owning the destination combines the segment results in
@@ -689,19 +611,39 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_heavy(Params p) {
     }
 }
 
+// largest r in [0, n] with ptr[r] <= x (ptr non-decreasing, ptr[0] <= x)
+__device__ __forceinline__ uint32_t row_of(const uint32_t *ptr, uint32_t n, uint32_t x) {
+    uint32_t lo = 0, hi = n + 1;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (ptr[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Gather of one (column q, destination range) task:
+//  1. PC messages of light destinations, round by round: kTile entries of the destination-sorted
+//     lists are staged in shared memory (coalesced slot loads, independent message-value loads), then
+//     every thread folds the staged values of the destinations it owns (destination r belongs to
+//     thread r mod blockDim for the whole task, so no two threads ever touch the same accumulator);
+//  2. heavy destinations take their segment partials, in segment order;
+//  3. SC pairs of the fresh SC bins of the column, each warp applying those of its destination slice;
+//  4. reInit / gather apply / filter of every destination of the range and the next frontier (Alg. 2).
 template <int ALGO>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
     using O = Op<ALGO>;
     __shared__ uint32_t s_acc[kGatherWidth];
-    __shared__ uint2 s_carry[kGatherWarps];
+    __shared__ uint32_t s_ptr[kGatherWidth + 1];
+    __shared__ uint32_t s_val[kTile];
     __shared__ uint32_t s_stage[kGatherWarps][32];
     __shared__ uint32_t s_task;
     __shared__ uint32_t s_va[kGatherWarps];
     __shared__ unsigned long long s_ea[kGatherWarps];
     __shared__ double s_res[kGatherWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     for (;;) {
-        if (threadIdx.x == 0) s_task = atomicAdd(&p.counters[2], 1u);
+        if (tid == 0) s_task = atomicAdd(&p.counters[2], 1u);
         __syncthreads();
         const uint32_t t = s_task;
         __syncthreads();
@@ -709,44 +651,67 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
         const GatherTask gt = p.gtask[t];
         const uint32_t q = gt.q;
         if (p.gflag[q] != p.epoch) continue;
-        unsigned long long t0 = (p.t_task && threadIdx.x == 0) ? globaltimer() : 0ull;
+        unsigned long long t0 = (p.t_task && tid == 0) ? globaltimer() : 0ull;
         const uint32_t width = gt.d1 - gt.d0;
         const uint32_t gq = q << p.shift;
-        for (uint32_t i = threadIdx.x; i < width; i += blockDim.x) s_acc[i] = O::identity();
-        if (threadIdx.x < kGatherWarps) s_carry[threadIdx.x] = make_uint2(kSent, 0);
-        __syncthreads();
+        const uint32_t gbase = gq + gt.d0;
+        const uint32_t wv = min(width, p.V - gbase);  // destinations that exist
+        for (uint32_t i = tid; i < width; i += nthr) s_acc[i] = O::identity();
 
-        // PC messages: destination-sorted lists of this range, split evenly over the warps
         if (p.gflag_pc[q] == p.epoch) {
-            uint32_t e0 = p.cptr[gq + gt.d0], e1 = p.cptr[min(gq + gt.d1, p.V)];
-            uint32_t n = e1 - e0;
-            uint32_t a = e0 + (uint32_t)(((uint64_t)n * wid) / kGatherWarps);
-            uint32_t b = e0 + (uint32_t)(((uint64_t)n * (wid + 1)) / kGatherWarps);
-            csc_warp<ALGO>(p, a, b, gt.d0, s_acc, &s_carry[wid], lane);
+            for (uint32_t i = tid; i <= wv; i += nthr) s_ptr[i] = p.cptr[gbase + i];
             __syncthreads();
-            if (threadIdx.x == 0)
-                for (int w = 0; w < kGatherWarps; ++w) {
-                    uint2 c = s_carry[w];
-                    if (c.x != kSent) s_acc[c.x] = O::combine(s_acc[c.x], c.y);
+            const uint32_t e0 = s_ptr[0], n = s_ptr[wv] - e0;
+            for (uint32_t tb = 0; tb < n; tb += kTile) {
+                const uint32_t tn = min((uint32_t)kTile, n - tb);
+                constexpr int U = kTile / kGatherThreads;
+                uint32_t idx[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    uint32_t j = tid + u * kGatherThreads;
+                    idx[u] = j < tn ? p.cidx[e0 + tb + j] : kSent;
                 }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    uint32_t j = tid + u * kGatherThreads;
+                    if (idx[u] != kSent) {
+                        uint32_t x = p.pdata[idx[u]];
+                        s_val[j] = (x == kNull) ? O::identity()
+                                                : O::weigh(x, (ALGO == ALG_SSSP) ? p.cw[e0 + tb + j] : 0);
+                    }
+                }
+                __syncthreads();
+                // rows meeting [tb, tb + tn): the row holding entry tb up to the row holding tb + tn - 1
+                const uint32_t r_lo = row_of(s_ptr, wv, e0 + tb), r_hi = row_of(s_ptr, wv, e0 + tb + tn - 1);
+                for (uint32_t r = r_lo + ((tid + nthr - (r_lo % nthr)) % nthr); r <= r_hi; r += nthr) {
+                    uint32_t a = max(s_ptr[r], e0 + tb), b = min(s_ptr[r + 1], e0 + tb + tn);
+                    if (a < b) {
+                        uint32_t acc = s_acc[r];
+                        for (uint32_t j = a; j < b; ++j) acc = O::combine(acc, s_val[j - e0 - tb]);
+                        s_acc[r] = acc;
+                    }
+                }
+                __syncthreads();
+            }
             // heavy destinations of this range: their segment partials, in segment order
-            for (uint32_t h = p.task_hptr[t] + threadIdx.x; h < p.task_hptr[t + 1]; h += blockDim.x) {
+            for (uint32_t h = p.task_hptr[t] + tid; h < p.task_hptr[t + 1]; h += nthr) {
                 uint4 hd = p.task_heavy[h];
                 uint32_t r = O::identity();
                 for (uint32_t sgi = 0; sgi < hd.z; ++sgi) r = O::combine(r, p.hpart[hd.y + sgi]);
                 s_acc[hd.x] = r;
             }
-            __syncthreads();
         }
+        __syncthreads();
 
-        // SC messages: every warp walks the column's fresh SC bins (binPartList) and applies
+        // SC messages: every warp walks this task's fresh SC bins (binPartList) and applies
         // the pairs whose destination lies in its own slice of [d0, d1)
-        if (p.gflag_sc[q] == p.epoch) {
+        const uint32_t nfresh = p.task_sc_cnt[t];
+        if (nfresh) {
             const uint32_t lo = (width * wid) / kGatherWarps, hi = (width * (wid + 1)) / kGatherWarps;
-            const uint32_t nfresh = p.col_sc_cnt[q], lbase = p.col_bin[q];
+            const uint32_t lbase = p.task_sub_ptr[t];
             for (uint32_t i = 0; i < nfresh; ++i) {
-                uint32_t bn = p.col_sc_list[lbase + i];
-                uint32_t cnt = p.sccnt[bn], sb = p.bin_sc[bn];
+                uint32_t bn = p.task_sc_list[lbase + i];
+                uint32_t cnt = p.sccnt[bn], sb = p.sub_cap[bn];
                 for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
                     uint32_t j = j0 + lane;
                     uint32_t d = kSent, v = 0;
@@ -776,60 +741,116 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
             __syncthreads();
         }
 
-        // reInit (init of previously active vertices), gather apply, filter, next frontier
+        // reInit (init of previously active vertices), gather apply, filter, next frontier.
+        // Each thread takes 4 consecutive destinations (16-byte vector accesses); 8 threads form
+        // one 32-bit frontier word.
         uint32_t va = 0;
         unsigned long long ea = 0;
         double res = 0.0;
-        for (uint32_t i = threadIdx.x; i < ((width + 31) & ~31u); i += blockDim.x) {
-            const uint32_t g = gq + gt.d0 + i;
-            const bool inrange = i < width && g < p.V;
-            bool act = false;
-            uint32_t deg = 0;
-            if (inrange) {
-                const bool was = (p.bits[g >> 5] >> (g & 31)) & 1u;
-                const uint32_t m = s_acc[i];
-                deg = p.rowptr[g + 1] - p.rowptr[g];
-                uint32_t sv = kNull;
-                if (ALGO == ALG_PR) {
-                    // Alg. 6: initFunc PR = 0 (continue), gatherFunc +=, filterFunc damping
-                    float xo = u2f(p.val[g]);
-                    float xn = fmaf(p.c1, u2f(m), p.c0);
-                    p.val[g] = f2u(xn);
-                    res += fabs((double)xn - (double)xo);
-                    act = true;
-                    sv = f2u(deg ? xn / (float)deg : 0.f);
-                } else if (ALGO == ALG_PPR) {
-                    // initFunc PR = 0, continue iff seed; gatherFunc +=; filterFunc restart, keep iff > 0
-                    float xo = u2f(p.val[g]);
-                    bool cont = was && g == p.source;
-                    bool recv = m != 0u;
-                    float xn = 0.f;
-                    if (cont || recv) xn = fmaf(p.c1, u2f(m), g == p.source ? p.c0 : 0.f);
-                    act = (cont || recv) && xn > 0.f;
-                    if (f2u(xn) != f2u(xo)) p.val[g] = f2u(xn);
-                    res += fabs((double)xn - (double)xo);
-                    if (act) sv = f2u(deg ? xn / (float)deg : 0.f);
-                } else if (ALGO == ALG_BFS) {
-                    // Alg. 5: first discovery sets the parent (smallest candidate) and level
-                    if (m != kInf && p.lvl[g] == kInf) {
-                        p.lvl[g] = p.iter;
-                        p.val[g] = m;
-                        act = true;
-                        sv = g;
-                    }
-                } else {
-                    // Alg. 7 / CC: keep the minimum distance or label, activate on improvement
-                    if (m < p.val[g]) {
-                        p.val[g] = m;
-                        act = true;
-                        sv = m;
+        const uint32_t wround = (width + 31) & ~31u;
+        // the bound is tested on the warp's first destination so that every lane of a warp runs the
+        // same iterations (the word assembly below uses full-warp shuffles)
+        for (uint32_t i0 = tid * 4; i0 - (uint32_t)lane * 4 < wround; i0 += nthr * 4) {
+            const uint32_t g0 = gbase + i0;
+            const bool any = i0 < wv;
+            uint32_t nib = 0;
+            uint32_t was_word = any ? p.bits[g0 >> 5] : 0u;
+            if (any) {
+                const bool full = i0 + 4 <= wv;
+                uint4 rp = full ? *reinterpret_cast<const uint4 *>(p.rowptr + g0) : make_uint4(0, 0, 0, 0);
+                uint32_t rp4 = p.rowptr[min(g0 + 4, p.V)];
+                uint32_t rpv[5] = {rp.x, rp.y, rp.z, rp.w, rp4};
+                if (!full)
+                    for (int c = 0; c < 4; ++c) rpv[c] = (i0 + c < wv) ? p.rowptr[g0 + c] : rp4;
+                uint4 vv = full ? *reinterpret_cast<const uint4 *>(p.val + g0) : make_uint4(0, 0, 0, 0);
+                uint32_t vals[4] = {vv.x, vv.y, vv.z, vv.w};
+                uint32_t lv[4] = {kInf, kInf, kInf, kInf};
+                if (!full)
+                    for (int c = 0; c < 4; ++c) vals[c] = (i0 + c < wv) ? p.val[g0 + c] : 0u;
+                if (ALGO == ALG_BFS) {
+                    if (full) {
+                        uint4 l4 = *reinterpret_cast<const uint4 *>(p.lvl + g0);
+                        lv[0] = l4.x; lv[1] = l4.y; lv[2] = l4.z; lv[3] = l4.w;
+                    } else {
+                        for (int c = 0; c < 4; ++c) lv[c] = (i0 + c < wv) ? p.lvl[g0 + c] : 0u;
                     }
                 }
-                p.sval[g] = sv;
+                uint32_t nv[4], ns[4];
+                bool wrote_lv = false;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const uint32_t g = g0 + c;
+                    nv[c] = vals[c];
+                    ns[c] = kNull;
+                    if (i0 + c >= wv) continue;
+                    const bool was = (was_word >> (g & 31)) & 1u;
+                    const uint32_t m = s_acc[i0 + c];
+                    const uint32_t deg = rpv[c + 1] - rpv[c];
+                    bool act = false;
+                    if (ALGO == ALG_PR) {
+                        // Alg. 6: initFunc PR = 0 (continue), gatherFunc +=, filterFunc damping
+                        float xo = u2f(vals[c]);
+                        float xn = fmaf(p.c1, u2f(m), p.c0);
+                        nv[c] = f2u(xn);
+                        res += fabs((double)xn - (double)xo);
+                        act = true;
+                        ns[c] = f2u(deg ? xn / (float)deg : 0.f);
+                    } else if (ALGO == ALG_PPR) {
+                        // initFunc PR = 0, continue iff seed; gatherFunc +=; filterFunc restart, keep iff > 0
+                        float xo = u2f(vals[c]);
+                        bool cont = was && g == p.source;
+                        bool recv = m != 0u;
+                        float xn = 0.f;
+                        if (cont || recv) xn = fmaf(p.c1, u2f(m), g == p.source ? p.c0 : 0.f);
+                        act = (cont || recv) && xn > 0.f;
+                        nv[c] = f2u(xn);
+                        res += fabs((double)xn - (double)xo);
+                        if (act) ns[c] = f2u(deg ? xn / (float)deg : 0.f);
+                    } else if (ALGO == ALG_BFS) {
+                        // Alg. 5: first discovery sets the parent (smallest candidate) and level
+                        if (m != kInf && lv[c] == kInf) {
+                            lv[c] = p.iter;
+                            wrote_lv = true;
+                            nv[c] = m;
+                            act = true;
+                            ns[c] = g;
+                        }
+                    } else {
+                        // Alg. 7 / CC: keep the minimum distance or label, activate on improvement
+                        if (m < vals[c]) {
+                            nv[c] = m;
+                            act = true;
+                            ns[c] = m;
+                        }
+                    }
+                    if (act) {
+                        nib |= 1u << c;
+                        va++;
+                        ea += deg;
+                    }
+                }
+                if (full) {
+                    if (nv[0] != vals[0] || nv[1] != vals[1] || nv[2] != vals[2] || nv[3] != vals[3])
+                        *reinterpret_cast<uint4 *>(p.val + g0) = make_uint4(nv[0], nv[1], nv[2], nv[3]);
+                    *reinterpret_cast<uint4 *>(p.sval + g0) = make_uint4(ns[0], ns[1], ns[2], ns[3]);
+                    if (ALGO == ALG_BFS && wrote_lv)
+                        *reinterpret_cast<uint4 *>(p.lvl + g0) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                } else {
+                    for (int c = 0; c < 4; ++c)
+                        if (i0 + c < wv) {
+                            if (nv[c] != vals[c]) p.val[g0 + c] = nv[c];
+                            p.sval[g0 + c] = ns[c];
+                            if (ALGO == ALG_BFS) p.lvl[g0 + c] = lv[c];
+                        }
+                }
             }
-            uint32_t word = __ballot_sync(0xffffffffu, act);
-            if (lane == 0 && (gq + gt.d0 + (i & ~31u)) < p.V) p.bits[(gq + gt.d0 + (i & ~31u)) >> 5] = word;
-            if (act) { va++; ea += deg; }
+            // 8 consecutive threads own one frontier word
+            uint32_t word = nib << (i0 & 31);
+            word |= __shfl_xor_sync(0xffffffffu, word, 1);
+            word |= __shfl_xor_sync(0xffffffffu, word, 2);
+            word |= __shfl_xor_sync(0xffffffffu, word, 4);
+            if ((lane & 7) == 0 && i0 < wround && (gbase + (i0 & ~31u)) < p.V)
+                p.bits[(gbase + (i0 & ~31u)) >> 5] = word;
         }
         for (int o = 16; o > 0; o >>= 1) {
             va += __shfl_xor_sync(0xffffffffu, va, o);
@@ -838,7 +859,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
         }
         if (lane == 0) { s_va[wid] = va; s_ea[wid] = ea; s_res[wid] = res; }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             uint32_t a = 0;
             unsigned long long b2 = 0;
             double r = 0.0;
@@ -853,10 +874,6 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
     }
 }
 
-__global__ void k_copy_f32(uint32_t n, const uint32_t *src, uint32_t *dst) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
-}
-
 // --- host side --------------------------------------------------------------------------------
 
 struct RunBuffers {
@@ -865,8 +882,8 @@ struct RunBuffers {
     unsigned long long *t_ea = nullptr;
     double *t_res = nullptr;
     uint8_t *mode = nullptr, *action = nullptr;
-    uint32_t *gflag = nullptr, *gflag_pc = nullptr, *gflag_sc = nullptr, *sc_list = nullptr, *counters = nullptr;
-    uint32_t *col_sc_cnt = nullptr, *col_sc_list = nullptr;
+    uint32_t *gflag = nullptr, *gflag_pc = nullptr, *sc_list = nullptr, *counters = nullptr;
+    uint32_t *task_sc_cnt = nullptr, *task_sc_list = nullptr;
     Control *ctrl = nullptr, *h_ctrl = nullptr;
     // LOG_BOTH only (allocated on first use)
     uint32_t *shadow = nullptr, *all_list = nullptr, *part_va = nullptr;
@@ -876,8 +893,8 @@ struct RunBuffers {
 
 static void release_runbufs(RunBuffers *rb) {
     void *ptrs[] = {rb->val, rb->lvl, rb->sval, rb->bits, rb->t_va, rb->t_stamp, rb->t_ea, rb->t_res,
-                    rb->mode, rb->action, rb->gflag, rb->gflag_pc, rb->gflag_sc, rb->sc_list, rb->counters,
-                    rb->ctrl, rb->col_sc_cnt, rb->col_sc_list, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_ga,
+                    rb->mode, rb->action, rb->gflag, rb->gflag_pc, rb->sc_list, rb->counters,
+                    rb->ctrl, rb->task_sc_cnt, rb->task_sc_list, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_ga,
                     rb->feat};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -904,17 +921,16 @@ static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
     A(&rb->action, g->k);
     A(&rb->gflag, g->k);
     A(&rb->gflag_pc, g->k);
-    A(&rb->gflag_sc, g->k);
     A(&rb->sc_list, g->k);
     A(&rb->counters, 8);
-    A(&rb->col_sc_cnt, g->k);
-    A(&rb->col_sc_list, g->nb);
+    A(&rb->task_sc_cnt, g->ngt);
+    A(&rb->task_sc_list, g->nsub);
     A(&rb->ctrl, 1);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&rb->h_ctrl, sizeof(Control));
     if (e == cudaSuccess) e = cudaMemset(rb->t_stamp, 0, 4ull * std::max<uint32_t>(g->ngt, 1));
     if (e == cudaSuccess) e = cudaMemset(rb->gflag, 0, 4ull * g->k);
     if (e == cudaSuccess) e = cudaMemset(rb->gflag_pc, 0, 4ull * g->k);
-    if (e == cudaSuccess) e = cudaMemset(rb->gflag_sc, 0, 4ull * g->k);
+    if (e == cudaSuccess) e = cudaMemset(rb->task_sc_cnt, 0, 4ull * std::max<uint32_t>(g->ngt, 1));
     if (e == cudaSuccess) e = cudaMemset(rb->bits, 0, 4ull * nw);
     if (e != cudaSuccess) {
         release_runbufs(rb);
@@ -992,12 +1008,13 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     Params p;
     memset(&p, 0, sizeof p);
     p.V = g->V; p.P = g->P; p.shift = g->shift; p.k = g->k;
-    p.rowptr = g->rowptr; p.col = g->col; p.w = g->w; p.ebin = g->ebin;
-    p.row_bin = g->row_bin; p.bin_q = g->bin_q; p.bin_sc = g->bin_sc; p.col_bin = g->col_bin; p.col_bins = g->col_bins;
+    p.rowptr = g->rowptr; p.col = g->col; p.w = g->w; p.esub = g->esub;
+    p.row_bin = g->row_bin; p.bin_q = g->bin_q; p.col_bin = g->col_bin; p.col_bins = g->col_bins;
     p.png = g->png; p.pdata = g->pdata; p.row_png = g->row_png;
-    p.cptr = g->cptr; p.cidx = g->cidx; p.cdst = g->cdst; p.cw = g->cw;
-    p.scpair = g->scpair; p.sccnt = g->sccnt; p.scstamp = g->scstamp;
-    p.col_sc_cnt = rb->col_sc_cnt; p.col_sc_list = rb->col_sc_list;
+    p.cptr = g->cptr; p.cidx = g->cidx; p.cw = g->cw;
+    p.scpair = g->scpair; p.sccnt = g->sccnt;
+    p.sub_cap = g->sub_cap; p.sub_task = g->sub_task; p.row_sub = g->row_sub; p.task_sub_ptr = g->task_sub_ptr;
+    p.task_sc_cnt = rb->task_sc_cnt; p.task_sc_list = rb->task_sc_list;
     p.hidx = g->hidx; p.hw = g->hw; p.hseg = g->hseg; p.hpart = g->hpart; p.nseg = g->nseg;
     p.task_hptr = g->task_hptr; p.task_heavy = g->task_heavy;
     p.Ep = g->Ep; p.npng_p = g->npng_p;
@@ -1006,7 +1023,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     p.val = rb->val; p.lvl = rb->lvl; p.sval = rb->sval; p.bits = rb->bits;
     p.t_va = rb->t_va; p.t_ea = rb->t_ea; p.t_res = rb->t_res; p.t_stamp = rb->t_stamp;
     p.mode = rb->mode; p.action = rb->action; p.gflag = rb->gflag; p.gflag_pc = rb->gflag_pc;
-    p.gflag_sc = rb->gflag_sc; p.sc_list = rb->sc_list; p.counters = rb->counters; p.ctrl = rb->ctrl;
+    p.sc_list = rb->sc_list; p.counters = rb->counters; p.ctrl = rb->ctrl;
     p.selector = (o->mode == GPOP_MODE_LEARNED) ? selector_device_params() : nullptr;
     p.list = rb->sc_list; p.list_count = &rb->ctrl->n_sc; p.counter_slot = 0; p.dry = 0; p.t_task = nullptr;
     p.log_both = o->mode == GPOP_MODE_LOG_BOTH && o->log_buffer && o->log_capacity;
@@ -1038,7 +1055,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     }
 
     int grid_pc = 0, grid_sc = 0, grid_ga = 0;
-    const size_t sc_smem = sizeof(uint32_t) * std::max<uint32_t>(g->max_row_bins, 1);
+    const size_t sc_smem = sizeof(uint32_t) * std::max<uint32_t>(g->max_row_subs, 1);
     if (sc_smem > 48 * 1024)
         GPOP_CUDA_TRY(cudaFuncSetAttribute(k_scatter_sc<ALGO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sc_smem));

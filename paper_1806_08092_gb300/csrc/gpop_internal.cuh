@@ -23,7 +23,7 @@ constexpr uint32_t kGatherWidth = 4096;  // max destinations per gather task (sm
 constexpr uint32_t kGatherEntries = 32768;  // target in-entries per gather task
 constexpr uint32_t kScatterChunk = 16384;   // PNG entries per static PC scatter task
 constexpr uint32_t kMaxRowBins = 40960;     // SC scatter keeps one cursor per row bin in smem
-constexpr uint32_t kHeavy = 1024;           // destinations with more in-entries are reduced in segments
+constexpr uint32_t kHeavy = 256;            // destinations with more in-entries are reduced in segments
 constexpr uint32_t kHeavySeg = 2048;        // in-entries per heavy segment (one warp each)
 
 enum Mode : uint8_t { kModeNone = 0, kModeSC = 1, kModePC = 2 };
@@ -63,12 +63,11 @@ struct Graph {
     uint32_t *rowptr = nullptr;   // V+1
     uint32_t *col = nullptr;      // E
     int32_t *w = nullptr;         // E or null
-    uint16_t *ebin = nullptr;     // E: bin index of the edge within its bin row
+    uint16_t *esub = nullptr;     // E: index of the edge's SC bin within its bin row
 
     // bins bin[p][q] (non-empty), row-major
     uint32_t *row_bin = nullptr;  // k+1
     uint32_t *bin_q = nullptr;    // nb
-    uint32_t *bin_sc = nullptr;   // nb+1: SC capacity offsets (edges per bin)
     uint32_t *col_bin = nullptr;  // k+1
     uint32_t *col_bins = nullptr; // nb: bin ids per column, ascending p
 
@@ -80,7 +79,6 @@ struct Graph {
     // destination lists of PC messages, grouped per destination (column CSC)
     uint32_t *cptr = nullptr;     // V+1
     uint32_t *cidx = nullptr;     // E: PNG slot of the message that carries the edge
-    uint16_t *cdst = nullptr;     // E: local destination
     int32_t *cw = nullptr;        // E or null
 
     // heavy destinations (more than kHeavy in-entries): entries in destination order, cut into
@@ -95,10 +93,14 @@ struct Graph {
     uint4 *task_heavy = nullptr;    // (local destination, first segment, segment count)
     std::vector<uint32_t> h_hv, h_hseg0;  // host: heavy destinations and their first segment
 
-    // SC bins
-    uint2 *scpair = nullptr;      // E: (local destination, value)
-    uint32_t *sccnt = nullptr;    // nb
-    uint32_t *scstamp = nullptr;  // nb
+    // SC bins, one per (source partition p, gather task t) with edges p -> t
+    uint2 *scpair = nullptr;      // E: (local destination, value), regions of capacity edges(p, t)
+    uint32_t *sccnt = nullptr;    // nsub: pairs written this iteration
+    uint32_t *sub_cap = nullptr;  // nsub+1: region offsets
+    uint32_t *sub_task = nullptr; // nsub: gather task of the bin
+    uint32_t *row_sub = nullptr;  // k+1: bins of each source partition
+    uint32_t *task_sub_ptr = nullptr;  // ngt+1: capacity of each task's fresh-bin list
+    uint32_t nsub = 0, max_row_subs = 0;
 
     // per partition statics
     uint32_t *Ep = nullptr, *npng_p = nullptr, *nbins_p = nullptr;  // device, k each
