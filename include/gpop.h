@@ -224,6 +224,24 @@ gpop_status gpop_selector_train(const float *features, const float *targets, uin
 gpop_status gpop_selector_grad(const float *params, const float *x, const float *y, uint32_t n,
                                void *cuda_stream, float *pred_out, float *grad_out, float *loss_out);
 
+/*
+ * Allocation-free variant of gpop_selector_grad for callers that cannot call cudaMalloc: code running
+ * while a stream is captured into a CUDA graph, code whose device memory belongs to another allocator
+ * (a framework's caching allocator or a fixed arena), and loops where an allocation would synchronise
+ * the device.  The paper has no counterpart; this is a convenience of this library.
+ *   params   GPOP_SELECTOR_WEIGHTS device floats;  x  n x 8 device floats (standardised);  y  n device floats
+ *   n        1 <= n <= 16384 (GPOP_ERR_INVALID_ARG otherwise)
+ *   pred_out n device floats or NULL;  grad_out GPOP_SELECTOR_WEIGHTS device floats;  loss_out 1 device float or NULL
+ * The call only enqueues two kernels on cuda_stream and returns; results are ready when the stream
+ * reaches them.  Its scratch is one fixed 1.4 MB device array inside the library, held by every GPU that
+ * loads the library until the process exits; nothing in it needs clearing between calls, and calls whose
+ * kernels overlap on the GPU (different streams, or different host threads) race on it.  The first call
+ * on each device looks up that array's device address with the device current; make that first call
+ * before any stream capture begins.  No cudaMalloc, cudaFree or other allocating routine is called.
+ */
+gpop_status gpop_selector_grad_noalloc(const float *params, const float *x, const float *y, uint32_t n,
+                                       void *cuda_stream, float *pred_out, float *grad_out, float *loss_out);
+
 /* Description of the last error on the calling thread ("" if none). */
 const char *gpop_last_error(void);
 

@@ -72,6 +72,7 @@ SIGNATURES = {
     "gpop_selector_get": (ctypes.c_int, [_vp]),
     "gpop_selector_train": (ctypes.c_int, [_vp, _vp, _u32, _u32, _f32, _u64, _vp, _vp, _vp]),
     "gpop_selector_grad": (ctypes.c_int, [_vp, _vp, _vp, _u32, _vp, _vp, _vp, _vp]),
+    "gpop_selector_grad_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _u32, _vp, _vp, _vp, _vp]),
     "gpop_last_error": (ctypes.c_char_p, []),
 }
 

@@ -313,3 +313,63 @@ extern "C" gpop_status gpop_selector_train(const float *features, const float *t
     if (loss_out) *loss_out = l;
     return GPOP_OK;
 }
+
+// --- allocation-free variant of gpop_selector_grad ---------------------------------------------
+//
+// For callers that must not allocate device memory: code that runs while a stream is being captured
+// into a CUDA graph (an allocation there would break or be baked into the capture), code whose device
+// memory is owned by another allocator (a framework's caching allocator, a fixed pre-sized arena), and
+// latency-critical loops where cudaMalloc/cudaFree would synchronise the device.  The caller passes
+// device buffers for every input and output; the per-block partial gradients live in the fixed array
+// below, which every GPU that loads this library keeps until the process exits.
+
+namespace gpop {
+namespace {
+
+constexpr uint32_t kNoAllocMaxSamples = 16384;             // largest n accepted
+constexpr uint32_t kNoAllocMaxBlocks = kNoAllocMaxSamples / S;
+// per-block gradient sums (kNoAllocMaxBlocks x NW), per-block loss sums, one spare loss slot
+constexpr size_t kNoAllocFloats = (size_t)kNoAllocMaxBlocks * NW + kNoAllocMaxBlocks + 1;
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+
+std::mutex g_noalloc_mu;
+float *g_noalloc_addr[256] = {};  // device address of g_noalloc_scratch per device ordinal
+
+}  // namespace
+}  // namespace gpop
+
+extern "C" gpop_status gpop_selector_grad_noalloc(const float *params, const float *x, const float *y, uint32_t n,
+                                                 void *cuda_stream, float *pred_out, float *grad_out,
+                                                 float *loss_out) {
+    set_error("");
+    if (!params || !x || !y || !grad_out) return fail(GPOP_ERR_INVALID_ARG, "params, x, y and grad_out must be device pointers");
+    if (n == 0 || n > kNoAllocMaxSamples)
+        return fail(GPOP_ERR_INVALID_ARG, "gpop_selector_grad_noalloc: n must be in [1, 16384] (fixed scratch size)");
+    int dev = 0;
+    GPOP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(GPOP_ERR_INVALID_ARG, "device ordinal out of range");
+    float *scratch;
+    {
+        // one-time set-up per device, with that device current: the host-side name of the array is
+        // not a device address, so ask the runtime for the address this device uses
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *addr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+            if (e != cudaSuccess || !addr)
+                return fail(GPOP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_noalloc_addr[dev] = static_cast<float *>(addr);
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const uint32_t nblk = (n + S - 1) / S;
+    float *part = scratch;
+    float *loss_part = scratch + (size_t)kNoAllocMaxBlocks * NW;
+    float *loss = loss_out ? loss_out : loss_part + kNoAllocMaxBlocks;
+    // every slot the reduction reads is written by k_mlp_grad first, so nothing needs clearing
+    k_mlp_grad<<<nblk, T, 0, s>>>(params, x, y, n, 1.f / (float)n, part, loss_part, pred_out);
+    k_mlp_reduce<<<(NW + 256) / 256, 256, 0, s>>>(part, loss_part, nblk, grad_out, loss);
+    GPOP_CUDA_TRY(cudaGetLastError());
+    return GPOP_OK;
+}
