@@ -148,6 +148,18 @@ def traffic_from_profile():
     return None
 
 
+def reduce_over_ranks(seconds, edges, dist, device):
+    """Whole-job numbers of independent replicas: the slowest rank's time and the sum of counted edges."""
+    if dist is None:
+        return seconds, edges
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    e = torch.tensor([edges], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return
@@ -169,9 +181,11 @@ def run_reference(a, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64/u32", "data": "synthetic",
-            "config": {"workload": f"rmat{a.scale}_pr_bfs", "scale": a.scale, "edge_factor": 16,
-                       "vertices": g.num_vertices, "edges": g.num_edges,
-                       "step": "oracle PageRank 1 iteration + BFS from one root (bounded sample of the GPU step)"},
+            "config": {"workload": f"rmat{a.scale}_pr_bfs_sssp", "scale": a.scale, "edge_factor": 16,
+                       "vertices": g.num_vertices, "edges": g.num_edges, "partition_size": a.partition,
+                       "pr_tol_l1": a.pr_tol,
+                       "sample": "each step: oracle PageRank 1 iteration + BFS from one root, a bounded sample "
+                                 "of the GPU step (edges counted the same way)"},
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                              "sample": "each step: serial C oracle PageRank 1 iteration + BFS from one root"},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -234,15 +248,7 @@ def run_ours(a, rank, world, local_rank):
     for i, s in enumerate(stats):
         r = my_roots[a.warmup + i]
         edges += E * s["pr"]["iterations"] + 2 * te_of[r]
-    t_s = torch.tensor([ms / 1e3, float(edges)], dtype=torch.float64, device="cuda")
-    if dist:
-        tmax = t_s[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tot = t_s[1:].clone()
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        t_all, edges_all = float(tmax.item()), float(tot.item())
-    else:
-        t_all, edges_all = ms / 1e3, float(edges)
+    t_all, edges_all = reduce_over_ranks(ms / 1e3, float(edges), dist, "cuda")
     value = edges_all / t_all / 1e9
 
     # per-application device throughput and the roofline of the dominant kernel (PageRank gather)
@@ -263,20 +269,18 @@ def run_ours(a, rank, world, local_rank):
         return ms_ / max(n_, 1) / 1e3, n_
 
     npng, npad, k = info["num_png"], info["num_png_padded"], info["num_partitions"]
-    eh = info["num_heavy_entries"]
-    el = E - eh
     # Algorithmic bytes per launch of an all-PC PageRank iteration (every vertex active):
     #  PC scatter: PNG source IDs (2 B) + message values (4 B) per padded slot, one message value per vertex;
-    #  gather (light destinations): PNG slot (4 B) per entry, column offsets, per vertex rank read +
-    #    write, next message value, two row offsets, frontier bits, and the message values (4 B per PNG
-    #    entry) in proportion to the entries it reads;
-    #  heavy-destination gather: PNG slot (4 B) per entry plus its share of the message values.
+    #  PC gather (k_gather_pc): every message value once (4 B per PNG entry, staged bin by bin), the
+    #    destination-list word of every in-entry (4 B) and the per-vertex PC result written (4 B);
+    #  task gather + filter (k_gather): per vertex the PC result read, rank read + write, next message
+    #    value, two row offsets (one per vertex in a stream) and the frontier bits.
     per_kernel_bytes = {
         1: 6 * npad + 4 * V,
-        3: 4 * el + 4 * (V + 1) + 16 * V + V // 4 + 4 * npng * el / max(E, 1),
-        4: 4 * eh + 4 * npng * eh / max(E, 1),
+        4: 4 * E + 4 * npng + 4 * V,
+        3: 4 * V + 16 * V + V // 4,
     }
-    names = {1: "k_scatter_pc", 3: "k_gather", 4: "k_gather_heavy"}
+    names = {1: "k_scatter_pc", 3: "k_gather", 4: "k_gather_pc"}
     hbm, peak_kind = peaks()
     kinfo = {}
     for i in (1, 3, 4):

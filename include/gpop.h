@@ -59,7 +59,7 @@ typedef struct gpop_graph gpop_graph;
  *   col            E destination IDs (< V); rows need not be sorted; self loops
  *                  and repeated edges are kept as parallel edges
  *   weights        E non-negative int32 edge weights (SSSP), or NULL
- *   partition_size P, a power of two in [32, 65536], or 0 for the default
+ *   partition_size P, a power of two in [32, 16384], or 0 for the default
  *                  (16384, clamped to V rounded up to a power of two); the
  *                  partition count k = ceil(V/P) must not exceed 65536
  *   mem_is_device  non-zero if row_ptr/col/weights are device pointers
@@ -86,9 +86,9 @@ typedef struct {
     uint32_t max_row_bins;        /* largest number of bins in one bin row */
     uint32_t reserved;
     uint64_t device_bytes;        /* device memory held by the handle */
-    uint64_t num_heavy_entries;   /* in-entries of destinations reduced in fixed segments */
-    uint32_t num_heavy_vertices;  /* destinations with more than 256 in-entries */
-    uint32_t num_heavy_segments;
+    uint64_t num_pc_blocks;       /* staged message blocks of the PC gather */
+    uint32_t num_pc_tasks;        /* PC gather tasks (column, block range) */
+    uint32_t num_pc_partials;     /* partial result vectors of columns split over several tasks */
 } gpop_graph_info;
 
 /* Fills *info.  Errors: GPOP_ERR_INVALID_ARG on NULL arguments. */

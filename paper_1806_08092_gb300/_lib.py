@@ -32,8 +32,8 @@ class GraphInfo(ctypes.Structure):
                 ("num_png_padded", ctypes.c_uint64), ("num_gather_tasks", ctypes.c_uint32),
                 ("num_scatter_tasks", ctypes.c_uint32), ("max_row_bins", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64),
-                ("num_heavy_entries", ctypes.c_uint64), ("num_heavy_vertices", ctypes.c_uint32),
-                ("num_heavy_segments", ctypes.c_uint32)]
+                ("num_pc_blocks", ctypes.c_uint64), ("num_pc_tasks", ctypes.c_uint32),
+                ("num_pc_partials", ctypes.c_uint32)]
 
 
 class RunOpts(ctypes.Structure):

@@ -25,11 +25,10 @@ gpop_status fail(gpop_status st, const std::string &msg) {
 void free_graph(Graph *g) {
     release_run_state(g);
     void *ptrs[] = {g->rowptr, g->col, g->w, g->esub, g->row_bin, g->bin_q, g->col_bin,
-                    g->col_bins, g->png, g->pdata, g->row_png, g->cptr, g->cidx, g->cw,
+                    g->col_bins, g->png, g->pdata, g->row_png, g->pc_runs, g->pc_blk_run, g->pc_blk_ent,
+                    g->pc_task, g->pc_rng, g->pc_tsp, g->pc_wsp, g->col_ntask, g->col_part0, g->pc_part, g->pe, g->pw,
                     g->scpair, g->sccnt, g->sub_cap, g->sub_task, g->row_sub, g->task_sub_ptr,
-                    g->Ep, g->npng_p, g->nbins_p, g->gtask,
-                    g->col_task, g->stask, g->pc_state, g->hidx, g->hw, g->hseg, g->hpart, g->task_hptr,
-                    g->task_heavy};
+                    g->Ep, g->npng_p, g->nbins_p, g->gtask, g->col_task, g->stask, g->pc_state};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete[] g->h_Ep;
@@ -150,7 +149,7 @@ __global__ void k_pad8(uint32_t k, const uint32_t *m, uint32_t *mp) {
 __global__ void k_place_msgs(uint64_t nmsg, uint32_t shift, uint32_t k, const uint64_t *skey,
                              const uint32_t *shead, const uint32_t *binscan, const uint32_t *row_msg,
                              const uint32_t *row_png, uint16_t *png, uint32_t *slot_of_head,
-                             uint32_t *bin_of_head, uint32_t *bin_q) {
+                             uint32_t *bin_of_head, uint32_t *bin_q, uint32_t *bin_j0, uint32_t *bin_slot0) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nmsg; j += stride) {
         uint64_t key = skey[j];
@@ -161,16 +160,35 @@ __global__ void k_place_msgs(uint64_t nmsg, uint32_t shift, uint32_t k, const ui
         uint32_t b = binscan[j] - 1;  // inclusive scan of new-bin flags
         slot_of_head[shead[j]] = slot;
         bin_of_head[shead[j]] = b;
-        if (j == 0 || (skey[j - 1] >> shift) != pk) bin_q[b] = q;
+        if (j == 0 || (skey[j - 1] >> shift) != pk) {
+            bin_q[b] = q;
+            bin_j0[b] = (uint32_t)j;  // first message of the bin (sorted order) and its PNG slot
+            bin_slot0[b] = slot;
+        }
     }
 }
 
-// every edge inherits the slot and bin of its message head
-__global__ void k_edge_msg(uint64_t E, const uint32_t *head_of, const uint32_t *slot_of_head, const uint32_t *col,
-                           uint64_t *ckey) {
+// key of every PC in-entry: (gather block << 32) | (local destination << 16) | index in the block,
+// where the message of edge e is the one of its head (same source, same destination partition)
+__global__ void k_pc_keys(uint64_t E, uint32_t shift, uint32_t P, const uint32_t *head_of,
+                          const uint32_t *slot_of_head, const uint32_t *bin_of_head, const uint32_t *col,
+                          const uint32_t *bin_slot0, const uint32_t *bin_cseq0, const uint32_t *col_blk0,
+                          uint64_t *key) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E; e += stride)
-        ckey[e] = ((uint64_t)col[e] << 32) | slot_of_head[head_of[e]];  // destination-major column lists
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E; e += stride) {
+        uint32_t h = head_of[e], b = bin_of_head[h], v = col[e];
+        uint32_t cseq = bin_cseq0[b] + (slot_of_head[h] - bin_slot0[b]);
+        uint32_t blk = col_blk0[v >> shift] + cseq / kPcBlock;
+        key[e] = ((uint64_t)blk << 32) | ((uint64_t)(v & (P - 1)) << 16) | (cseq % kPcBlock);
+    }
+}
+
+__global__ void k_pc_unpack(uint64_t E, const uint64_t *key, uint32_t *pe, uint32_t *blk_hist) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < E; i += stride) {
+        pe[i] = (uint32_t)key[i];
+        atomicAdd(&blk_hist[key[i] >> 32], 1u);
+    }
 }
 
 // SC bins are (source partition p, gather task t) pairs: key (p << 32) | t per edge
@@ -213,23 +231,26 @@ __global__ void k_indegree(uint64_t E, const uint32_t *col, uint32_t *indeg) {
         atomicAdd(&indeg[col[e]], 1u);
 }
 
-__global__ void k_unpack_csc(uint64_t E, uint32_t P, const uint64_t *key, uint32_t *cidx, uint16_t *cdst) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < E; i += stride) {
-        uint64_t x = key[i];
-        cidx[i] = (uint32_t)x;
-        if (cdst) cdst[i] = (uint16_t)((x >> 32) & (P - 1));
-    }
-}
-
-// splits the destination-sorted entries into light and heavy destinations
-__global__ void k_heavy_flags(uint64_t E, const uint64_t *key, const uint32_t *indeg, uint32_t heavy, uint8_t *fl,
-                              uint8_t *fh) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < E; i += stride) {
-        bool h = indeg[(uint32_t)(key[i] >> 32)] > heavy;
-        fl[i] = !h;
-        fh[i] = h;
+// Warp splits of the PC gather: for every task block (entries [lo, hi), sorted by destination) and w in
+// 0..kPcGatherWarps, the w-th of kPcGatherWarps ranges of about equal size: the nominal cut
+// lo + (hi - lo) w / kPcGatherWarps moved forward to the next change of destination, so that every
+// destination's entries of the block fall into one range.
+__global__ void k_warp_splits(uint32_t nrow, const uint32_t *lo, const uint32_t *hi, const uint32_t *pe,
+                              uint32_t *out) {
+    constexpr uint32_t kSp = kPcGatherWarps + 1;
+    uint64_t n = (uint64_t)nrow * kSp, stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t r = (uint32_t)(i / kSp), w = (uint32_t)(i % kSp);
+        const uint32_t l = lo[r], h = hi[r];
+        uint32_t a = (uint32_t)(l + (uint64_t)(h - l) * w / kPcGatherWarps), b = h;
+        if (a > l && a < h) {
+            const uint32_t d = pe[a - 1] >> 16;
+            while (a < b) {  // first entry in [a, h) with destination > d
+                const uint32_t m = a + (b - a) / 2;
+                if ((pe[m] >> 16) <= d) a = m + 1; else b = m;
+            }
+        }
+        out[i] = a;
     }
 }
 
@@ -427,116 +448,23 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
     GPOP_CUDA_TRY(dalloc(g, &g->bin_q, g->nb));
     GPOP_CUDA_TRY(cudaMemsetAsync(g->png, 0, 2ull * std::max<uint64_t>(g->npng_pad, 1), s));
     GPOP_CUDA_TRY(cudaMemsetAsync(g->pdata, 0xFF, 4ull * std::max<uint64_t>(g->npng_pad, 1), s));
-    uint32_t *slot_of_head, *bin_of_head;
+    uint32_t *slot_of_head, *bin_of_head, *bin_j0, *bin_slot0;
     GPOP_CUDA_TRY(t.alloc(&slot_of_head, E));
     GPOP_CUDA_TRY(t.alloc(&bin_of_head, E));
+    GPOP_CUDA_TRY(t.alloc(&bin_j0, g->nb + 1));
+    GPOP_CUDA_TRY(t.alloc(&bin_slot0, g->nb + 1));
     if (nmsg)
         k_place_msgs<<<blocks_for(nmsg), kThreads, 0, s>>>(nmsg, shift, k, skey, shead, binscan, row_msg, g->row_png,
-                                                           g->png, slot_of_head, bin_of_head, g->bin_q);
+                                                           g->png, slot_of_head, bin_of_head, g->bin_q, bin_j0,
+                                                           bin_slot0);
 
-    // 5. per-edge message slot (keys of the column lists)
+    // 5. message head of every edge (its first edge to the same destination partition)
     uint32_t *head_of;
-    uint64_t *ckey;
     GPOP_CUDA_TRY(t.alloc(&head_of, E));
-    GPOP_CUDA_TRY(t.alloc(&ckey, E));
     if (E) {
         GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
             return cub::DeviceScan::InclusiveScan(tmp, bytes, head_idx, head_of, MaxOp(), E, s);
         }));
-        k_edge_msg<<<blocks_for(E), kThreads, 0, s>>>(E, head_of, slot_of_head, g->col, ckey);
-    }
-
-    // 6. destination lists grouped per destination vertex (column CSC over PNG slots).  A destination
-    //    with more than kHeavy in-entries keeps its entries in a separate list cut into segments of at
-    //    most kHeavySeg entries, reduced by their own warps so that no single task serialises a hub.
-    GPOP_CUDA_TRY(dalloc(g, &g->cptr, (uint64_t)V + 1));
-    GPOP_CUDA_TRY(dalloc(g, &g->cidx, E));
-    if (g->weighted) GPOP_CUDA_TRY(dalloc(g, &g->cw, E));
-    std::vector<uint32_t> hin(V);
-    {
-        uint32_t *indeg, *light;
-        GPOP_CUDA_TRY(t.alloc(&indeg, (uint64_t)V + 1));
-        GPOP_CUDA_TRY(t.alloc(&light, (uint64_t)V + 1));
-        GPOP_CUDA_TRY(cudaMemsetAsync(indeg, 0, 4ull * (V + 1), s));
-        if (E) k_indegree<<<blocks_for(E), kThreads, 0, s>>>(E, g->col, indeg);
-        GPOP_CUDA_TRY(cudaMemcpyAsync(hin.data(), indeg, 4ull * V, cudaMemcpyDeviceToHost, s));
-        GPOP_CUDA_TRY(cudaStreamSynchronize(s));
-        std::vector<uint32_t> hlight(V + 1, 0);
-        uint64_t nheavy_entries = 0;
-        for (uint32_t v = 0; v < V; ++v) {
-            if (hin[v] > kHeavy) {
-                g->h_hv.push_back(v);
-                nheavy_entries += hin[v];
-            } else {
-                hlight[v] = hin[v];
-            }
-        }
-        GPOP_CUDA_TRY(cudaMemcpyAsync(light, hlight.data(), 4ull * (V + 1), cudaMemcpyHostToDevice, s));
-        GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-            return cub::DeviceScan::ExclusiveSum(tmp, bytes, light, g->cptr, (uint64_t)V + 1, s);
-        }));
-        g->nheavy = nheavy_entries;
-        GPOP_CUDA_TRY(dalloc(g, &g->hidx, nheavy_entries));
-        if (g->weighted) GPOP_CUDA_TRY(dalloc(g, &g->hw, nheavy_entries));
-        if (E) {
-            uint64_t *ck2, *ckl, *ckh;
-            int32_t *cw2 = nullptr;
-            uint8_t *fl, *fh;
-            uint32_t *d_cnt;
-            GPOP_CUDA_TRY(t.alloc(&ck2, E));
-            GPOP_CUDA_TRY(t.alloc(&ckl, E));
-            GPOP_CUDA_TRY(t.alloc(&ckh, nheavy_entries));
-            GPOP_CUDA_TRY(t.alloc(&fl, E));
-            GPOP_CUDA_TRY(t.alloc(&fh, E));
-            GPOP_CUDA_TRY(t.alloc(&d_cnt, 2));
-            int end_bit = 32 + bits_for(V);
-            if (g->weighted) {
-                GPOP_CUDA_TRY(t.alloc(&cw2, E));
-                GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-                    return cub::DeviceRadixSort::SortPairs(tmp, bytes, ckey, ck2, g->w, cw2, E, 0, end_bit, s);
-                }));
-            } else {
-                GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-                    return cub::DeviceRadixSort::SortKeys(tmp, bytes, ckey, ck2, E, 0, end_bit, s);
-                }));
-            }
-            k_heavy_flags<<<blocks_for(E), kThreads, 0, s>>>(E, ck2, indeg, kHeavy, fl, fh);
-            GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-                return cub::DeviceSelect::Flagged(tmp, bytes, ck2, fl, ckl, d_cnt, (int64_t)E, s);
-            }));
-            GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-                return cub::DeviceSelect::Flagged(tmp, bytes, ck2, fh, ckh, d_cnt + 1, (int64_t)E, s);
-            }));
-            if (g->weighted) {
-                GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-                    return cub::DeviceSelect::Flagged(tmp, bytes, cw2, fl, g->cw, d_cnt, (int64_t)E, s);
-                }));
-                GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-                    return cub::DeviceSelect::Flagged(tmp, bytes, cw2, fh, g->hw, d_cnt + 1, (int64_t)E, s);
-                }));
-            }
-            uint64_t nlight = E - nheavy_entries;
-            if (nlight) k_unpack_csc<<<blocks_for(nlight), kThreads, 0, s>>>(nlight, P, ckl, g->cidx, nullptr);
-            if (nheavy_entries)
-                k_unpack_csc<<<blocks_for(nheavy_entries), kThreads, 0, s>>>(nheavy_entries, P, ckh, g->hidx, nullptr);
-        }
-        // heavy destinations: contiguous entry ranges in destination order, cut into segments
-        uint64_t off = 0;
-        std::vector<uint4> segs;
-        for (size_t i = 0; i < g->h_hv.size(); ++i) {
-            uint32_t v = g->h_hv[i];
-            g->h_hseg0.push_back((uint32_t)segs.size());
-            for (uint64_t b = 0; b < hin[v]; b += kHeavySeg)
-                segs.push_back(make_uint4(v, (uint32_t)(off + b), (uint32_t)std::min<uint64_t>(off + b + kHeavySeg, off + hin[v]), 0));
-            off += hin[v];
-        }
-        g->h_hseg0.push_back((uint32_t)segs.size());
-        g->nseg = (uint32_t)segs.size();
-        GPOP_CUDA_TRY(dalloc(g, &g->hseg, g->nseg));
-        GPOP_CUDA_TRY(dalloc(g, &g->hpart, g->nseg));
-        if (g->nseg)
-            GPOP_CUDA_TRY(cudaMemcpyAsync(g->hseg, segs.data(), sizeof(uint4) * segs.size(), cudaMemcpyHostToDevice, s));
-        GPOP_CUDA_TRY(cudaStreamSynchronize(s));
     }
 
     // 7. bins per column in ascending source partition
@@ -562,6 +490,197 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         }));
     }
 
+    // 6. PC gather blocks.  The messages of column q (its bins (p, q), p ascending, each bin's
+    //    messages in source order) form the column sequence; it is cut into blocks of kPcBlock messages
+    //    that the gather stages in shared memory by coalesced copies of bin runs ("runs": row-major
+    //    source offset, length, offset in the block).  Every PC in-entry becomes a 4-byte word
+    //    (local destination << 16 | index in its block), sorted by (block, destination, index).
+    //    Gather tasks cover consecutive entries of one column: about max(kPcTaskMinEntries, E / (8 x
+    //    SMs)) entries and at most kPcTaskBlocks blocks each, a block's entries split over several
+    //    tasks when it is larger; a column with several tasks leaves one partial vector per task,
+    //    merged in column order by the filter.  Tasks are listed largest first.
+    {
+        const uint32_t nb = (uint32_t)g->nb;
+        std::vector<uint32_t> hj0(nb + 1), hslot0(nb), hcolbins(nb), hcolbin(k + 1);
+        if (nb) {
+            GPOP_CUDA_TRY(cudaMemcpyAsync(hj0.data(), bin_j0, 4ull * nb, cudaMemcpyDeviceToHost, s));
+            GPOP_CUDA_TRY(cudaMemcpyAsync(hslot0.data(), bin_slot0, 4ull * nb, cudaMemcpyDeviceToHost, s));
+            GPOP_CUDA_TRY(cudaMemcpyAsync(hcolbins.data(), g->col_bins, 4ull * nb, cudaMemcpyDeviceToHost, s));
+        }
+        GPOP_CUDA_TRY(cudaMemcpyAsync(hcolbin.data(), g->col_bin, 4ull * (k + 1), cudaMemcpyDeviceToHost, s));
+        GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+        hj0[nb] = (uint32_t)nmsg;
+        std::vector<uint32_t> cseq0(nb + 1, 0), col_blk0(k + 1, 0);
+        std::vector<uint4> runs;
+        uint32_t nblocks = 0;
+        for (uint32_t q = 0; q < k; ++q) {
+            col_blk0[q] = nblocks;
+            uint64_t cs = 0;
+            for (uint32_t i = hcolbin[q]; i < hcolbin[q + 1]; ++i) {
+                uint32_t b = hcolbins[i], cnt = hj0[b + 1] - hj0[b];
+                cseq0[b] = (uint32_t)cs;
+                uint32_t done = 0;
+                while (done < cnt) {  // split the bin's run at block boundaries
+                    uint64_t pos = cs + done;
+                    uint32_t piece = (uint32_t)std::min<uint64_t>(cnt - done, kPcBlock - pos % kPcBlock);
+                    runs.push_back(make_uint4(hslot0[b] + done, piece, (uint32_t)(pos % kPcBlock),
+                                              nblocks + (uint32_t)(pos / kPcBlock)));
+                    done += piece;
+                }
+                cs += cnt;
+            }
+            nblocks += (uint32_t)((cs + kPcBlock - 1) / kPcBlock);
+        }
+        col_blk0[k] = nblocks;
+        std::vector<uint32_t> blk_run0(nblocks + 1, (uint32_t)runs.size());
+        for (size_t r = runs.size(); r-- > 0;) blk_run0[runs[r].w] = (uint32_t)r;
+        for (uint32_t bl = nblocks; bl-- > 0;)  // blocks without runs (none in practice) take the next start
+            if (blk_run0[bl] > blk_run0[bl + 1]) blk_run0[bl] = blk_run0[bl + 1];
+        g->npcb = nblocks;
+        GPOP_CUDA_TRY(dalloc(g, &g->pc_runs, runs.size()));
+        GPOP_CUDA_TRY(dalloc(g, &g->pc_blk_run, (uint64_t)nblocks + 1));
+        GPOP_CUDA_TRY(dalloc(g, &g->pc_blk_ent, (uint64_t)nblocks + 1));
+        GPOP_CUDA_TRY(dalloc(g, &g->col_ntask, k));
+        GPOP_CUDA_TRY(dalloc(g, &g->col_part0, k));
+        // +4: the gather copies entry ranges as whole aligned 16-byte words
+        GPOP_CUDA_TRY(dalloc(g, &g->pe, E + 4));
+        if (g->weighted) GPOP_CUDA_TRY(dalloc(g, &g->pw, E + 4));
+        if (!runs.empty())
+            GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_runs, runs.data(), sizeof(uint4) * runs.size(), cudaMemcpyHostToDevice, s));
+        GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_blk_run, blk_run0.data(), 4ull * (nblocks + 1), cudaMemcpyHostToDevice, s));
+        // entries: sort keys (block, local destination, index in block)
+        uint32_t *d_cseq0, *d_colblk0, *blk_hist;
+        GPOP_CUDA_TRY(t.alloc(&d_cseq0, nb + 1));
+        GPOP_CUDA_TRY(t.alloc(&d_colblk0, (uint64_t)k + 1));
+        GPOP_CUDA_TRY(t.alloc(&blk_hist, (uint64_t)nblocks + 1));
+        GPOP_CUDA_TRY(cudaMemcpyAsync(d_cseq0, cseq0.data(), 4ull * (nb + 1), cudaMemcpyHostToDevice, s));
+        GPOP_CUDA_TRY(cudaMemcpyAsync(d_colblk0, col_blk0.data(), 4ull * (k + 1), cudaMemcpyHostToDevice, s));
+        GPOP_CUDA_TRY(cudaMemsetAsync(blk_hist, 0, 4ull * (nblocks + 1), s));
+        if (E) {
+            uint64_t *pk, *pk2;
+            GPOP_CUDA_TRY(t.alloc(&pk, E));
+            GPOP_CUDA_TRY(t.alloc(&pk2, E));
+            k_pc_keys<<<blocks_for(E), kThreads, 0, s>>>(E, shift, P, head_of, slot_of_head, bin_of_head, g->col,
+                                                         bin_slot0, d_cseq0, d_colblk0, pk);
+            int end_bit = 32 + bits_for((uint64_t)nblocks + 1);
+            if (g->weighted) {
+                GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+                    return cub::DeviceRadixSort::SortPairs(tmp, bytes, pk, pk2, g->w, g->pw, E, 0, end_bit, s);
+                }));
+            } else {
+                GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+                    return cub::DeviceRadixSort::SortKeys(tmp, bytes, pk, pk2, E, 0, end_bit, s);
+                }));
+            }
+            k_pc_unpack<<<blocks_for(E), kThreads, 0, s>>>(E, pk2, g->pe, blk_hist);
+        }
+        GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+            return cub::DeviceScan::ExclusiveSum(tmp, bytes, blk_hist, g->pc_blk_ent, (uint64_t)nblocks + 1, s);
+        }));
+        std::vector<uint32_t> hbe(nblocks + 1);
+        GPOP_CUDA_TRY(cudaMemcpyAsync(hbe.data(), g->pc_blk_ent, 4ull * (nblocks + 1), cudaMemcpyDeviceToHost, s));
+        GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+
+        // gather tasks over each column's entries
+        const uint64_t target = std::max<uint64_t>(kPcTaskMinEntries, E / (8ull * (uint64_t)std::max(1, g->num_sms)));
+        std::vector<uint4> ptasks;
+        std::vector<uint2> prng;
+        std::vector<uint32_t> col_ntask(k, 0), col_part0(k, 0);
+        uint32_t nparts = 0;
+        for (uint32_t q = 0; q < k; ++q) {
+            const uint32_t b_end = col_blk0[q + 1];
+            uint32_t b = col_blk0[q];
+            uint64_t pos = hbe[b];
+            const uint64_t end = hbe[b_end];
+            const size_t first_task = ptasks.size();
+            for (;;) {
+                while (b < b_end && pos >= hbe[b + 1]) ++b;  // skip exhausted blocks
+                if (b == b_end || pos >= end) break;
+                const uint32_t tb = b;
+                const uint64_t ea = pos;
+                uint64_t cnt = 0;
+                uint32_t tb_end;
+                for (;;) {
+                    const uint64_t avail = hbe[b + 1] - pos, room = target - cnt;
+                    if (avail >= room) {  // task full; the block may continue in the next task
+                        pos += room;
+                        tb_end = b + 1;
+                        break;
+                    }
+                    cnt += avail;
+                    pos = hbe[b + 1];
+                    ++b;
+                    if (b - tb == kPcTaskBlocks || b == b_end) {
+                        tb_end = b;
+                        break;
+                    }
+                }
+                ptasks.push_back(make_uint4(q, tb, tb_end, kNull));
+                prng.push_back(make_uint2((uint32_t)ea, (uint32_t)pos));
+                b = tb_end - 1;
+            }
+            const uint32_t ntq = (uint32_t)(ptasks.size() - first_task);
+            col_ntask[q] = ntq;
+            col_part0[q] = nparts;
+            if (ntq > 1) {
+                for (uint32_t j = 0; j < ntq; ++j) ptasks[first_task + j].w = nparts + j;
+                nparts += ntq;
+            }
+        }
+        // largest tasks first, so that the persistent CTAs finish together
+        std::vector<uint32_t> order(ptasks.size());
+        for (uint32_t i = 0; i < order.size(); ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+            return prng[x].y - prng[x].x > prng[y].y - prng[y].x;
+        });
+        std::vector<uint4> stasks(ptasks.size());
+        std::vector<uint2> srng(ptasks.size());
+        for (size_t i = 0; i < order.size(); ++i) {
+            stasks[i] = ptasks[order[i]];
+            srng[i] = prng[order[i]];
+        }
+        // warp splits: per task block, kPcGatherWarps entry ranges of about equal size cut at
+        // destination boundaries
+        constexpr uint32_t kSp = kPcGatherWarps + 1;
+        {
+            std::vector<uint32_t> tsp(stasks.size()), rlo, rhi;
+            for (size_t ti = 0; ti < stasks.size(); ++ti) {
+                tsp[ti] = (uint32_t)rlo.size();
+                const uint4 tk = stasks[ti];
+                for (uint32_t b = tk.y; b < tk.z; ++b) {
+                    rlo.push_back(b == tk.y ? srng[ti].x : hbe[b]);
+                    rhi.push_back(b + 1 == tk.z ? srng[ti].y : hbe[b + 1]);
+                }
+            }
+            const uint32_t nrow = (uint32_t)rlo.size();
+            uint32_t *d_lo, *d_hi;
+            GPOP_CUDA_TRY(t.alloc(&d_lo, (uint64_t)nrow + 1));
+            GPOP_CUDA_TRY(t.alloc(&d_hi, (uint64_t)nrow + 1));
+            GPOP_CUDA_TRY(dalloc(g, &g->pc_wsp, (uint64_t)nrow * kSp + 1));
+            GPOP_CUDA_TRY(dalloc(g, &g->pc_tsp, (uint64_t)tsp.size() + 1));
+            if (nrow) {
+                GPOP_CUDA_TRY(cudaMemcpyAsync(d_lo, rlo.data(), 4ull * nrow, cudaMemcpyHostToDevice, s));
+                GPOP_CUDA_TRY(cudaMemcpyAsync(d_hi, rhi.data(), 4ull * nrow, cudaMemcpyHostToDevice, s));
+                GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_tsp, tsp.data(), 4ull * tsp.size(), cudaMemcpyHostToDevice, s));
+                k_warp_splits<<<blocks_for((uint64_t)nrow * kSp), kThreads, 0, s>>>(nrow, d_lo, d_hi, g->pe,
+                                                                                    g->pc_wsp);
+            }
+            GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        g->npct = (uint32_t)stasks.size();
+        g->npart = nparts;
+        GPOP_CUDA_TRY(dalloc(g, &g->pc_task, stasks.size()));
+        GPOP_CUDA_TRY(dalloc(g, &g->pc_rng, stasks.size()));
+        GPOP_CUDA_TRY(dalloc(g, &g->pc_part, (uint64_t)nparts * P));
+        if (!stasks.empty()) {
+            GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_task, stasks.data(), sizeof(uint4) * stasks.size(), cudaMemcpyHostToDevice, s));
+            GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_rng, srng.data(), sizeof(uint2) * srng.size(), cudaMemcpyHostToDevice, s));
+        }
+        GPOP_CUDA_TRY(cudaMemcpyAsync(g->col_ntask, col_ntask.data(), 4ull * k, cudaMemcpyHostToDevice, s));
+        GPOP_CUDA_TRY(cudaMemcpyAsync(g->col_part0, col_part0.data(), 4ull * k, cudaMemcpyHostToDevice, s));
+        GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+
     // 8. per-partition statics
     GPOP_CUDA_TRY(dalloc(g, &g->Ep, (uint64_t)k + 1));
     k_part_edges<<<blocks_for(k), kThreads, 0, s>>>(k, V, shift, g->rowptr, g->Ep);
@@ -571,11 +690,8 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
     GPOP_CUDA_TRY(cudaMemcpyAsync(hnb.data(), g->nbins_p, 4ull * k, cudaMemcpyDeviceToHost, s));
     GPOP_CUDA_TRY(cudaMemcpyAsync(hrow_png.data(), g->row_png, 4ull * (k + 1), cudaMemcpyDeviceToHost, s));
 
-    // 9. static gather tasks: destination ranges of <= kGatherWidth vertices, ~kGatherEntries in-entries
+    // 9. static gather tasks: destination ranges of at most kGatherWidth vertices of one column
     uint32_t nblk = (V + 31) / 32;
-    std::vector<uint32_t> hcnt(nblk, 0);  // light in-entries per block of 32 destinations
-    for (uint32_t v = 0; v < V; ++v)
-        if (hin[v] <= kHeavy) hcnt[v / 32] += hin[v];
     GPOP_CUDA_TRY(cudaStreamSynchronize(s));
     g->h_Ep = new uint64_t[k];
     g->h_npng = new uint64_t[k];
@@ -597,35 +713,13 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         uint32_t b1 = (uint32_t)std::min<uint64_t>((((uint64_t)q + 1) << shift) / 32, nblk);
         uint32_t base = b0;
         while (b0 < b1) {
-            uint32_t e = 0, b = b0;
-            while (b < b1 && (b - b0) < width_blocks && (b == b0 || e + hcnt[b] <= kGatherEntries)) e += hcnt[b++];
-            gt.push_back(GatherTask{q, (b0 - base) * 32, (b - base) * 32, e});
+            uint32_t b = std::min(b0 + width_blocks, b1);
+            gt.push_back(GatherTask{q, (b0 - base) * 32, (b - base) * 32, 0});
             b0 = b;
         }
     }
     col_task[k] = (uint32_t)gt.size();
     g->ngt = (uint32_t)gt.size();
-    // heavy destinations of every task: (local destination, first segment, segment count)
-    {
-        std::vector<uint32_t> thp(g->ngt + 1, 0);
-        std::vector<uint4> th;
-        size_t hi = 0;
-        for (uint32_t ti = 0; ti < g->ngt; ++ti) {
-            thp[ti] = (uint32_t)th.size();
-            uint64_t lo = ((uint64_t)gt[ti].q << shift) + gt[ti].d0, up = ((uint64_t)gt[ti].q << shift) + gt[ti].d1;
-            while (hi < g->h_hv.size() && g->h_hv[hi] < lo) ++hi;
-            for (size_t j = hi; j < g->h_hv.size() && g->h_hv[j] < up; ++j)
-                th.push_back(make_uint4((uint32_t)(g->h_hv[j] - ((uint64_t)gt[ti].q << shift) - gt[ti].d0),
-                                        g->h_hseg0[j], g->h_hseg0[j + 1] - g->h_hseg0[j], 0));
-        }
-        thp[g->ngt] = (uint32_t)th.size();
-        GPOP_CUDA_TRY(dalloc(g, &g->task_hptr, (uint64_t)g->ngt + 1));
-        GPOP_CUDA_TRY(dalloc(g, &g->task_heavy, th.size()));
-        GPOP_CUDA_TRY(cudaMemcpyAsync(g->task_hptr, thp.data(), 4ull * (g->ngt + 1), cudaMemcpyHostToDevice, s));
-        if (!th.empty())
-            GPOP_CUDA_TRY(cudaMemcpyAsync(g->task_heavy, th.data(), sizeof(uint4) * th.size(), cudaMemcpyHostToDevice, s));
-        GPOP_CUDA_TRY(cudaStreamSynchronize(s));
-    }
     GPOP_CUDA_TRY(dalloc(g, &g->gtask, g->ngt));
     GPOP_CUDA_TRY(dalloc(g, &g->col_task, (uint64_t)k + 1));
     GPOP_CUDA_TRY(cudaMemcpyAsync(g->gtask, gt.data(), sizeof(GatherTask) * gt.size(), cudaMemcpyHostToDevice, s));
@@ -731,7 +825,7 @@ extern "C" gpop_status gpop_graph_build(uint32_t num_vertices, uint64_t num_edge
         P = 32;
         while (P < 16384 && P < num_vertices) P <<= 1;
     }
-    if (P < 32 || P > 65536 || (P & (P - 1))) return fail(GPOP_ERR_INVALID_ARG, "partition_size must be a power of two in [32, 65536]");
+    if (P < 32 || P > 16384 || (P & (P - 1))) return fail(GPOP_ERR_INVALID_ARG, "partition_size must be a power of two in [32, 16384]");
     if (((uint64_t)num_vertices + P - 1) / P > 65536) return fail(GPOP_ERR_INVALID_ARG, "more than 65536 partitions");
     gpop_graph *h = new (std::nothrow) gpop_graph();
     if (!h) return fail(GPOP_ERR_OOM, "host allocation failed");
@@ -765,9 +859,9 @@ extern "C" gpop_status gpop_graph_get_info(const gpop_graph *h, gpop_graph_info 
     info->num_scatter_tasks = g.nst;
     info->max_row_bins = g.max_row_bins;
     info->device_bytes = g.device_bytes;
-    info->num_heavy_vertices = (uint32_t)g.h_hv.size();
-    info->num_heavy_segments = g.nseg;
-    info->num_heavy_entries = g.nheavy;
+    info->num_pc_blocks = g.npcb;
+    info->num_pc_tasks = g.npct;
+    info->num_pc_partials = g.npart;
     return GPOP_OK;
 }
 

@@ -34,7 +34,17 @@ constexpr int kGatherWarps = kGatherThreads / 32;
 constexpr int kScatterThreads = 256;
 constexpr int kPlanThreads = 1024;
 constexpr uint32_t kSent = 0xFFFFFFFFu;
-constexpr int kTile = 2048;  // PC entries staged in shared memory per gather round
+constexpr int kPcWarps = kPcGatherWarps;          // k_gather_pc warps (one destination slice of a block each)
+constexpr int kPcThreads = 32 * kPcWarps;
+constexpr uint32_t kPcMaxSlots = 4;               // entry ring depth per consumer warp
+constexpr uint32_t kPcSpinLimit = 1u << 24;       // bounded mbarrier waits
+// destination entries a lane folds serially per round (SSSP also stages weights: half as many)
+template <int ALGO>
+struct PcShape {
+    static constexpr uint32_t K = ALGO == ALG_SSSP ? 8 : 16;
+    static constexpr uint32_t kRound = 32 * K;  // entries per warp round
+    static constexpr uint32_t kSlotWords = kRound * (ALGO == ALG_SSSP ? 2 : 1);
+};
 
 struct Params {
     // graph
@@ -47,18 +57,19 @@ struct Params {
     const uint16_t *png;
     uint32_t *pdata;
     const uint32_t *row_png;
-    const uint32_t *cptr, *cidx;
-    const int32_t *cw;
     uint2 *scpair;
     uint32_t *sccnt;
     uint32_t *task_sc_cnt, *task_sc_list;  // per gather task: fresh SC bins of this iteration
-    const uint32_t *hidx;
-    const int32_t *hw;
-    const uint4 *hseg;
-    uint32_t *hpart;
-    uint32_t nseg;
-    const uint32_t *task_hptr;
-    const uint4 *task_heavy;
+    // PC gather blocks
+    const uint4 *pc_runs, *pc_task;
+    const uint2 *pc_rng;
+    const uint32_t *pc_wsp, *pc_tsp;  // per task block: kPcWarps+1 entry splits; per task: first split row
+    const uint32_t *pc_blk_run, *pc_blk_ent, *col_ntask, *col_part0, *pe;
+    const int32_t *pw;
+    uint32_t *pc_part;
+    uint32_t npct;
+    uint32_t pc_slots;  // entry ring slots per consumer warp of k_gather_pc (2..kPcMaxSlots)
+    uint32_t *pc_sum;  // per vertex: combined PC message of the iteration (single-task columns)
     const uint32_t *Ep, *npng_p;
     const GatherTask *gtask;
     uint32_t ngt;
@@ -223,6 +234,7 @@ __device__ uint8_t learned_mode(const float *sp, const float f[8], int lane) {
 
 template <int ALGO>
 __global__ void k_init(Params p) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.ctrl->error = 0;  // device check flags, sticky for the run
     uint32_t nw = (p.V + 31) / 32;
     for (uint32_t wi = blockIdx.x * blockDim.x + threadIdx.x; wi < nw; wi += gridDim.x * blockDim.x) {
         uint32_t word = 0;
@@ -402,7 +414,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         if ((p.algo == ALG_PR || p.algo == ALG_PPR) && p.iter > 1 && r < p.tol) done = 1;
         Control c;
         c.frontier_v = a; c.frontier_e = b; c.residual = r; c.model_bytes = by;
-        c.n_pc = c0; c.n_sc = c1; c.n_null = c2; c.done = done; c.n_fallback = c3; c.error = 0;
+        c.n_pc = c0; c.n_sc = c1; c.n_null = c2; c.done = done; c.n_fallback = c3; c.error = p.ctrl->error;
         c.pad[0] = c.pad[1] = 0;
         *p.ctrl = c;
         for (int i = 0; i < 8; ++i) p.counters[i] = 0;
@@ -574,67 +586,358 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
 
 // --- gather + filter ---------------------------------------------------------------------------
 
-// Heavy destinations (more than kHeavy PC in-entries): one warp reduces one fixed-size segment of a
-// destination's entries; the gather task owning the destination combines the segment results in
-// segment order.  Lane l accumulates entries l, l+32, ... in order and a fixed xor tree combines the
-// lanes, so the result does not depend on scheduling.
-template <int ALGO>
-__global__ void __launch_bounds__(kGatherThreads) k_gather_heavy(Params p) {
+// Asynchronous global -> shared copies (cp.async): the copies of one group land together and are
+// waited for with cp.async.wait_group, so a CTA keeps several chunks of bins and destination lists in
+// flight while it reduces the current one.
+__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// waits until at most n of this thread's most recent groups are still in flight (n < kPcMaxSlots)
+__device__ __forceinline__ void cp_async_wait_n(uint32_t n) {
+    switch (n) {
+        case 0: cp_async_wait<0>(); break;
+        case 1: cp_async_wait<1>(); break;
+        case 2: cp_async_wait<2>(); break;
+        case 3: cp_async_wait<3>(); break;
+        case 4: cp_async_wait<4>(); break;
+        case 5: cp_async_wait<5>(); break;
+        case 6: cp_async_wait<6>(); break;
+        default: cp_async_wait<7>(); break;
+    }
+}
+
+// --- mbarriers (block value buffers of k_gather_pc) ---------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(bar)) : "memory");
+}
+// arrives once this thread's earlier cp.async copies have landed (counts against the init count)
+__device__ __forceinline__ void mbar_arrive_cp_async(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the completion of the barrier phase with the given parity, at most kPcSpinLimit tries;
+// gives up early when another warp has raised *abort, and raises it (with the run's error flag) when
+// its own tries run out.  Returns false when the caller must stop.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort, uint32_t *err) {
+    for (uint32_t it = 0; it < kPcSpinLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+    }
+    *abort = 1;
+    atomicOr(err, 1u);
+    return false;
+}
+
+// Position in one warp's entry stream through a PC gather task: block i (relative to the
+// task's first block), next entry s.  sp[i * (kPcWarps + 1) + w] .. [.. + w + 1] bound warp w's entries in
+// block i; blocks where the warp has none are skipped.
+struct PcCursor {
+    uint32_t i, s;
+};
+__device__ __forceinline__ void pc_skip_empty(const uint32_t *sp, uint32_t nb, int w, PcCursor &c) {
+    while (c.i < nb && c.s >= sp[c.i * (kPcWarps + 1) + w + 1]) {
+        ++c.i;
+        if (c.i < nb) c.s = sp[c.i * (kPcWarps + 1) + w];
+    }
+}
+// A round's entries [s, e) are copied as the aligned words [s & ~3, e rounded up to 4), at most C.
+template <uint32_t C>
+__device__ __forceinline__ uint32_t pc_round_end(const uint32_t *sp, int w, const PcCursor &c) {
+    return (uint32_t)min((uint64_t)(c.s & ~3u) + C, (uint64_t)sp[c.i * (kPcWarps + 1) + w + 1]);
+}
+
+// Serial fold of one lane's K entries (round positions j0 .. j0+K-1), in batches of 8: the batch's
+// message values are loaded first (independent shared loads), runs of equal destination are then found
+// in registers, and the complete inner runs are folded into acc with batched read-modify-writes (inner
+// runs of a lane have distinct destinations, and no other lane or warp touches them).  CHECK selects the
+// bounds tests of the lanes at the round's edges: positions before off repeat the first entry's
+// destination with the identity, positions from R on take the sentinel destination.
+template <int ALGO, bool CHECK>
+__device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt, uint32_t j0, uint32_t off,
+                                        uint32_t R, const uint32_t *stage, uint32_t *acc, uint32_t &fd,
+                                        uint32_t &head, uint32_t &run_d, uint32_t &run_v, bool &in_head) {
     using O = Op<ALGO>;
-    const int lane = threadIdx.x & 31;
-    const uint32_t wglobal = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t sg = wglobal; sg < p.nseg; sg += nwarps) {
-        const uint4 s = p.hseg[sg];
-        if (p.gflag_pc[s.x >> p.shift] != p.epoch) continue;
-        uint32_t acc = O::identity();
-        constexpr int U = 4;
-        for (uint32_t j0 = s.y; j0 < s.z; j0 += 32 * U) {
-            uint32_t idx[U];
+    constexpr uint32_t K = PcShape<ALGO>::K;
+    uint32_t lead = 0;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                uint32_t j = j0 + u * 32 + lane;
-                idx[u] = j < s.z ? p.hidx[j] : kSent;
-            }
+    for (uint32_t hb = 0; hb < K; hb += 8) {
+        const uint4 e0 = *reinterpret_cast<const uint4 *>(ent + j0 + hb);
+        const uint4 e1 = *reinterpret_cast<const uint4 *>(ent + j0 + hb + 4);
+        const uint32_t ee[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+        int32_t ww[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (ALGO == ALG_SSSP) {
+            const int4 w0 = *reinterpret_cast<const int4 *>(wgt + j0 + hb);
+            const int4 w1 = *reinterpret_cast<const int4 *>(wgt + j0 + hb + 4);
+            ww[0] = w0.x; ww[1] = w0.y; ww[2] = w0.z; ww[3] = w0.w;
+            ww[4] = w1.x; ww[5] = w1.y; ww[6] = w1.z; ww[7] = w1.w;
+        }
+        if (CHECK && hb == 0) {  // destination of the first entry (off <= 3)
+            const uint32_t k0 = off > j0 ? off - j0 : 0;
+            lead = (k0 == 0 ? ee[0] : k0 == 1 ? ee[1] : k0 == 2 ? ee[2] : ee[3]) >> 16;
+        }
+        uint32_t d[8], x[8];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (idx[u] != kSent) {
-                    uint32_t x = p.pdata[idx[u]];
-                    if (x != kNull)
-                        acc = O::combine(acc, O::weigh(x, (ALGO == ALG_SSSP) ? p.hw[j0 + u * 32 + lane] : 0));
-                }
+        for (int i = 0; i < 8; ++i) {
+            if (CHECK) {
+                const uint32_t j = j0 + hb + i;
+                const bool valid = j >= off && j < R;
+                d[i] = valid ? (ee[i] >> 16) : (j < off ? lead : kSent);
+                x[i] = valid ? stage[ee[i] & 0xFFFFu] : kNull;
+            } else {
+                d[i] = ee[i] >> 16;
+                x[i] = stage[ee[i] & 0xFFFFu];
             }
         }
+        bool fl[8];
+        uint32_t fk[8], fv[8];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc = O::combine(acc, __shfl_xor_sync(0xffffffffu, acc, o));
-        if (lane == 0) p.hpart[sg] = acc;
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t v = (x[i] != kNull) ? O::weigh(x[i], ww[i]) : O::identity();
+            if (hb == 0 && i == 0) {
+                fd = run_d = d[0];
+                run_v = v;
+                fl[0] = false;
+                continue;
+            }
+            const bool ch = d[i] != run_d;
+            fl[i] = ch && !in_head;
+            fk[i] = run_d;
+            fv[i] = run_v;
+            head = (ch && in_head) ? run_v : head;
+            in_head = in_head && !ch;
+            const uint32_t joined = O::combine(run_v, v);
+            run_v = ch ? v : joined;
+            run_d = d[i];
+        }
+        uint32_t old[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (fl[i]) old[i] = acc[fk[i]];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (fl[i]) acc[fk[i]] = O::combine(old[i], fv[i]);
     }
 }
 
-// largest r in [0, n] with ptr[r] <= x (ptr non-decreasing, ptr[0] <= x)
-__device__ __forceinline__ uint32_t row_of(const uint32_t *ptr, uint32_t n, uint32_t x) {
-    uint32_t lo = 0, hi = n + 1;
-    while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (ptr[mid] <= x) lo = mid; else hi = mid;
+// One warp round: positions [off, off+n) of the round buffer, sorted by destination, all inside this
+// warp's destination slice.  Lane l folds positions [l K, (l+1) K) serially; one segmented warp scan,
+// keyed by destination, joins the lanes' last runs, and a lane's first run takes the scan value of the
+// lane before it when they share the destination.  Every complete run is folded into acc directly: a
+// run cut by the round's end continues in the warp's next round, folded after this part.
+template <int ALGO>
+__device__ __forceinline__ void pc_round(const uint32_t *ent, const uint32_t *wgt, uint32_t off, uint32_t n,
+                                         const uint32_t *stage, uint32_t *acc, int lane) {
+    using O = Op<ALGO>;
+    constexpr uint32_t K = PcShape<ALGO>::K;
+    const uint32_t R = off + n;
+    const uint32_t j0 = lane * K;
+    uint32_t fd = kSent, head = O::identity(), run_d = kSent, run_v = O::identity();
+    bool in_head = true;
+    const bool edge = j0 < R && (j0 < off || j0 + K > R);
+    if (__any_sync(0xffffffffu, edge)) {
+        if (j0 < R) pc_lane<ALGO, true>(ent, wgt, j0, off, R, stage, acc, fd, head, run_d, run_v, in_head);
+    } else {
+        if (j0 < R) pc_lane<ALGO, false>(ent, wgt, j0, off, R, stage, acc, fd, head, run_d, run_v, in_head);
     }
-    return lo;
+    const bool uni = in_head;  // all K positions share one destination
+    const uint32_t ld = run_d;
+    uint32_t S = run_v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t vu = __shfl_up_sync(0xffffffffu, S, o);
+        const uint32_t du = __shfl_up_sync(0xffffffffu, ld, o);
+        if (lane >= o && du == ld) S = O::combine(vu, S);
+    }
+    const uint32_t prev_S = __shfl_up_sync(0xffffffffu, S, 1);
+    const uint32_t prev_d = __shfl_up_sync(0xffffffffu, ld, 1);
+    const uint32_t next_fd = __shfl_down_sync(0xffffffffu, fd, 1);
+    if (!uni && fd != kSent) {  // first run ends inside this lane
+        const uint32_t hv = (lane > 0 && prev_d == fd) ? O::combine(prev_S, head) : head;
+        acc[fd] = O::combine(acc[fd], hv);
+    }
+    if (ld != kSent && (lane == 31 || next_fd != ld)) acc[ld] = O::combine(acc[ld], S);  // last run ends here
 }
 
-// Gather of one (column q, destination range) task:
-//  1. PC messages of light destinations, round by round: kTile entries of the destination-sorted
-//     lists are staged in shared memory (coalesced slot loads, independent message-value loads), then
-//     every thread folds the staged values of the destinations it owns (destination r belongs to
-//     thread r mod blockDim for the whole task, so no two threads ever touch the same accumulator);
-//  2. heavy destinations take their segment partials, in segment order;
-//  3. SC pairs of the fresh SC bins of the column, each warp applying those of its destination slice;
-//  4. reInit / gather apply / filter of every destination of the range and the next frontier (Alg. 2).
+// Issues the copies of one round, entries [s, e): the destination words (and the SSSP weights) as
+// 16-byte copies of the aligned superset [s & ~3, e rounded up to 4), spread over the warp's lanes.
+template <int ALGO>
+__device__ __forceinline__ void pc_issue_round(const Params &p, uint32_t s, uint32_t e, uint32_t *ent,
+                                               uint32_t *wgt, int lane) {
+    const uint64_t a0 = s & ~3u, a1 = ((uint64_t)e + 3) & ~3ull;
+    for (uint64_t i = a0 + 4u * lane; i < a1; i += 128u) {
+        cp_async16(ent + (i - a0), p.pe + i);
+        if (ALGO == ALG_SSSP) cp_async16(wgt + (i - a0), p.pw + i);
+    }
+}
+
+// Issues the copies of a block's message values into a value buffer: the block's bin runs (row-major
+// source offset, length, offset in the block) are dealt to the warps round-robin, each run copied by a
+// warp's lanes as coalesced 4-byte asynchronous copies; every thread then arrives on the buffer's "full"
+// mbarrier once its own copies have landed.
+__device__ __forceinline__ void pc_issue_values(const Params &p, uint32_t r0, uint32_t r1, uint32_t *st,
+                                                uint64_t *full, int lane, int wid) {
+    for (uint32_t rb = r0 + wid; rb < r1; rb += 32u * kPcWarps) {
+        const uint32_t rr = rb + (uint32_t)lane * kPcWarps;
+        const uint4 run = rr < r1 ? p.pc_runs[rr] : make_uint4(0, 0, 0, 0);
+        const uint32_t nr = min(32u, (r1 - rb + kPcWarps - 1) / kPcWarps);
+        for (uint32_t j = 0; j < nr; ++j) {
+            const uint32_t x = __shfl_sync(0xffffffffu, run.x, j);
+            const uint32_t len = __shfl_sync(0xffffffffu, run.y, j);
+            const uint32_t z = __shfl_sync(0xffffffffu, run.z, j);
+            for (uint32_t k = lane; k < len; k += 32) cp_async4(st + z + k, p.pdata + x + k);
+        }
+    }
+    mbar_arrive_cp_async(full);
+}
+
+// PC part of the gather (Alg. 2 gather over the PC bins, Sec. 3.1.2): one CTA per task (a range of
+// consecutive entries of column q's blocks), one task at a time per CTA, largest tasks first.
+//  * A block's message values are copied from the data bins into one of two shared buffers by coalesced
+//    asynchronous copies of its bin runs (the bins are read in order, as the paper's gather streams
+//    bin[:][q]), issued by all warps while the previous block is being reduced; a "full" mbarrier
+//    (bounded wait) tells when they have landed.
+//  * Within a block, warp w takes the w-th of 16 entry ranges of about equal size, cut at destination
+//    boundaries when the graph is built, so no two warps touch one destination of the block.  Each warp
+//    streams its entries through its own ring of asynchronous copies, several rounds ahead (across block
+//    boundaries), and folds them into the shared column accumulator with lane-serial runs and a
+//    segmented warp scan: random accesses touch shared memory only.  One CTA barrier per block separates
+//    the blocks' slices and frees the block's value buffer.
+// The accumulator stays in shared memory for the whole task; a column split over several tasks writes
+// one partial vector per task.  When a bounded wait runs out, the run's error flag is raised and all
+// warps leave.
+template <int ALGO>
+__global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
+    using O = Op<ALGO>;
+    constexpr uint32_t C = PcShape<ALGO>::kRound, kSlotWords = PcShape<ALGO>::kSlotWords;
+    constexpr uint32_t kSp = kPcWarps + 1;
+    extern __shared__ __align__(16) uint32_t s_pc_dyn[];
+    uint32_t *acc = s_pc_dyn;                     // P values of the column
+    uint32_t *stage = s_pc_dyn + p.P;             // 2 x kPcBlock message values
+    uint32_t *rings = stage + 2 * kPcBlock;       // kPcWarps x pc_slots rounds (entries, then SSSP weights)
+    __shared__ __align__(8) uint64_t s_full[2];
+    __shared__ uint32_t s_state, s_abort;
+    __shared__ uint4 s_tk;
+    __shared__ uint2 s_rng;
+    __shared__ uint32_t s_tsp;
+    __shared__ uint32_t s_run[kPcTaskBlocks + 1];
+    __shared__ uint32_t s_sp[kPcTaskBlocks * kSp];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t ns = p.pc_slots;
+    uint32_t *ring = rings + (uint32_t)wid * ns * kSlotWords;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_full[0], kPcThreads);
+        mbar_init(&s_full[1], kPcThreads);
+        s_abort = 0;
+    }
+    uint32_t gb = 0;  // blocks this CTA has passed through (buffer = gb & 1, use = gb >> 1)
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t t = atomicAdd(&p.counters[5], 1u);
+            uint32_t state = 2;  // 0 idle column, 1 work, 2 no tasks left (or abort)
+            if (t < p.npct && !s_abort) {
+                const uint4 tk = p.pc_task[t];  // column, first block, end block, partial slot
+                state = p.gflag_pc[tk.x] == p.epoch ? 1u : 0u;
+                s_tk = tk;
+                s_rng = p.pc_rng[t];
+                s_tsp = p.pc_tsp[t];
+            }
+            s_state = state;
+        }
+        __syncthreads();
+        const uint32_t state = s_state;
+        const uint4 tk = s_tk;
+        if (state == 2) break;
+        if (state == 0) {
+            __syncthreads();
+            continue;
+        }
+        const uint32_t nb = tk.z - tk.y;
+        if (threadIdx.x <= nb) s_run[threadIdx.x] = p.pc_blk_run[tk.y + threadIdx.x];
+        for (uint32_t i = threadIdx.x; i < nb * kSp; i += kPcThreads) s_sp[i] = p.pc_wsp[(uint64_t)s_tsp * kSp + i];
+        const uint32_t gq = tk.x << p.shift;
+        const uint32_t wq = min(p.P, p.V - gq);
+        for (uint32_t i = threadIdx.x; i < wq; i += kPcThreads) acc[i] = O::identity();
+        __syncthreads();
+        pc_issue_values(p, s_run[0], s_run[1], stage + (gb & 1) * kPcBlock, &s_full[gb & 1], lane, wid);
+        PcCursor pc{0, s_sp[wid]};
+        pc_skip_empty(s_sp, nb, wid, pc);
+        PcCursor cc = pc;
+        uint32_t issued = 0, done = 0;
+        bool ok = true;
+        for (uint32_t i = 0; i < nb; ++i) {
+            const uint32_t g = gb + i, buf = g & 1, use = g >> 1;
+            if (i + 1 < nb)  // the next block's values go to the other buffer, freed by the last barrier
+                pc_issue_values(p, s_run[i + 1], s_run[i + 2], stage + (buf ^ 1) * kPcBlock, &s_full[buf ^ 1], lane,
+                                wid);
+            if (ok && cc.i == i && !mbar_wait(&s_full[buf], use & 1, &s_abort, &p.ctrl->error)) ok = false;
+            while (ok && cc.i == i) {
+                while (issued - done < ns && pc.i < nb) {
+                    const uint32_t e = pc_round_end<C>(s_sp, wid, pc);
+                    uint32_t *slot = ring + (issued % ns) * kSlotWords;
+                    pc_issue_round<ALGO>(p, pc.s, e, slot, slot + C, lane);
+                    cp_async_commit();
+                    ++issued;
+                    pc.s = e;
+                    pc_skip_empty(s_sp, nb, wid, pc);
+                }
+                cp_async_wait_n(issued - done - 1);
+                __syncwarp();
+                const uint32_t e = pc_round_end<C>(s_sp, wid, cc);
+                const uint32_t *slot = ring + (done % ns) * kSlotWords;
+                pc_round<ALGO>(slot, slot + C, cc.s & 3u, e - cc.s, stage + buf * kPcBlock, acc, lane);
+                __syncwarp();
+                ++done;
+                cc.s = e;
+                pc_skip_empty(s_sp, nb, wid, cc);
+            }
+            // every block of a task has entries, so some warp has waited for the values before this
+            // barrier, after which the buffer may be refilled
+            __syncthreads();
+        }
+        cp_async_wait<0>();
+        gb += nb;
+        __syncthreads();
+        if (s_abort) break;
+        uint32_t *out = (tk.w == kNull) ? p.pc_sum + gq : p.pc_part + (uint64_t)tk.w * p.P;
+        for (uint32_t i = threadIdx.x; i < wq; i += kPcThreads) out[i] = acc[i];
+    }
+    cp_async_wait<0>();
+}
+
+// Gather of one (column q, destination range) task, after k_gather_pc:
+//  1. PC messages: light destinations take pc_sum, heavy destinations combine their segment results in
+//     segment order (only when some partition sent PC messages to the column this iteration);
+//  2. SC pairs of the task's fresh SC bins, each warp applying those of its destination slice;
+//  3. reInit / gather apply / filter of every destination of the range and the next frontier (Alg. 2).
 template <int ALGO>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
     using O = Op<ALGO>;
     __shared__ uint32_t s_acc[kGatherWidth];
-    __shared__ uint32_t s_ptr[kGatherWidth + 1];
-    __shared__ uint32_t s_val[kTile];
     __shared__ uint32_t s_stage[kGatherWarps][32];
     __shared__ uint32_t s_task;
     __shared__ uint32_t s_va[kGatherWarps];
@@ -656,50 +959,24 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
         const uint32_t gq = q << p.shift;
         const uint32_t gbase = gq + gt.d0;
         const uint32_t wv = min(width, p.V - gbase);  // destinations that exist
-        for (uint32_t i = tid; i < width; i += nthr) s_acc[i] = O::identity();
-
         if (p.gflag_pc[q] == p.epoch) {
-            for (uint32_t i = tid; i <= wv; i += nthr) s_ptr[i] = p.cptr[gbase + i];
-            __syncthreads();
-            const uint32_t e0 = s_ptr[0], n = s_ptr[wv] - e0;
-            for (uint32_t tb = 0; tb < n; tb += kTile) {
-                const uint32_t tn = min((uint32_t)kTile, n - tb);
-                constexpr int U = kTile / kGatherThreads;
-                uint32_t idx[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    uint32_t j = tid + u * kGatherThreads;
-                    idx[u] = j < tn ? p.cidx[e0 + tb + j] : kSent;
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    uint32_t j = tid + u * kGatherThreads;
-                    if (idx[u] != kSent) {
-                        uint32_t x = p.pdata[idx[u]];
-                        s_val[j] = (x == kNull) ? O::identity()
-                                                : O::weigh(x, (ALGO == ALG_SSSP) ? p.cw[e0 + tb + j] : 0);
-                    }
-                }
-                __syncthreads();
-                // rows meeting [tb, tb + tn): the row holding entry tb up to the row holding tb + tn - 1
-                const uint32_t r_lo = row_of(s_ptr, wv, e0 + tb), r_hi = row_of(s_ptr, wv, e0 + tb + tn - 1);
-                for (uint32_t r = r_lo + ((tid + nthr - (r_lo % nthr)) % nthr); r <= r_hi; r += nthr) {
-                    uint32_t a = max(s_ptr[r], e0 + tb), b = min(s_ptr[r + 1], e0 + tb + tn);
-                    if (a < b) {
-                        uint32_t acc = s_acc[r];
-                        for (uint32_t j = a; j < b; ++j) acc = O::combine(acc, s_val[j - e0 - tb]);
-                        s_acc[r] = acc;
-                    }
-                }
-                __syncthreads();
-            }
-            // heavy destinations of this range: their segment partials, in segment order
-            for (uint32_t h = p.task_hptr[t] + tid; h < p.task_hptr[t + 1]; h += nthr) {
-                uint4 hd = p.task_heavy[h];
+            // the column's PC result: one vector (pc_sum), several partial vectors merged in task
+            // order, or none (no PC in-edges)
+            const uint32_t nt = p.col_ntask[q], part0 = p.col_part0[q];
+            for (uint32_t i = tid; i < width; i += nthr) {
                 uint32_t r = O::identity();
-                for (uint32_t sgi = 0; sgi < hd.z; ++sgi) r = O::combine(r, p.hpart[hd.y + sgi]);
-                s_acc[hd.x] = r;
+                if (i < wv) {
+                    if (nt == 1) {
+                        r = p.pc_sum[gbase + i];
+                    } else {
+                        for (uint32_t j = 0; j < nt; ++j)
+                            r = O::combine(r, p.pc_part[(uint64_t)(part0 + j) * p.P + gt.d0 + i]);
+                    }
+                }
+                s_acc[i] = r;
             }
+        } else {
+            for (uint32_t i = tid; i < width; i += nthr) s_acc[i] = O::identity();
         }
         __syncthreads();
 
@@ -883,7 +1160,7 @@ struct RunBuffers {
     double *t_res = nullptr;
     uint8_t *mode = nullptr, *action = nullptr;
     uint32_t *gflag = nullptr, *gflag_pc = nullptr, *sc_list = nullptr, *counters = nullptr;
-    uint32_t *task_sc_cnt = nullptr, *task_sc_list = nullptr;
+    uint32_t *task_sc_cnt = nullptr, *task_sc_list = nullptr, *pc_sum = nullptr;
     Control *ctrl = nullptr, *h_ctrl = nullptr;
     // LOG_BOTH only (allocated on first use)
     uint32_t *shadow = nullptr, *all_list = nullptr, *part_va = nullptr;
@@ -894,7 +1171,7 @@ struct RunBuffers {
 static void release_runbufs(RunBuffers *rb) {
     void *ptrs[] = {rb->val, rb->lvl, rb->sval, rb->bits, rb->t_va, rb->t_stamp, rb->t_ea, rb->t_res,
                     rb->mode, rb->action, rb->gflag, rb->gflag_pc, rb->sc_list, rb->counters,
-                    rb->ctrl, rb->task_sc_cnt, rb->task_sc_list, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_ga,
+                    rb->ctrl, rb->task_sc_cnt, rb->task_sc_list, rb->pc_sum, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_ga,
                     rb->feat};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -924,6 +1201,7 @@ static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
     A(&rb->sc_list, g->k);
     A(&rb->counters, 8);
     A(&rb->task_sc_cnt, g->ngt);
+    A(&rb->pc_sum, g->V);
     A(&rb->task_sc_list, g->nsub);
     A(&rb->ctrl, 1);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&rb->h_ctrl, sizeof(Control));
@@ -1011,12 +1289,12 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     p.rowptr = g->rowptr; p.col = g->col; p.w = g->w; p.esub = g->esub;
     p.row_bin = g->row_bin; p.bin_q = g->bin_q; p.col_bin = g->col_bin; p.col_bins = g->col_bins;
     p.png = g->png; p.pdata = g->pdata; p.row_png = g->row_png;
-    p.cptr = g->cptr; p.cidx = g->cidx; p.cw = g->cw;
+    p.pc_runs = g->pc_runs; p.pc_task = g->pc_task; p.pc_rng = g->pc_rng; p.pc_wsp = g->pc_wsp; p.pc_tsp = g->pc_tsp; p.pc_blk_run = g->pc_blk_run; p.pc_blk_ent = g->pc_blk_ent;
     p.scpair = g->scpair; p.sccnt = g->sccnt;
     p.sub_cap = g->sub_cap; p.sub_task = g->sub_task; p.row_sub = g->row_sub; p.task_sub_ptr = g->task_sub_ptr;
     p.task_sc_cnt = rb->task_sc_cnt; p.task_sc_list = rb->task_sc_list;
-    p.hidx = g->hidx; p.hw = g->hw; p.hseg = g->hseg; p.hpart = g->hpart; p.nseg = g->nseg;
-    p.task_hptr = g->task_hptr; p.task_heavy = g->task_heavy;
+    p.col_ntask = g->col_ntask; p.col_part0 = g->col_part0; p.pe = g->pe; p.pw = g->pw; p.pc_part = g->pc_part;
+    p.npct = g->npct; p.pc_sum = rb->pc_sum;
     p.Ep = g->Ep; p.npng_p = g->npng_p;
     p.gtask = g->gtask; p.ngt = g->ngt; p.col_task = g->col_task;
     p.stask = g->stask; p.nst = g->nst; p.pc_state = g->pc_state;
@@ -1056,13 +1334,31 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
 
     int grid_pc = 0, grid_sc = 0, grid_ga = 0;
     const size_t sc_smem = sizeof(uint32_t) * std::max<uint32_t>(g->max_row_subs, 1);
-    if (sc_smem > 48 * 1024)
-        GPOP_CUDA_TRY(cudaFuncSetAttribute(k_scatter_sc<ALGO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)sc_smem));
+    GPOP_CUDA_TRY(cudaFuncSetAttribute(k_scatter_sc<ALGO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sc_smem));
     grid_pc = persistent_grid(k_scatter_pc, kScatterThreads, 0, g->num_sms);
     grid_sc = persistent_grid(k_scatter_sc<ALGO>, kScatterThreads, sc_smem, g->num_sms);
     grid_ga = persistent_grid(k_gather<ALGO>, kGatherThreads, 0, g->num_sms);
-    const int grid_gh = persistent_grid(k_gather_heavy<ALGO>, kGatherThreads, 0, g->num_sms);
+    // k_gather_pc: column accumulator, two block value buffers and as many entry-chunk slots as the
+    // opt-in shared memory holds (at most kPcMaxSlots); dynamic shared memory is opted in explicitly
+    size_t gpc_smem = 0;
+    {
+        cudaFuncAttributes fa;
+        GPOP_CUDA_TRY(cudaFuncGetAttributes(&fa, k_gather_pc<ALGO>));
+        int optin = 0, dev = 0;
+        GPOP_CUDA_TRY(cudaGetDevice(&dev));
+        GPOP_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        const size_t fixed = sizeof(uint32_t) * ((size_t)g->P + 2 * kPcBlock);
+        const size_t slot = sizeof(uint32_t) * PcShape<ALGO>::kSlotWords * kPcWarps;
+        const size_t avail = (size_t)optin > fixed + fa.sharedSizeBytes ? optin - fixed - fa.sharedSizeBytes : 0;
+        const uint32_t ns = (uint32_t)std::min<size_t>(kPcMaxSlots, avail / slot);
+        if (ns < 2) return fail(GPOP_ERR_INVALID_ARG, "partition size too large for the PC gather's shared memory");
+        p.pc_slots = ns;
+        gpc_smem = fixed + ns * slot;
+        GPOP_CUDA_TRY(cudaFuncSetAttribute(k_gather_pc<ALGO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)gpc_smem));
+    }
+    const int grid_gh = persistent_grid(k_gather_pc<ALGO>, kPcThreads, gpc_smem, g->num_sms);
 
     // initial frontier (Alg. 4 driver: loadFrontier and initial values)
     p.epoch = ++g->epoch;
@@ -1112,6 +1408,10 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("plan: ") + cudaGetErrorString(ce)); break; }
         if (prof) resolve();
         const Control c = *rb->h_ctrl;
+        if (c.error) {
+            status = fail(GPOP_ERR_TIMEOUT, "PC gather: a bounded mbarrier wait ran out");
+            break;
+        }
         st.residual = c.residual;
         if (c.done) {
             st.converged = (c.frontier_v == 0) || ((ALGO == ALG_PR || ALGO == ALG_PPR) && iter > 0 && c.residual < o->tol_l1);
@@ -1149,7 +1449,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         pg.t_task = p.log_both ? rb->t_ga : nullptr;
         if (c.n_pc + c.n_null > 0) timed(1, [&] { k_scatter_pc<<<grid_pc, kScatterThreads, 0, s>>>(p); });
         if (c.n_sc > 0) timed(2, [&] { k_scatter_sc<ALGO><<<grid_sc, kScatterThreads, sc_smem, s>>>(ps); });
-        if (c.n_pc > 0 && g->nseg > 0) timed(4, [&] { k_gather_heavy<ALGO><<<grid_gh, kGatherThreads, 0, s>>>(p); });
+        if (c.n_pc > 0) timed(4, [&] { k_gather_pc<ALGO><<<grid_gh, kPcThreads, gpc_smem, s>>>(p); });
         timed(3, [&] { k_gather<ALGO><<<grid_ga, kGatherThreads, 0, s>>>(pg); });
         ce = cudaGetLastError();
         if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(ce)); break; }

@@ -23,8 +23,10 @@ constexpr uint32_t kGatherWidth = 4096;  // max destinations per gather task (sm
 constexpr uint32_t kGatherEntries = 32768;  // target in-entries per gather task
 constexpr uint32_t kScatterChunk = 16384;   // PNG entries per static PC scatter task
 constexpr uint32_t kMaxRowBins = 40960;     // SC scatter keeps one cursor per row bin in smem
-constexpr uint32_t kHeavy = 256;            // destinations with more in-entries are reduced in segments
-constexpr uint32_t kHeavySeg = 2048;        // in-entries per heavy segment (one warp each)
+constexpr uint32_t kPcBlock = 8192;         // messages staged in shared memory per PC gather block
+constexpr uint32_t kPcTaskBlocks = 8;       // at most this many blocks per PC gather task
+constexpr uint32_t kPcGatherWarps = 16;     // consumer warps of the PC gather, one destination slice each
+constexpr uint32_t kPcTaskMinEntries = 65536;  // PC gather tasks hold about max(this, E / (8 SMs)) entries
 
 enum Mode : uint8_t { kModeNone = 0, kModeSC = 1, kModePC = 2 };
 enum Action : uint8_t { kActSkip = 0, kActPC = 1, kActNull = 2 };
@@ -76,22 +78,22 @@ struct Graph {
     uint32_t *pdata = nullptr;    // npng_pad: message values
     uint32_t *row_png = nullptr;  // k+1: padded row offsets
 
-    // destination lists of PC messages, grouped per destination (column CSC)
-    uint32_t *cptr = nullptr;     // V+1
-    uint32_t *cidx = nullptr;     // E: PNG slot of the message that carries the edge
-    int32_t *cw = nullptr;        // E or null
-
-    // heavy destinations (more than kHeavy in-entries): entries in destination order, cut into
-    // segments (destination, begin, end) whose partial results the owning gather task merges
-    uint32_t *hidx = nullptr;     // heavy entries: PNG slot
-    int32_t *hw = nullptr;        // heavy entries: weight or null
-    uint4 *hseg = nullptr;        // nseg segments
-    uint32_t *hpart = nullptr;    // nseg partial results
-    uint32_t nseg = 0;
-    uint64_t nheavy = 0;          // heavy in-entries
-    uint32_t *task_hptr = nullptr;  // ngt+1 offsets into task_heavy
-    uint4 *task_heavy = nullptr;    // (local destination, first segment, segment count)
-    std::vector<uint32_t> h_hv, h_hseg0;  // host: heavy destinations and their first segment
+    // PC gather blocks: each column's message sequence (bins (p, q), p ascending) cut into blocks of
+    // kPcBlock messages, staged by runs; destination lists as (local destination << 16 | index in block)
+    uint4 *pc_runs = nullptr;     // (row-major source slot, length, offset in block, block)
+    uint32_t *pc_blk_run = nullptr;  // npcb+1: runs of each block
+    uint32_t *pc_blk_ent = nullptr;  // npcb+1: entries of each block
+    uint4 *pc_task = nullptr;     // npct: (column, first block, end block, partial slot or kNull), largest first
+    uint2 *pc_rng = nullptr;      // npct: entry range [begin, end) of the task within its blocks
+    uint32_t *pc_tsp = nullptr;   // npct: first row of the task's blocks in pc_wsp
+    uint32_t *pc_wsp = nullptr;   // per task block: kPcGatherWarps+1 entry offsets splitting its entries by
+                                  // the column's destination slices (one slice per gather warp)
+    uint32_t *col_ntask = nullptr;   // k: PC gather tasks of the column (0 = no PC in-edges)
+    uint32_t *col_part0 = nullptr;   // k: first partial slot of a multi-task column
+    uint32_t *pc_part = nullptr;  // npart x P partial results
+    uint32_t *pe = nullptr;       // E: entries, sorted by (block, destination, index)
+    int32_t *pw = nullptr;        // E or null: weights aligned with pe
+    uint32_t npcb = 0, npct = 0, npart = 0;
 
     // SC bins, one per (source partition p, gather task t) with edges p -> t
     uint2 *scpair = nullptr;      // E: (local destination, value), regions of capacity edges(p, t)

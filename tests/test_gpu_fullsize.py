@@ -1,0 +1,95 @@
+"""Parity at full workload sizes, in the launch configuration bench.py times (partition size 16384).
+
+RMAT scale 22 (4.2M vertices, ~65M edges): BFS levels and parents, SSSP distances (weights 1..255) and
+CC labels (symmetrised graph) bit-exact against the full oracle.  RMAT scale 24 (16.8M vertices, ~263M
+edges): PageRank 10 iterations against the FP64 oracle (L-inf relative <= 1e-5), and the run to an L1
+residual below 1e-9 checked on sampled vertices against the fixed-point equation of Alg. 6 evaluated in
+FP64 from the GPU's own ranks.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P_BENCH = 16384
+
+
+@pytest.fixture(scope="module")
+def gp():
+    import paper_1806_08092_gb300 as gp
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gp.build()
+    return gp
+
+
+@pytest.fixture(scope="module")
+def rmat22():
+    return gg.rmat(22).with_weights()
+
+
+def test_rmat22_bfs_sssp_exact(gp, rmat22):
+    g = rmat22
+    G = gp.Graph.from_csr(g.row_ptr, g.col, g.weights, partition_size=P_BENCH)
+    for root in gg.roots(g, 2):
+        root = int(root)
+        level, parent = O.bfs(g, root)
+        r = G.run("bfs", source=root)
+        assert np.array_equal(r.values.cpu().numpy(), level)
+        assert np.array_equal(r.parent.cpu().numpy(), parent)
+        d = O.sssp(g, root)
+        assert int(d[d != O.U64_INF].max()) < 2**32 - 1
+        dd = d.copy()
+        dd[d == O.U64_INF] = O.U32_INF
+        assert np.array_equal(G.run("sssp", source=root).values.cpu().numpy(), dd.astype(np.uint32))
+    G.close()
+
+
+def test_rmat22_cc_exact(gp, rmat22):
+    gs = gg.symmetrized(rmat22)
+    G = gp.Graph.from_csr(gs.row_ptr, gs.col, partition_size=P_BENCH)
+    assert np.array_equal(G.run("cc").values.cpu().numpy(), O.cc(gs))
+    G.close()
+
+
+@pytest.fixture(scope="module")
+def rmat24(gp):
+    g = gg.rmat(24)
+    G = gp.Graph.from_csr(g.row_ptr, g.col, partition_size=P_BENCH)
+    yield g, G
+    G.close()
+
+
+def test_rmat24_pagerank_10_iterations(rmat24):
+    g, G = rmat24
+    ref, _, _ = O.pagerank(g, 0.85, max_iters=10)
+    x = G.run("pagerank", max_iters=10).values.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(x - ref) / ref) <= 1e-5
+
+
+def test_rmat24_pagerank_converged_fixed_point_sampled(rmat24):
+    g, G = rmat24
+    r = G.run("pagerank", max_iters=300, tol=1e-9)
+    assert r.stats["converged"] == 1 and r.stats["residual"] < 1e-9
+    x = r.values.cpu().numpy().astype(np.float64)
+    n = g.num_vertices
+    deg = np.diff(g.row_ptr).astype(np.float64)
+    # sampled destinations: the 64 largest in-degrees plus 4000 uniform draws
+    indeg = np.bincount(g.col, minlength=n)
+    rng = np.random.default_rng(24)
+    sample = np.unique(np.concatenate([np.argsort(indeg)[-64:], rng.integers(0, n, 4000)]))
+    want = np.zeros(n, dtype=bool)
+    want[sample] = True
+    src = g.src()
+    m = want[g.col]
+    y = np.zeros(n)
+    np.add.at(y, g.col[m].astype(np.int64), x[src[m]] / deg[src[m]])
+    fixed = (1 - 0.85) / n + 0.85 * y[sample]
+    assert np.max(np.abs(x[sample] - fixed) / fixed) <= 1e-5
+    # rank mass: sum x = (1-d) + d (sum x - sink mass) at the fixed point
+    sink = deg == 0
+    assert abs(x.sum() - ((1 - 0.85) + 0.85 * (x.sum() - x[sink].sum()))) <= 1e-5 * x.sum()

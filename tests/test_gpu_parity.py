@@ -124,6 +124,41 @@ def test_modes_and_frontiers_match_tier2(scale, P):
     assert np.array_equal(r.modes, t2.modes)
 
 
+def _dense_column_graph():
+    # every one of 16384 sources sends 16 edges into partition 0 (P = 1024): two message blocks of
+    # 131072 entries each, so each block is split over several PC gather tasks
+    n, P, fan = 16384, 1024, 16
+    u = np.repeat(np.arange(n, dtype=np.int64), fan)
+    j = np.tile(np.arange(fan, dtype=np.int64), n)
+    v = (u * 37 + j * 61) % P
+    return gg.multigraph(n, u.tolist(), v.tolist()).with_weights(), P
+
+
+@pytest.mark.parametrize("case", ["rmat18_p8192", "rmat18_p16384", "dense_column"])
+def test_large_partitions_multi_task_columns(case):
+    # columns split over several PC gather tasks (partial vectors), blocks of several entry chunks,
+    # blocks whose entries are split over tasks, and at P = 16384 the largest accumulator
+    if case == "dense_column":
+        g, P = _dense_column_graph()
+    else:
+        g, P = gg.rmat(18).with_weights(), int(case.split("_p")[1])
+    Gd = G(g, P)
+    assert Gd.info()["num_pc_partials"] > 0
+    ref, _, _ = O.pagerank(g, 0.85, max_iters=5)
+    for pol in ("analytic", "force_pc"):
+        r = Gd.run("pagerank", max_iters=5, mode=pol)
+        assert pr_err(r.values.cpu().numpy(), ref) <= PR_TOL, pol
+    root = int(gg.roots(g, 1)[0])
+    level, parent = O.bfs(g, root)
+    dist = u64_to_u32(O.sssp(g, root))
+    for pol in ("analytic", "force_pc"):
+        r = Gd.run("bfs", source=root, mode=pol)
+        assert np.array_equal(r.values.cpu().numpy(), level), pol
+        assert np.array_equal(r.parent.cpu().numpy(), parent), pol
+        r = Gd.run("sssp", source=root, mode=pol)
+        assert np.array_equal(r.values.cpu().numpy(), dist), pol
+
+
 def test_pagerank_rmat16_p1024_10_iterations():
     # PageRank, 10 iterations, d = 0.85, RMAT scale 16, partitions of 1024 vertices
     g = gg.rmat(16)
@@ -186,6 +221,9 @@ def test_errors_are_reported():
     bad[3] = g.num_vertices + 5
     with pytest.raises(gp.GpopError, match="INVALID_ARG"):
         gp.Graph.from_csr(g.row_ptr, bad, partition_size=32)
+    for P in (16, 48, 32768):  # not a power of two in [32, 16384]
+        with pytest.raises(gp.GpopError, match="partition_size"):
+            gp.Graph.from_csr(g.row_ptr, g.col, partition_size=P)
     Gd = G(g, 32)
     with pytest.raises(gp.GpopError, match="weighted"):
         Gd.run("sssp", source=0)
