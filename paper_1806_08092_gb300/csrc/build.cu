@@ -25,8 +25,8 @@ gpop_status fail(gpop_status st, const std::string &msg) {
 void free_graph(Graph *g) {
     release_run_state(g);
     void *ptrs[] = {g->rowptr, g->col, g->w, g->esub, g->row_bin, g->bin_q, g->col_bin,
-                    g->col_bins, g->png, g->pdata, g->row_png, g->pc_runs, g->pc_blk_run, g->pc_blk_ent,
-                    g->pc_task, g->pc_rng, g->pc_tsp, g->pc_wsp, g->col_ntask, g->col_part0, g->pc_part, g->pe, g->pw,
+                    g->col_bins, g->png, g->pdata, g->row_png, g->pc_runs, g->pc_blk_run, g->pc_blk_nval, g->pc_blk_ent,
+                    g->pc_task, g->pc_tsp, g->pc_wsp, g->col_ntask, g->col_part0, g->pc_part, g->pe, g->pw,
                     g->scpair, g->sccnt, g->sub_cap, g->sub_task, g->row_sub, g->task_sub_ptr,
                     g->Ep, g->npng_p, g->nbins_p, g->gtask, g->col_task, g->stask, g->pc_state};
     for (void *p : ptrs)
@@ -145,26 +145,46 @@ __global__ void k_pad8(uint32_t k, const uint32_t *m, uint32_t *mp) {
         mp[p] = (m[p] + kPngAlign - 1) / kPngAlign * kPngAlign;
 }
 
-// places every message in its padded PNG slot and records, per head edge, its slot and bin
-__global__ void k_place_msgs(uint64_t nmsg, uint32_t shift, uint32_t k, const uint64_t *skey,
-                             const uint32_t *shead, const uint32_t *binscan, const uint32_t *row_msg,
-                             const uint32_t *row_png, uint16_t *png, uint32_t *slot_of_head,
-                             uint32_t *bin_of_head, uint32_t *bin_q, uint32_t *bin_j0, uint32_t *bin_slot0) {
+// first message (sorted order), destination partition and source partition of every bin
+__global__ void k_bin_starts(uint64_t nmsg, uint32_t shift, uint32_t k, const uint64_t *skey, const uint32_t *binscan,
+                             uint32_t *bin_j0, uint32_t *bin_q, uint32_t *bin_p) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nmsg; j += stride) {
-        uint64_t key = skey[j];
-        uint64_t pk = key >> shift;
-        uint32_t p = (uint32_t)(pk / k), q = (uint32_t)(pk % k);
-        uint32_t slot = (uint32_t)j - row_msg[p] + row_png[p];
-        png[slot] = (uint16_t)(key & ((1u << shift) - 1));
-        uint32_t b = binscan[j] - 1;  // inclusive scan of new-bin flags
+        uint64_t pk = skey[j] >> shift;
+        if (j == 0 || (skey[j - 1] >> shift) != pk) {
+            uint32_t b = binscan[j] - 1;
+            bin_j0[b] = (uint32_t)j;
+            bin_q[b] = (uint32_t)(pk % k);
+            bin_p[b] = (uint32_t)(pk / k);
+        }
+    }
+}
+
+// every bin occupies its message count rounded up to kBinAlign slots of its PNG row (so that each bin,
+// and each block of a column's message sequence, starts 16-byte aligned); per row, the padded length
+__global__ void k_bin_pad(uint32_t nb, const uint32_t *bin_j0, const uint32_t *bin_p, uint32_t *cnt4,
+                          uint32_t *row_len4) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        uint32_t c = (bin_j0[b + 1] - bin_j0[b] + kBinAlign - 1) / kBinAlign * kBinAlign;
+        cnt4[b] = c;
+        atomicAdd(&row_len4[bin_p[b]], c);
+    }
+}
+
+// places every message in its PNG slot (row start + padded offset of its bin + rank in the bin) and
+// records, per head edge, its slot and bin; bin_slot0 = slot of the bin's first message
+__global__ void k_place_msgs(uint64_t nmsg, uint32_t shift, const uint64_t *skey, const uint32_t *shead,
+                             const uint32_t *binscan, const uint32_t *bin_j0, const uint32_t *bin_p,
+                             const uint32_t *binoff, const uint32_t *row_bin, const uint32_t *row_png, uint16_t *png,
+                             uint32_t *slot_of_head, uint32_t *bin_of_head, uint32_t *bin_slot0) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nmsg; j += stride) {
+        uint32_t b = binscan[j] - 1, p = bin_p[b];
+        uint32_t slot = row_png[p] + (binoff[b] - binoff[row_bin[p]]) + ((uint32_t)j - bin_j0[b]);
+        png[slot] = (uint16_t)(skey[j] & ((1u << shift) - 1));
         slot_of_head[shead[j]] = slot;
         bin_of_head[shead[j]] = b;
-        if (j == 0 || (skey[j - 1] >> shift) != pk) {
-            bin_q[b] = q;
-            bin_j0[b] = (uint32_t)j;  // first message of the bin (sorted order) and its PNG slot
-            bin_slot0[b] = slot;
-        }
+        if ((uint32_t)j == bin_j0[b]) bin_slot0[b] = slot;
     }
 }
 
@@ -225,12 +245,6 @@ __global__ void k_edge_sub(uint64_t E, uint32_t shift, const uint32_t *src, cons
     }
 }
 
-__global__ void k_indegree(uint64_t E, const uint32_t *col, uint32_t *indeg) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E; e += stride)
-        atomicAdd(&indeg[col[e]], 1u);
-}
-
 // Warp splits of the PC gather: for every task block (entries [lo, hi), sorted by destination) and w in
 // 0..kPcGatherWarps, the w-th of kPcGatherWarps ranges of about equal size: the nominal cut
 // lo + (hi - lo) w / kPcGatherWarps moved forward to the next change of destination, so that every
@@ -251,6 +265,28 @@ __global__ void k_warp_splits(uint32_t nrow, const uint32_t *lo, const uint32_t 
             }
         }
         out[i] = a;
+    }
+}
+
+// Copies each warp range [old0, old0 + len) of the destination entries to new0, padded to a multiple of
+// kPcPad with entries that repeat the range's last destination and point to the NULL value slot.
+__global__ void k_pad_entries(uint32_t nrange, const uint32_t *old0, const uint32_t *len, const uint32_t *new0,
+                              const uint32_t *pe, const int32_t *pw, uint32_t *pe2, int32_t *pw2) {
+    for (uint32_t r = blockIdx.x; r < nrange; r += gridDim.x) {
+        const uint32_t a = old0[r], L = len[r], b = new0[r];
+        const uint32_t PL = (L + kPcPad - 1) / kPcPad * kPcPad;
+        for (uint32_t i = threadIdx.x; i < PL; i += blockDim.x) {
+            uint32_t v;
+            int32_t w = 0;
+            if (i < L) {
+                v = pe[a + i];
+                if (pw) w = pw[a + i];
+            } else {
+                v = (pe[a + L - 1] & 0xFFFF0000u) | kPcPadIdx;
+            }
+            pe2[b + i] = v;
+            if (pw2) pw2[b + i] = w;
+        }
     }
 }
 
@@ -405,11 +441,10 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
     g->npng = nmsg;
 
     // 4. bins, rows, padded PNG slots
-    uint32_t *newbin, *binscan, *msgs_row, *row_msg, *msgs_row_pad;
+    uint32_t *newbin, *binscan, *msgs_row, *msgs_row_pad;
     GPOP_CUDA_TRY(t.alloc(&newbin, nmsg));
     GPOP_CUDA_TRY(t.alloc(&binscan, nmsg));
     GPOP_CUDA_TRY(t.alloc(&msgs_row, (uint64_t)k + 1));
-    GPOP_CUDA_TRY(t.alloc(&row_msg, (uint64_t)k + 1));
     GPOP_CUDA_TRY(t.alloc(&msgs_row_pad, (uint64_t)k + 1));
     GPOP_CUDA_TRY(dalloc(g, &g->nbins_p, (uint64_t)k + 1));
     GPOP_CUDA_TRY(dalloc(g, &g->npng_p, (uint64_t)k + 1));
@@ -423,39 +458,56 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
             return cub::DeviceScan::InclusiveSum(tmp, bytes, newbin, binscan, nmsg, s);
         }));
     }
-    k_pad8<<<blocks_for(k), kThreads, 0, s>>>(k, msgs_row, msgs_row_pad);
-    GPOP_CUDA_TRY(cudaMemsetAsync(msgs_row_pad + k, 0, 4, s));
     GPOP_CUDA_TRY(cudaMemsetAsync(msgs_row + k, 0, 4, s));
-    GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-        return cub::DeviceScan::ExclusiveSum(tmp, bytes, msgs_row, row_msg, (uint64_t)k + 1, s);
-    }));
-    GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-        return cub::DeviceScan::ExclusiveSum(tmp, bytes, msgs_row_pad, g->row_png, (uint64_t)k + 1, s);
-    }));
     GPOP_CUDA_TRY(cudaMemcpyAsync(g->npng_p, msgs_row, 4ull * (k + 1), cudaMemcpyDeviceToDevice, s));
     GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
         return cub::DeviceScan::ExclusiveSum(tmp, bytes, g->nbins_p, g->row_bin, (uint64_t)k + 1, s);
     }));
-    uint32_t h_npad = 0, h_nb = 0;
-    GPOP_CUDA_TRY(cudaMemcpyAsync(&h_npad, g->row_png + k, 4, cudaMemcpyDeviceToHost, s));
+    uint32_t h_nb = 0;
     GPOP_CUDA_TRY(cudaMemcpyAsync(&h_nb, g->row_bin + k, 4, cudaMemcpyDeviceToHost, s));
     GPOP_CUDA_TRY(cudaStreamSynchronize(s));
-    g->npng_pad = h_npad;
     g->nb = h_nb;
+    // bins padded to kBinAlign slots, rows to kPngAlign
+    uint32_t *bin_j0, *bin_p, *cnt4, *binoff, *row_len4;
+    GPOP_CUDA_TRY(t.alloc(&bin_j0, g->nb + 1));
+    GPOP_CUDA_TRY(t.alloc(&bin_p, g->nb + 1));
+    GPOP_CUDA_TRY(t.alloc(&cnt4, g->nb + 1));
+    GPOP_CUDA_TRY(t.alloc(&binoff, g->nb + 1));
+    GPOP_CUDA_TRY(t.alloc(&row_len4, (uint64_t)k + 1));
+    GPOP_CUDA_TRY(dalloc(g, &g->bin_q, g->nb));
+    GPOP_CUDA_TRY(cudaMemsetAsync(row_len4, 0, 4ull * (k + 1), s));
+    const uint32_t nmsg32 = (uint32_t)nmsg;  // messages <= edges < 2^32
+    GPOP_CUDA_TRY(cudaMemcpyAsync(bin_j0 + g->nb, &nmsg32, 4, cudaMemcpyHostToDevice, s));
+    GPOP_CUDA_TRY(cudaMemsetAsync(cnt4 + g->nb, 0, 4, s));
+    if (nmsg) {
+        k_bin_starts<<<blocks_for(nmsg), kThreads, 0, s>>>(nmsg, shift, k, skey, binscan, bin_j0, g->bin_q, bin_p);
+        k_bin_pad<<<blocks_for(g->nb), kThreads, 0, s>>>((uint32_t)g->nb, bin_j0, bin_p, cnt4, row_len4);
+    }
+    GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+        return cub::DeviceScan::ExclusiveSum(tmp, bytes, cnt4, binoff, g->nb + 1, s);
+    }));
+    k_pad8<<<blocks_for(k), kThreads, 0, s>>>(k, row_len4, msgs_row_pad);
+    GPOP_CUDA_TRY(cudaMemsetAsync(msgs_row_pad + k, 0, 4, s));
+    GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
+        return cub::DeviceScan::ExclusiveSum(tmp, bytes, msgs_row_pad, g->row_png, (uint64_t)k + 1, s);
+    }));
+    uint32_t h_npad = 0;
+    GPOP_CUDA_TRY(cudaMemcpyAsync(&h_npad, g->row_png + k, 4, cudaMemcpyDeviceToHost, s));
+    GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+    g->npng_pad = h_npad;
 
     GPOP_CUDA_TRY(dalloc(g, &g->png, g->npng_pad));
     GPOP_CUDA_TRY(dalloc(g, &g->pdata, g->npng_pad));
-    GPOP_CUDA_TRY(dalloc(g, &g->bin_q, g->nb));
+    // padding slots keep local source 0: their values are staged but no entry refers to them
     GPOP_CUDA_TRY(cudaMemsetAsync(g->png, 0, 2ull * std::max<uint64_t>(g->npng_pad, 1), s));
     GPOP_CUDA_TRY(cudaMemsetAsync(g->pdata, 0xFF, 4ull * std::max<uint64_t>(g->npng_pad, 1), s));
-    uint32_t *slot_of_head, *bin_of_head, *bin_j0, *bin_slot0;
+    uint32_t *slot_of_head, *bin_of_head, *bin_slot0;
     GPOP_CUDA_TRY(t.alloc(&slot_of_head, E));
     GPOP_CUDA_TRY(t.alloc(&bin_of_head, E));
-    GPOP_CUDA_TRY(t.alloc(&bin_j0, g->nb + 1));
     GPOP_CUDA_TRY(t.alloc(&bin_slot0, g->nb + 1));
     if (nmsg)
-        k_place_msgs<<<blocks_for(nmsg), kThreads, 0, s>>>(nmsg, shift, k, skey, shead, binscan, row_msg, g->row_png,
-                                                           g->png, slot_of_head, bin_of_head, g->bin_q, bin_j0,
+        k_place_msgs<<<blocks_for(nmsg), kThreads, 0, s>>>(nmsg, shift, skey, shead, binscan, bin_j0, bin_p, binoff,
+                                                           g->row_bin, g->row_png, g->png, slot_of_head, bin_of_head,
                                                            bin_slot0);
 
     // 5. message head of every edge (its first edge to the same destination partition)
@@ -512,12 +564,14 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         hj0[nb] = (uint32_t)nmsg;
         std::vector<uint32_t> cseq0(nb + 1, 0), col_blk0(k + 1, 0);
         std::vector<uint4> runs;
+        std::vector<uint32_t> blk_nval;  // staged values (padded messages) of every block
         uint32_t nblocks = 0;
         for (uint32_t q = 0; q < k; ++q) {
             col_blk0[q] = nblocks;
             uint64_t cs = 0;
             for (uint32_t i = hcolbin[q]; i < hcolbin[q + 1]; ++i) {
-                uint32_t b = hcolbins[i], cnt = hj0[b + 1] - hj0[b];
+                const uint32_t b = hcolbins[i];
+                const uint32_t cnt = (hj0[b + 1] - hj0[b] + kBinAlign - 1) / kBinAlign * kBinAlign;  // padded bin
                 cseq0[b] = (uint32_t)cs;
                 uint32_t done = 0;
                 while (done < cnt) {  // split the bin's run at block boundaries
@@ -529,6 +583,7 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
                 }
                 cs += cnt;
             }
+            for (uint64_t j = 0; j < cs; j += kPcBlock) blk_nval.push_back((uint32_t)std::min<uint64_t>(kPcBlock, cs - j));
             nblocks += (uint32_t)((cs + kPcBlock - 1) / kPcBlock);
         }
         col_blk0[k] = nblocks;
@@ -548,6 +603,9 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         if (!runs.empty())
             GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_runs, runs.data(), sizeof(uint4) * runs.size(), cudaMemcpyHostToDevice, s));
         GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_blk_run, blk_run0.data(), 4ull * (nblocks + 1), cudaMemcpyHostToDevice, s));
+        GPOP_CUDA_TRY(dalloc(g, &g->pc_blk_nval, (uint64_t)nblocks + 1));
+        if (nblocks)
+            GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_blk_nval, blk_nval.data(), 4ull * nblocks, cudaMemcpyHostToDevice, s));
         // entries: sort keys (block, local destination, index in block)
         uint32_t *d_cseq0, *d_colblk0, *blk_hist;
         GPOP_CUDA_TRY(t.alloc(&d_cseq0, nb + 1));
@@ -665,16 +723,61 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
                 k_warp_splits<<<blocks_for((uint64_t)nrow * kSp), kThreads, 0, s>>>(nrow, d_lo, d_hi, g->pe,
                                                                                     g->pc_wsp);
             }
+            // re-lay the entries so that every warp range starts 16-aligned and is padded to kPcPad
+            std::vector<uint32_t> sp((size_t)nrow * kSp);
+            if (nrow) GPOP_CUDA_TRY(cudaMemcpyAsync(sp.data(), g->pc_wsp, 4ull * nrow * kSp, cudaMemcpyDeviceToHost, s));
             GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+            const uint32_t nrange = nrow * kPcGatherWarps;
+            std::vector<uint32_t> old0(nrange), len(nrange), new0(nrange), nsp((size_t)nrow * kSp);
+            uint64_t pos = 0;
+            for (uint32_t r = 0; r < nrow; ++r) {
+                for (uint32_t w = 0; w < kPcGatherWarps; ++w) {
+                    const uint32_t i = r * kPcGatherWarps + w, a = sp[(size_t)r * kSp + w];
+                    old0[i] = a;
+                    len[i] = sp[(size_t)r * kSp + w + 1] - a;
+                    new0[i] = (uint32_t)pos;
+                    nsp[(size_t)r * kSp + w] = (uint32_t)pos;
+                    pos += (len[i] + kPcPad - 1) / kPcPad * kPcPad;
+                }
+                nsp[(size_t)r * kSp + kPcGatherWarps] = (uint32_t)pos;
+            }
+            if (pos + kPcPad >= (1ull << 32)) return fail(GPOP_ERR_INVALID_ARG, "too many edges for the padded PC entry layout");
+            uint32_t *d_old0, *d_len, *d_new0, *pe2 = nullptr;
+            int32_t *pw2 = nullptr;
+            GPOP_CUDA_TRY(t.alloc(&d_old0, (uint64_t)nrange + 1));
+            GPOP_CUDA_TRY(t.alloc(&d_len, (uint64_t)nrange + 1));
+            GPOP_CUDA_TRY(t.alloc(&d_new0, (uint64_t)nrange + 1));
+            cudaError_t ae = cudaMalloc(&pe2, 4ull * (pos + 4));
+            if (ae == cudaSuccess && g->weighted) {
+                ae = cudaMalloc(&pw2, 4ull * (pos + 4));
+                if (ae != cudaSuccess) cudaFree(pe2);
+            }
+            GPOP_CUDA_TRY(ae);
+            g->device_bytes += 4ull * (pos + 4) * (g->weighted ? 2 : 1);
+            if (nrange) {
+                GPOP_CUDA_TRY(cudaMemcpyAsync(d_old0, old0.data(), 4ull * nrange, cudaMemcpyHostToDevice, s));
+                GPOP_CUDA_TRY(cudaMemcpyAsync(d_len, len.data(), 4ull * nrange, cudaMemcpyHostToDevice, s));
+                GPOP_CUDA_TRY(cudaMemcpyAsync(d_new0, new0.data(), 4ull * nrange, cudaMemcpyHostToDevice, s));
+                GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_wsp, nsp.data(), 4ull * nrow * kSp, cudaMemcpyHostToDevice, s));
+                k_pad_entries<<<std::min<uint32_t>(nrange, 65535u), kThreads, 0, s>>>(nrange, d_old0, d_len, d_new0,
+                                                                                    g->pe, g->pw, pe2, pw2);
+            }
+            GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(g->pe);
+            g->device_bytes -= 4ull * (E + 4);
+            g->pe = pe2;
+            if (g->weighted) {
+                cudaFree(g->pw);
+                g->device_bytes -= 4ull * (E + 4);
+                g->pw = pw2;
+            }
         }
         g->npct = (uint32_t)stasks.size();
         g->npart = nparts;
         GPOP_CUDA_TRY(dalloc(g, &g->pc_task, stasks.size()));
-        GPOP_CUDA_TRY(dalloc(g, &g->pc_rng, stasks.size()));
         GPOP_CUDA_TRY(dalloc(g, &g->pc_part, (uint64_t)nparts * P));
         if (!stasks.empty()) {
             GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_task, stasks.data(), sizeof(uint4) * stasks.size(), cudaMemcpyHostToDevice, s));
-            GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_rng, srng.data(), sizeof(uint2) * srng.size(), cudaMemcpyHostToDevice, s));
         }
         GPOP_CUDA_TRY(cudaMemcpyAsync(g->col_ntask, col_ntask.data(), 4ull * k, cudaMemcpyHostToDevice, s));
         GPOP_CUDA_TRY(cudaMemcpyAsync(g->col_part0, col_part0.data(), 4ull * k, cudaMemcpyHostToDevice, s));

@@ -62,9 +62,8 @@ struct Params {
     uint32_t *task_sc_cnt, *task_sc_list;  // per gather task: fresh SC bins of this iteration
     // PC gather blocks
     const uint4 *pc_runs, *pc_task;
-    const uint2 *pc_rng;
     const uint32_t *pc_wsp, *pc_tsp;  // per task block: kPcWarps+1 entry splits; per task: first split row
-    const uint32_t *pc_blk_run, *pc_blk_ent, *col_ntask, *col_part0, *pe;
+    const uint32_t *pc_blk_run, *pc_blk_nval, *pc_blk_ent, *col_ntask, *col_part0, *pe;
     const int32_t *pw;
     uint32_t *pc_part;
     uint32_t npct;
@@ -586,38 +585,6 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
 
 // --- gather + filter ---------------------------------------------------------------------------
 
-// Asynchronous global -> shared copies (cp.async): the copies of one group land together and are
-// waited for with cp.async.wait_group, so a CTA keeps several chunks of bins and destination lists in
-// flight while it reduces the current one.
-__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async16(uint32_t *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-// waits until at most n of this thread's most recent groups are still in flight (n < kPcMaxSlots)
-__device__ __forceinline__ void cp_async_wait_n(uint32_t n) {
-    switch (n) {
-        case 0: cp_async_wait<0>(); break;
-        case 1: cp_async_wait<1>(); break;
-        case 2: cp_async_wait<2>(); break;
-        case 3: cp_async_wait<3>(); break;
-        case 4: cp_async_wait<4>(); break;
-        case 5: cp_async_wait<5>(); break;
-        case 6: cp_async_wait<6>(); break;
-        default: cp_async_wait<7>(); break;
-    }
-}
-
 // --- mbarriers (block value buffers of k_gather_pc) ---------------------------------------------
 
 __device__ __forceinline__ uint32_t smem_addr(const void *ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
@@ -627,9 +594,20 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(bar)) : "memory");
 }
-// arrives once this thread's earlier cp.async copies have landed (counts against the init count)
-__device__ __forceinline__ void mbar_arrive_cp_async(uint64_t *bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// makes the barrier initialisations visible to the asynchronous (bulk copy) proxy
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+// 1-D bulk copy global -> shared (TMA engine): 16-byte aligned addresses, size a multiple of 16; the bytes
+// are counted against the barrier's transaction count when they land
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
@@ -653,6 +631,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     return false;
 }
 
+// Bounded wait used while leaving after an abort: lets copies still in flight land before the CTA exits.
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kPcSpinLimit && !mbar_try_wait(bar, parity); ++it) {
+    }
+}
+
 // Position in one warp's entry stream through a PC gather task: block i (relative to the
 // task's first block), next entry s.  sp[i * (kPcWarps + 1) + w] .. [.. + w + 1] bound warp w's entries in
 // block i; blocks where the warp has none are skipped.
@@ -665,25 +649,25 @@ __device__ __forceinline__ void pc_skip_empty(const uint32_t *sp, uint32_t nb, i
         if (c.i < nb) c.s = sp[c.i * (kPcWarps + 1) + w];
     }
 }
-// A round's entries [s, e) are copied as the aligned words [s & ~3, e rounded up to 4), at most C.
+// A round covers entries [s, min(s + C, end of the warp's range)); ranges start 16-aligned and are
+// padded to a multiple of kPcPad, so every round is a whole number of 16-entry groups.
 template <uint32_t C>
 __device__ __forceinline__ uint32_t pc_round_end(const uint32_t *sp, int w, const PcCursor &c) {
-    return (uint32_t)min((uint64_t)(c.s & ~3u) + C, (uint64_t)sp[c.i * (kPcWarps + 1) + w + 1]);
+    return min(c.s + C, sp[c.i * (kPcWarps + 1) + w + 1]);
 }
 
 // Serial fold of one lane's K entries (round positions j0 .. j0+K-1), in batches of 8: the batch's
 // message values are loaded first (independent shared loads), runs of equal destination are then found
-// in registers, and the complete inner runs are folded into acc with batched read-modify-writes (inner
-// runs of a lane have distinct destinations, and no other lane or warp touches them).  CHECK selects the
-// bounds tests of the lanes at the round's edges: positions before off repeat the first entry's
-// destination with the identity, positions from R on take the sentinel destination.
-template <int ALGO, bool CHECK>
-__device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt, uint32_t j0, uint32_t off,
-                                        uint32_t R, const uint32_t *stage, uint32_t *acc, uint32_t &fd,
-                                        uint32_t &head, uint32_t &run_d, uint32_t &run_v, bool &in_head) {
+// in registers, and the complete inner runs are folded into acc with batched, branch-free
+// read-modify-writes (inner runs of a lane have distinct destinations, and no other lane or warp touches
+// them; positions that end no inner run update the scratch word sink).  Padding entries repeat their
+// range's last destination and read the NULL value slot, so they fold as the identity.
+template <int ALGO>
+__device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt, uint32_t j0, const uint32_t *stage,
+                                        uint32_t *acc, uint32_t *sink, uint32_t &fd, uint32_t &head,
+                                        uint32_t &run_d, uint32_t &run_v, bool &in_head) {
     using O = Op<ALGO>;
     constexpr uint32_t K = PcShape<ALGO>::K;
-    uint32_t lead = 0;
 #pragma unroll
     for (uint32_t hb = 0; hb < K; hb += 8) {
         const uint4 e0 = *reinterpret_cast<const uint4 *>(ent + j0 + hb);
@@ -696,22 +680,11 @@ __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt
             ww[0] = w0.x; ww[1] = w0.y; ww[2] = w0.z; ww[3] = w0.w;
             ww[4] = w1.x; ww[5] = w1.y; ww[6] = w1.z; ww[7] = w1.w;
         }
-        if (CHECK && hb == 0) {  // destination of the first entry (off <= 3)
-            const uint32_t k0 = off > j0 ? off - j0 : 0;
-            lead = (k0 == 0 ? ee[0] : k0 == 1 ? ee[1] : k0 == 2 ? ee[2] : ee[3]) >> 16;
-        }
         uint32_t d[8], x[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            if (CHECK) {
-                const uint32_t j = j0 + hb + i;
-                const bool valid = j >= off && j < R;
-                d[i] = valid ? (ee[i] >> 16) : (j < off ? lead : kSent);
-                x[i] = valid ? stage[ee[i] & 0xFFFFu] : kNull;
-            } else {
-                d[i] = ee[i] >> 16;
-                x[i] = stage[ee[i] & 0xFFFFu];
-            }
+            d[i] = ee[i] >> 16;
+            x[i] = stage[ee[i] & 0xFFFFu];
         }
         bool fl[8];
         uint32_t fk[8], fv[8];
@@ -734,36 +707,30 @@ __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt
             run_v = ch ? v : joined;
             run_d = d[i];
         }
-        uint32_t old[8];
+        uint32_t *dst[8], old[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (fl[i]) old[i] = acc[fk[i]];
+        for (int i = 0; i < 8; ++i) dst[i] = fl[i] ? acc + fk[i] : sink;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (fl[i]) acc[fk[i]] = O::combine(old[i], fv[i]);
+        for (int i = 0; i < 8; ++i) old[i] = *dst[i];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) *dst[i] = O::combine(old[i], fv[i]);
     }
 }
 
-// One warp round: positions [off, off+n) of the round buffer, sorted by destination, all inside this
-// warp's destination slice.  Lane l folds positions [l K, (l+1) K) serially; one segmented warp scan,
-// keyed by destination, joins the lanes' last runs, and a lane's first run takes the scan value of the
-// lane before it when they share the destination.  Every complete run is folded into acc directly: a
-// run cut by the round's end continues in the warp's next round, folded after this part.
+// One warp round: n round positions (a multiple of K), sorted by destination, all inside this warp's
+// destination slice of the block.  Lane l folds positions [l K, (l+1) K) serially; one segmented warp
+// scan, keyed by destination, joins the lanes' last runs, and a lane's first run takes the scan value of
+// the lane before it when they share the destination.  Every complete run is folded into acc directly:
+// a run cut by the round's end continues in the warp's next round, folded after this part.
 template <int ALGO>
-__device__ __forceinline__ void pc_round(const uint32_t *ent, const uint32_t *wgt, uint32_t off, uint32_t n,
-                                         const uint32_t *stage, uint32_t *acc, int lane) {
+__device__ __forceinline__ void pc_round(const uint32_t *ent, const uint32_t *wgt, uint32_t n, const uint32_t *stage,
+                                         uint32_t *acc, uint32_t *sink, int lane) {
     using O = Op<ALGO>;
     constexpr uint32_t K = PcShape<ALGO>::K;
-    const uint32_t R = off + n;
     const uint32_t j0 = lane * K;
     uint32_t fd = kSent, head = O::identity(), run_d = kSent, run_v = O::identity();
     bool in_head = true;
-    const bool edge = j0 < R && (j0 < off || j0 + K > R);
-    if (__any_sync(0xffffffffu, edge)) {
-        if (j0 < R) pc_lane<ALGO, true>(ent, wgt, j0, off, R, stage, acc, fd, head, run_d, run_v, in_head);
-    } else {
-        if (j0 < R) pc_lane<ALGO, false>(ent, wgt, j0, off, R, stage, acc, fd, head, run_d, run_v, in_head);
-    }
+    if (j0 < n) pc_lane<ALGO>(ent, wgt, j0, stage, acc, sink, fd, head, run_d, run_v, in_head);
     const bool uni = in_head;  // all K positions share one destination
     const uint32_t ld = run_d;
     uint32_t S = run_v;
@@ -783,78 +750,71 @@ __device__ __forceinline__ void pc_round(const uint32_t *ent, const uint32_t *wg
     if (ld != kSent && (lane == 31 || next_fd != ld)) acc[ld] = O::combine(acc[ld], S);  // last run ends here
 }
 
-// Issues the copies of one round, entries [s, e): the destination words (and the SSSP weights) as
-// 16-byte copies of the aligned superset [s & ~3, e rounded up to 4), spread over the warp's lanes.
-template <int ALGO>
-__device__ __forceinline__ void pc_issue_round(const Params &p, uint32_t s, uint32_t e, uint32_t *ent,
-                                               uint32_t *wgt, int lane) {
-    const uint64_t a0 = s & ~3u, a1 = ((uint64_t)e + 3) & ~3ull;
-    for (uint64_t i = a0 + 4u * lane; i < a1; i += 128u) {
-        cp_async16(ent + (i - a0), p.pe + i);
-        if (ALGO == ALG_SSSP) cp_async16(wgt + (i - a0), p.pw + i);
+// Issues the bulk copies of a block's message values into a value buffer: its bin runs (row-major source
+// slot, length, offset in the block; all multiples of 4 values, so 16-byte aligned) are dealt to the
+// warps round-robin, one run per lane; thread 0 arms the buffer's "full" mbarrier with the block's byte
+// count.  first is this lane's descriptor of the first batch, loaded one block ahead.
+__device__ __forceinline__ void pc_issue_values(const Params &p, uint32_t r0, uint32_t r1, uint32_t nval, uint4 first,
+                                                uint32_t *st, uint64_t *full, int lane, int wid) {
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(full, nval * 4u);
+    for (uint32_t rb = r0 + wid, it = 0; rb < r1; rb += 32u * kPcWarps, ++it) {
+        const uint32_t rr = rb + (uint32_t)lane * kPcWarps;
+        const uint4 run = it == 0 ? first : (rr < r1 ? p.pc_runs[rr] : make_uint4(0, 0, 0, 0));
+        if (rr < r1) bulk_g2s(st + run.z, p.pdata + run.x, run.y * 4u, full);
     }
 }
-
-// Issues the copies of a block's message values into a value buffer: the block's bin runs (row-major
-// source offset, length, offset in the block) are dealt to the warps round-robin, each run copied by a
-// warp's lanes as coalesced 4-byte asynchronous copies; every thread then arrives on the buffer's "full"
-// mbarrier once its own copies have landed.
-__device__ __forceinline__ void pc_issue_values(const Params &p, uint32_t r0, uint32_t r1, uint32_t *st,
-                                                uint64_t *full, int lane, int wid) {
-    for (uint32_t rb = r0 + wid; rb < r1; rb += 32u * kPcWarps) {
-        const uint32_t rr = rb + (uint32_t)lane * kPcWarps;
-        const uint4 run = rr < r1 ? p.pc_runs[rr] : make_uint4(0, 0, 0, 0);
-        const uint32_t nr = min(32u, (r1 - rb + kPcWarps - 1) / kPcWarps);
-        for (uint32_t j = 0; j < nr; ++j) {
-            const uint32_t x = __shfl_sync(0xffffffffu, run.x, j);
-            const uint32_t len = __shfl_sync(0xffffffffu, run.y, j);
-            const uint32_t z = __shfl_sync(0xffffffffu, run.z, j);
-            for (uint32_t k = lane; k < len; k += 32) cp_async4(st + z + k, p.pdata + x + k);
-        }
-    }
-    mbar_arrive_cp_async(full);
+__device__ __forceinline__ uint4 pc_first_run(const Params &p, uint32_t r0, uint32_t r1, int lane, int wid) {
+    const uint32_t rr = r0 + wid + (uint32_t)lane * kPcWarps;
+    return rr < r1 ? p.pc_runs[rr] : make_uint4(0, 0, 0, 0);
 }
 
 // PC part of the gather (Alg. 2 gather over the PC bins, Sec. 3.1.2): one CTA per task (a range of
 // consecutive entries of column q's blocks), one task at a time per CTA, largest tasks first.
-//  * A block's message values are copied from the data bins into one of two shared buffers by coalesced
-//    asynchronous copies of its bin runs (the bins are read in order, as the paper's gather streams
-//    bin[:][q]), issued by all warps while the previous block is being reduced; a "full" mbarrier
-//    (bounded wait) tells when they have landed.
+//  * A block's message values are copied from the data bins into one of two shared buffers by bulk
+//    copies (TMA) of its bin runs (the bins are read in order, as the paper's gather streams bin[:][q]),
+//    issued while the previous block is being reduced; a "full" mbarrier counts the bytes in.
 //  * Within a block, warp w takes the w-th of 16 entry ranges of about equal size, cut at destination
-//    boundaries when the graph is built, so no two warps touch one destination of the block.  Each warp
-//    streams its entries through its own ring of asynchronous copies, several rounds ahead (across block
-//    boundaries), and folds them into the shared column accumulator with lane-serial runs and a
-//    segmented warp scan: random accesses touch shared memory only.  One CTA barrier per block separates
-//    the blocks' slices and frees the block's value buffer.
+//    boundaries and padded to whole 16-entry groups when the graph is built, so no two warps touch one
+//    destination of the block.  Each warp streams its entries through its own ring of rounds, one bulk
+//    copy and one mbarrier per round, several rounds ahead (across block boundaries), and folds them into
+//    the shared column accumulator with lane-serial runs and a segmented warp scan: random accesses touch
+//    shared memory only.  One CTA barrier per block separates the blocks' slices and frees the block's
+//    value buffer.
 // The accumulator stays in shared memory for the whole task; a column split over several tasks writes
-// one partial vector per task.  When a bounded wait runs out, the run's error flag is raised and all
-// warps leave.
+// one partial vector per task.  Every mbarrier wait is bounded: when one runs out, the run's error flag
+// is raised and all warps leave.
 template <int ALGO>
 __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
     using O = Op<ALGO>;
     constexpr uint32_t C = PcShape<ALGO>::kRound, kSlotWords = PcShape<ALGO>::kSlotWords;
-    constexpr uint32_t kSp = kPcWarps + 1;
+    constexpr uint32_t kSp = kPcWarps + 1, kStageWords = kPcBlock + 4;
     extern __shared__ __align__(16) uint32_t s_pc_dyn[];
     uint32_t *acc = s_pc_dyn;                     // P values of the column
-    uint32_t *stage = s_pc_dyn + p.P;             // 2 x kPcBlock message values
-    uint32_t *rings = stage + 2 * kPcBlock;       // kPcWarps x pc_slots rounds (entries, then SSSP weights)
+    uint32_t *stage = s_pc_dyn + p.P;             // 2 x (kPcBlock message values + the NULL slot)
+    uint32_t *rings = stage + 2 * kStageWords;    // kPcWarps x pc_slots rounds (entries, then SSSP weights)
     __shared__ __align__(8) uint64_t s_full[2];
-    __shared__ uint32_t s_state, s_abort;
+    __shared__ __align__(8) uint64_t s_slot[kPcWarps * kPcMaxSlots];  // one barrier per ring slot
+    __shared__ uint32_t s_state, s_abort, s_sink;  // s_sink: target of the no-op read-modify-writes
     __shared__ uint4 s_tk;
-    __shared__ uint2 s_rng;
     __shared__ uint32_t s_tsp;
-    __shared__ uint32_t s_run[kPcTaskBlocks + 1];
+    __shared__ uint32_t s_run[kPcTaskBlocks + 1], s_nval[kPcTaskBlocks];
     __shared__ uint32_t s_sp[kPcTaskBlocks * kSp];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t ns = p.pc_slots;
     uint32_t *ring = rings + (uint32_t)wid * ns * kSlotWords;
+    uint64_t *sbar = s_slot + wid * kPcMaxSlots;
     if (threadIdx.x == 0) {
-        mbar_init(&s_full[0], kPcThreads);
-        mbar_init(&s_full[1], kPcThreads);
+        mbar_init(&s_full[0], 1);
+        mbar_init(&s_full[1], 1);
+        for (int i = 0; i < kPcWarps * (int)kPcMaxSlots; ++i) mbar_init(&s_slot[i], 1);
+        fence_mbar_init();
         s_abort = 0;
+        stage[kPcPadIdx] = kNull;  // value slot of the padding entries; the copies never write it
+        stage[kStageWords + kPcPadIdx] = kNull;
     }
-    uint32_t gb = 0;  // blocks this CTA has passed through (buffer = gb & 1, use = gb >> 1)
+    uint32_t gb = 0;         // blocks this CTA has passed through (buffer = gb & 1, use = gb >> 1)
+    uint32_t ph = 0;         // this warp's ring slot phases (bit per slot)
+    uint32_t head_slot = 0;  // this warp's next slot to fold; rounds in flight follow it
     for (;;) {
         if (threadIdx.x == 0) {
             const uint32_t t = atomicAdd(&p.counters[5], 1u);
@@ -863,7 +823,6 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
                 const uint4 tk = p.pc_task[t];  // column, first block, end block, partial slot
                 state = p.gflag_pc[tk.x] == p.epoch ? 1u : 0u;
                 s_tk = tk;
-                s_rng = p.pc_rng[t];
                 s_tsp = p.pc_tsp[t];
             }
             s_state = state;
@@ -878,55 +837,81 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
         }
         const uint32_t nb = tk.z - tk.y;
         if (threadIdx.x <= nb) s_run[threadIdx.x] = p.pc_blk_run[tk.y + threadIdx.x];
+        if (threadIdx.x < nb) s_nval[threadIdx.x] = p.pc_blk_nval[tk.y + threadIdx.x];
         for (uint32_t i = threadIdx.x; i < nb * kSp; i += kPcThreads) s_sp[i] = p.pc_wsp[(uint64_t)s_tsp * kSp + i];
         const uint32_t gq = tk.x << p.shift;
         const uint32_t wq = min(p.P, p.V - gq);
         for (uint32_t i = threadIdx.x; i < wq; i += kPcThreads) acc[i] = O::identity();
         __syncthreads();
-        pc_issue_values(p, s_run[0], s_run[1], stage + (gb & 1) * kPcBlock, &s_full[gb & 1], lane, wid);
+        pc_issue_values(p, s_run[0], s_run[1], s_nval[0], pc_first_run(p, s_run[0], s_run[1], lane, wid),
+                        stage + (gb & 1) * kStageWords, &s_full[gb & 1], lane, wid);
+        uint4 next_run = nb > 1 ? pc_first_run(p, s_run[1], s_run[2], lane, wid) : make_uint4(0, 0, 0, 0);
         PcCursor pc{0, s_sp[wid]};
         pc_skip_empty(s_sp, nb, wid, pc);
         PcCursor cc = pc;
-        uint32_t issued = 0, done = 0;
-        bool ok = true;
-        for (uint32_t i = 0; i < nb; ++i) {
+        uint32_t inflight = 0;  // rounds issued and not yet folded
+        bool ok = true, abort = false;
+        uint32_t i = 0;
+        for (; i < nb && !abort; ++i) {
             const uint32_t g = gb + i, buf = g & 1, use = g >> 1;
-            if (i + 1 < nb)  // the next block's values go to the other buffer, freed by the last barrier
-                pc_issue_values(p, s_run[i + 1], s_run[i + 2], stage + (buf ^ 1) * kPcBlock, &s_full[buf ^ 1], lane,
-                                wid);
+            if (i + 1 < nb) {  // the next block's values go to the other buffer, freed by the last barrier
+                pc_issue_values(p, s_run[i + 1], s_run[i + 2], s_nval[i + 1], next_run,
+                                stage + (buf ^ 1) * kStageWords, &s_full[buf ^ 1], lane, wid);
+                if (i + 2 < nb) next_run = pc_first_run(p, s_run[i + 2], s_run[i + 3], lane, wid);
+            }
             if (ok && cc.i == i && !mbar_wait(&s_full[buf], use & 1, &s_abort, &p.ctrl->error)) ok = false;
             while (ok && cc.i == i) {
-                while (issued - done < ns && pc.i < nb) {
+                while (inflight < ns && pc.i < nb) {  // keep the ring full: one bulk copy per round
                     const uint32_t e = pc_round_end<C>(s_sp, wid, pc);
-                    uint32_t *slot = ring + (issued % ns) * kSlotWords;
-                    pc_issue_round<ALGO>(p, pc.s, e, slot, slot + C, lane);
-                    cp_async_commit();
-                    ++issued;
+                    uint32_t sl = head_slot + inflight;
+                    sl = sl >= ns ? sl - ns : sl;
+                    if (lane == 0) {
+                        const uint32_t bytes = (e - pc.s) * 4u;
+                        uint32_t *dst = ring + sl * kSlotWords;
+                        mbar_arrive_expect_tx(&sbar[sl], ALGO == ALG_SSSP ? 2 * bytes : bytes);
+                        bulk_g2s(dst, p.pe + pc.s, bytes, &sbar[sl]);
+                        if (ALGO == ALG_SSSP) bulk_g2s(dst + C, p.pw + pc.s, bytes, &sbar[sl]);
+                    }
+                    ++inflight;
                     pc.s = e;
                     pc_skip_empty(s_sp, nb, wid, pc);
                 }
-                cp_async_wait_n(issued - done - 1);
-                __syncwarp();
+                if (!mbar_wait(&sbar[head_slot], (ph >> head_slot) & 1u, &s_abort, &p.ctrl->error)) {
+                    ok = false;
+                    break;
+                }
+                ph ^= 1u << head_slot;
                 const uint32_t e = pc_round_end<C>(s_sp, wid, cc);
-                const uint32_t *slot = ring + (done % ns) * kSlotWords;
-                pc_round<ALGO>(slot, slot + C, cc.s & 3u, e - cc.s, stage + buf * kPcBlock, acc, lane);
-                __syncwarp();
-                ++done;
+                const uint32_t *slot = ring + head_slot * kSlotWords;
+                pc_round<ALGO>(slot, slot + C, e - cc.s, stage + buf * kStageWords, acc, &s_sink, lane);
+                __syncwarp();  // the slot is refilled only after every lane has read it
+                --inflight;
+                head_slot = head_slot + 1 == ns ? 0 : head_slot + 1;
                 cc.s = e;
                 pc_skip_empty(s_sp, nb, wid, cc);
             }
             // every block of a task has entries, so some warp has waited for the values before this
-            // barrier, after which the buffer may be refilled
-            __syncthreads();
+            // barrier, after which the buffer may be refilled; all warps learn of an abort here
+            abort = __syncthreads_or(!ok) != 0;
         }
-        cp_async_wait<0>();
+        if (abort) {  // let every copy still in flight land, then leave
+            const uint32_t last = gb + i - 1;  // block whose barrier saw the abort
+            for (uint32_t k = 0; k < inflight; ++k) {
+                const uint32_t sl = head_slot + k >= ns ? head_slot + k - ns : head_slot + k;
+                mbar_drain(&sbar[sl], (ph >> sl) & 1u);
+            }
+            if (threadIdx.x == 0) {
+                mbar_drain(&s_full[last & 1], (last >> 1) & 1u);
+                if (i < nb) mbar_drain(&s_full[(last + 1) & 1], ((last + 1) >> 1) & 1u);
+            }
+            __syncthreads();
+            break;
+        }
         gb += nb;
         __syncthreads();
-        if (s_abort) break;
         uint32_t *out = (tk.w == kNull) ? p.pc_sum + gq : p.pc_part + (uint64_t)tk.w * p.P;
         for (uint32_t i = threadIdx.x; i < wq; i += kPcThreads) out[i] = acc[i];
     }
-    cp_async_wait<0>();
 }
 
 // Gather of one (column q, destination range) task, after k_gather_pc:
@@ -1289,7 +1274,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     p.rowptr = g->rowptr; p.col = g->col; p.w = g->w; p.esub = g->esub;
     p.row_bin = g->row_bin; p.bin_q = g->bin_q; p.col_bin = g->col_bin; p.col_bins = g->col_bins;
     p.png = g->png; p.pdata = g->pdata; p.row_png = g->row_png;
-    p.pc_runs = g->pc_runs; p.pc_task = g->pc_task; p.pc_rng = g->pc_rng; p.pc_wsp = g->pc_wsp; p.pc_tsp = g->pc_tsp; p.pc_blk_run = g->pc_blk_run; p.pc_blk_ent = g->pc_blk_ent;
+    p.pc_runs = g->pc_runs; p.pc_task = g->pc_task; p.pc_wsp = g->pc_wsp; p.pc_tsp = g->pc_tsp; p.pc_blk_run = g->pc_blk_run; p.pc_blk_nval = g->pc_blk_nval; p.pc_blk_ent = g->pc_blk_ent;
     p.scpair = g->scpair; p.sccnt = g->sccnt;
     p.sub_cap = g->sub_cap; p.sub_task = g->sub_task; p.row_sub = g->row_sub; p.task_sub_ptr = g->task_sub_ptr;
     p.task_sc_cnt = rb->task_sc_cnt; p.task_sc_list = rb->task_sc_list;
@@ -1348,7 +1333,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         int optin = 0, dev = 0;
         GPOP_CUDA_TRY(cudaGetDevice(&dev));
         GPOP_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        const size_t fixed = sizeof(uint32_t) * ((size_t)g->P + 2 * kPcBlock);
+        const size_t fixed = sizeof(uint32_t) * ((size_t)g->P + 2 * (kPcBlock + 4));
         const size_t slot = sizeof(uint32_t) * PcShape<ALGO>::kSlotWords * kPcWarps;
         const size_t avail = (size_t)optin > fixed + fa.sharedSizeBytes ? optin - fixed - fa.sharedSizeBytes : 0;
         const uint32_t ns = (uint32_t)std::min<size_t>(kPcMaxSlots, avail / slot);

@@ -19,13 +19,16 @@ constexpr uint32_t kNull = 0xFFFFFFFFu;
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 
 constexpr int kPngAlign = 8;           // PNG rows padded to 8 entries (16-byte u16 vectors)
+constexpr uint32_t kBinAlign = 4;      // every bin padded to 4 slots: 16-byte aligned bulk copies of bin runs
 constexpr uint32_t kGatherWidth = 4096;  // max destinations per gather task (smem accumulator)
 constexpr uint32_t kGatherEntries = 32768;  // target in-entries per gather task
 constexpr uint32_t kScatterChunk = 16384;   // PNG entries per static PC scatter task
 constexpr uint32_t kMaxRowBins = 40960;     // SC scatter keeps one cursor per row bin in smem
 constexpr uint32_t kPcBlock = 8192;         // messages staged in shared memory per PC gather block
 constexpr uint32_t kPcTaskBlocks = 8;       // at most this many blocks per PC gather task
-constexpr uint32_t kPcGatherWarps = 16;     // consumer warps of the PC gather, one destination slice each
+constexpr uint32_t kPcGatherWarps = 16;     // warps of the PC gather, one destination slice of a block each
+constexpr uint32_t kPcPad = 16;             // each warp's entry range of a block is padded to a multiple of this
+constexpr uint32_t kPcPadIdx = kPcBlock;    // block index of the padding entries (a value slot that holds NULL)
 constexpr uint32_t kPcTaskMinEntries = 65536;  // PC gather tasks hold about max(this, E / (8 SMs)) entries
 
 enum Mode : uint8_t { kModeNone = 0, kModeSC = 1, kModePC = 2 };
@@ -82,17 +85,18 @@ struct Graph {
     // kPcBlock messages, staged by runs; destination lists as (local destination << 16 | index in block)
     uint4 *pc_runs = nullptr;     // (row-major source slot, length, offset in block, block)
     uint32_t *pc_blk_run = nullptr;  // npcb+1: runs of each block
+    uint32_t *pc_blk_nval = nullptr; // npcb: staged values of each block (a multiple of kBinAlign)
     uint32_t *pc_blk_ent = nullptr;  // npcb+1: entries of each block
     uint4 *pc_task = nullptr;     // npct: (column, first block, end block, partial slot or kNull), largest first
-    uint2 *pc_rng = nullptr;      // npct: entry range [begin, end) of the task within its blocks
     uint32_t *pc_tsp = nullptr;   // npct: first row of the task's blocks in pc_wsp
     uint32_t *pc_wsp = nullptr;   // per task block: kPcGatherWarps+1 entry offsets splitting its entries by
                                   // the column's destination slices (one slice per gather warp)
     uint32_t *col_ntask = nullptr;   // k: PC gather tasks of the column (0 = no PC in-edges)
     uint32_t *col_part0 = nullptr;   // k: first partial slot of a multi-task column
     uint32_t *pc_part = nullptr;  // npart x P partial results
-    uint32_t *pe = nullptr;       // E: entries, sorted by (block, destination, index)
-    int32_t *pw = nullptr;        // E or null: weights aligned with pe
+    uint32_t *pe = nullptr;       // entries, sorted by (block, destination, index); each warp range of a task
+                                  // block starts 16-aligned and is padded to a multiple of kPcPad
+    int32_t *pw = nullptr;        // null or weights aligned with pe (padding: 0)
     uint32_t npcb = 0, npct = 0, npart = 0;
 
     // SC bins, one per (source partition p, gather task t) with edges p -> t
