@@ -34,6 +34,8 @@ constexpr int kGatherWarps = kGatherThreads / 32;
 constexpr int kScatterThreads = 256;
 constexpr int kPlanThreads = 1024;
 constexpr uint32_t kSent = 0xFFFFFFFFu;
+constexpr uint32_t kBigScBin = 2048;     // SC bins at least this large are folded by the whole gather CTA
+constexpr uint32_t kMaxBigScBins = 64;
 constexpr int kPcWarps = kPcGatherWarps;          // k_gather_pc warps (one destination slice of a block each)
 constexpr int kPcThreads = 32 * kPcWarps;
 constexpr uint32_t kPcMaxSlots = 4;               // entry ring depth per consumer warp
@@ -914,17 +916,24 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
     }
 }
 
+// Folds one SC pair's value into a shared accumulator slot: an atomic minimum (BFS parents, CC labels,
+// SSSP distances: the result does not depend on the order) or a float addition (PR / PPR).
+template <int ALGO>
+__device__ __forceinline__ void sc_fold(uint32_t *slot, uint32_t v) {
+    if (ALGO == ALG_PR || ALGO == ALG_PPR) atomicAdd(reinterpret_cast<float *>(slot), u2f(v));
+    else atomicMin(slot, v);
+}
+
 // Gather of one (column q, destination range) task, after k_gather_pc:
-//  1. PC messages: light destinations take pc_sum, heavy destinations combine their segment results in
-//     segment order (only when some partition sent PC messages to the column this iteration);
-//  2. SC pairs of the task's fresh SC bins, each warp applying those of its destination slice;
+//  1. PC messages: the column's PC result (pc_sum, or its tasks' partial vectors combined in column
+//     order), only when some partition sent PC messages to the column this iteration;
+//  2. SC pairs of the task's fresh SC bins, folded with shared atomics;
 //  3. reInit / gather apply / filter of every destination of the range and the next frontier (Alg. 2).
 template <int ALGO>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
     using O = Op<ALGO>;
     __shared__ uint32_t s_acc[kGatherWidth];
-    __shared__ uint32_t s_stage[kGatherWarps][32];
-    __shared__ uint32_t s_task;
+    __shared__ uint32_t s_task, s_next, s_nbig, s_big[kMaxBigScBins];
     __shared__ uint32_t s_va[kGatherWarps];
     __shared__ unsigned long long s_ea[kGatherWarps];
     __shared__ double s_res[kGatherWarps];
@@ -965,39 +974,47 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
         }
         __syncthreads();
 
-        // SC messages: every warp walks this task's fresh SC bins (binPartList) and applies
-        // the pairs whose destination lies in its own slice of [d0, d1)
+        // SC messages: the task's fresh SC bins (binPartList) are dealt to the warps dynamically, a
+        // lane per pair, each pair folded into the accumulator with one shared atomic (min for BFS /
+        // CC / SSSP, float add for PR / PPR); bins of at least kBigScBin pairs are left to a second,
+        // CTA-wide pass so that no single warp carries a hub partition's bin alone
         const uint32_t nfresh = p.task_sc_cnt[t];
         if (nfresh) {
-            const uint32_t lo = (width * wid) / kGatherWarps, hi = (width * (wid + 1)) / kGatherWarps;
             const uint32_t lbase = p.task_sub_ptr[t];
-            for (uint32_t i = 0; i < nfresh; ++i) {
-                uint32_t bn = p.task_sc_list[lbase + i];
-                uint32_t cnt = p.sccnt[bn], sb = p.sub_cap[bn];
-                for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
-                    uint32_t j = j0 + lane;
-                    uint32_t d = kSent, v = 0;
-                    if (j < cnt) {
-                        uint2 pr = p.scpair[sb + j];
-                        d = pr.x - gt.d0;
-                        v = pr.y;
+            if (tid == 0) {
+                s_next = 0;
+                s_nbig = 0;
+            }
+            __syncthreads();
+            for (;;) {
+                uint32_t i = 0;
+                if (lane == 0) i = atomicAdd(&s_next, 1u);
+                i = __shfl_sync(0xffffffffu, i, 0);
+                if (i >= nfresh) break;
+                const uint32_t bn = p.task_sc_list[lbase + i];
+                const uint32_t cnt = p.sccnt[bn], sb = p.sub_cap[bn];
+                if (cnt >= kBigScBin) {
+                    uint32_t k = 0;
+                    if (lane == 0) k = atomicAdd(&s_nbig, 1u);
+                    k = __shfl_sync(0xffffffffu, k, 0);
+                    if (k < kMaxBigScBins) {
+                        if (lane == 0) s_big[k] = bn;
+                        continue;
                     }
-                    bool mine = (j < cnt) && d >= lo && d < hi;
-                    uint32_t key = mine ? d : (0x80000000u | (uint32_t)lane);
-                    uint32_t peers = __match_any_sync(0xffffffffu, key);
-                    s_stage[wid][lane] = v;
-                    __syncwarp();
-                    if (mine && lane == __ffs(peers) - 1) {
-                        uint32_t r = s_acc[d];
-                        uint32_t m = peers;
-                        while (m) {
-                            int l = __ffs(m) - 1;
-                            m &= m - 1;
-                            r = O::combine(r, s_stage[wid][l]);
-                        }
-                        s_acc[d] = r;
-                    }
-                    __syncwarp();
+                }
+                for (uint32_t j = lane; j < cnt; j += 32) {
+                    const uint2 pr = p.scpair[sb + j];
+                    sc_fold<ALGO>(&s_acc[pr.x - gt.d0], pr.y);
+                }
+            }
+            __syncthreads();
+            const uint32_t nbig = min(s_nbig, kMaxBigScBins);
+            for (uint32_t k = 0; k < nbig; ++k) {
+                const uint32_t bn = s_big[k];
+                const uint32_t cnt = p.sccnt[bn], sb = p.sub_cap[bn];
+                for (uint32_t j = tid; j < cnt; j += nthr) {
+                    const uint2 pr = p.scpair[sb + j];
+                    sc_fold<ALGO>(&s_acc[pr.x - gt.d0], pr.y);
                 }
             }
             __syncthreads();
