@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GTEPS & % of HBM peak (RMAT-24 PR/BFS/SSSP); learned vs analytic mode speedup"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "gather_pagerank_rmat24.md")
+PROFILES = os.path.join(ROOT, "profiles")
 ENGINE_SRC = os.path.join(ROOT, "paper_1806_08092_gb300", "csrc", "engine.cu")
 
 
@@ -49,6 +49,8 @@ def args_parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-pr-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--algos", default="pr,bfs,sssp",
+                    help="parts of the step to run (profiling of one part); the reported metric needs all three")
     return ap.parse_args()
 
 
@@ -134,17 +136,23 @@ def cpu_baseline(g, roots, pr_iters):
             "host_cores_available": os.cpu_count()}
 
 
-def traffic_from_profile():
-    """Per-launch DRAM bytes of the PageRank gather from the committed ncu summary, if it matches this source."""
+def traffic_from_profile(kernel):
+    """Per-launch DRAM bytes of `kernel` from a committed ncu summary under profiles/ that names this kernel
+    and was taken from the current engine source (sha256 prefix); None otherwise."""
+    sha = hashlib.sha256(open(ENGINE_SRC, "rb").read()).hexdigest()[:16]
     try:
-        text = open(PROFILE_SUMMARY).read()
-        sha = hashlib.sha256(open(ENGINE_SRC, "rb").read()).hexdigest()[:16]
+        names = sorted(os.listdir(PROFILES))
+    except OSError:
+        return None
+    for name in names:
+        if not name.endswith(".md"):
+            continue
+        text = open(os.path.join(PROFILES, name)).read()
+        k = re.search(r"kernel:\s*(\S+)", text)
         m = re.search(r"engine_sha256_16:\s*([0-9a-f]+)", text)
         t = re.search(r"traffic_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
-        if m and t and m.group(1) == sha:
+        if k and m and t and k.group(1) == kernel and m.group(1) == sha:
             return float(t.group(1))
-    except Exception:
-        pass
     return None
 
 
@@ -210,20 +218,24 @@ def run_ours(a, rank, world, local_rank):
     deg_t = torch.from_numpy(np.diff(g.row_ptr).astype(np.int64)).cuda()
     INF = 0xFFFFFFFF
 
+    parts = [x for x in a.algos.split(",") if x]
     # traversed edges per root (Graph500 count), outside the timed region
     te_of = {}
     nsteps = a.warmup + a.steps
     my_roots = [int(roots[(rank * nsteps + i) % len(roots)]) for i in range(nsteps)]
-    for r in set(my_roots):
-        lv = G.run("bfs", source=r).values
-        te_of[r] = int(deg_t[lv.to(torch.int64) != INF].sum().item())
+    if "bfs" in parts or "sssp" in parts:
+        for r in set(my_roots):
+            lv = G.run("bfs", source=r).values
+            te_of[r] = int(deg_t[lv.to(torch.int64) != INF].sum().item())
 
     def step(r):
         out = {}
-        pr = G.run("pagerank", max_iters=a.pr_max_iters, tol=a.pr_tol, profile=True)
-        bf = G.run("bfs", source=r, profile=True)
-        ss = G.run("sssp", source=r, profile=True)
-        out["pr"], out["bfs"], out["sssp"] = pr.stats, bf.stats, ss.stats
+        if "pr" in parts:
+            out["pr"] = G.run("pagerank", max_iters=a.pr_max_iters, tol=a.pr_tol, profile=True).stats
+        if "bfs" in parts:
+            out["bfs"] = G.run("bfs", source=r, profile=True).stats
+        if "sssp" in parts:
+            out["sssp"] = G.run("sssp", source=r, profile=True).stats
         return out
 
     for i in range(a.warmup):
@@ -247,54 +259,68 @@ def run_ours(a, rank, world, local_rank):
     edges = 0
     for i, s in enumerate(stats):
         r = my_roots[a.warmup + i]
-        edges += E * s["pr"]["iterations"] + 2 * te_of[r]
+        edges += (E * s["pr"]["iterations"] if "pr" in s else 0) + te_of.get(r, 0) * (("bfs" in s) + ("sssp" in s))
     t_all, edges_all = reduce_over_ranks(ms / 1e3, float(edges), dist, "cuda")
     value = edges_all / t_all / 1e9
 
     # per-application device throughput and the roofline of the dominant kernel (PageRank gather)
-    pr_ms = sum(s["pr"]["device_ms"] for s in stats)
-    pr_it = sum(s["pr"]["iterations"] for s in stats)
-    bfs_ms = sum(s["bfs"]["device_ms"] for s in stats)
-    sssp_ms = sum(s["sssp"]["device_ms"] for s in stats)
-    te = sum(te_of[my_roots[a.warmup + i]] for i in range(a.steps))
+    def total(key, field):
+        return sum(s[key][field] for s in stats if key in s)
+    te = sum(te_of.get(my_roots[a.warmup + i], 0) for i in range(a.steps))
     kern = np.zeros(5)
     launches = np.zeros(5, dtype=np.int64)
     for s in stats:
-        for key in ("pr", "bfs", "sssp"):
+        for key in s:
             kern += np.array(s[key]["kernel_ms"])
             launches += np.array(s[key]["kernel_launches"], dtype=np.int64)
+    per_algo = {}
+    if "pr" in parts:
+        pr_ms, pr_it = total("pr", "device_ms"), total("pr", "iterations")
+        per_algo["pagerank"] = {"iterations": pr_it / a.steps, "gteps": E * pr_it / (pr_ms / 1e3) / 1e9,
+                                "ms": pr_ms / a.steps, "residual": stats[-1]["pr"]["residual"]}
+    for key in ("bfs", "sssp"):
+        if key in parts:
+            ms_ = total(key, "device_ms")
+            per_algo[key] = {"gteps": te / (ms_ / 1e3) / 1e9, "ms": ms_ / a.steps,
+                             "iterations": total(key, "iterations") / a.steps}
     def pr_kernel(i):
         ms_ = sum(s["pr"]["kernel_ms"][i] for s in stats)
         n_ = sum(s["pr"]["kernel_launches"][i] for s in stats)
         return ms_ / max(n_, 1) / 1e3, n_
 
-    npng, npad, k = info["num_png"], info["num_png_padded"], info["num_partitions"]
+    npng, k = info["num_png"], info["num_partitions"]
     # Algorithmic bytes per launch of an all-PC PageRank iteration (every vertex active):
-    #  PC scatter: PNG source IDs (2 B) + message values (4 B) per padded slot, one message value per vertex;
+    #  PC scatter: PNG source ID (2 B) + message value (4 B) per message, one message value per vertex;
     #  PC gather (k_gather_pc): every message value once (4 B per PNG entry, staged bin by bin), the
     #    destination-list word of every in-entry (4 B) and the per-vertex PC result written (4 B);
     #  task gather + filter (k_gather): per vertex the PC result read, rank read + write, next message
     #    value, two row offsets (one per vertex in a stream) and the frontier bits.
     per_kernel_bytes = {
-        1: 6 * npad + 4 * V,
+        1: 6 * npng + 4 * V,
         4: 4 * E + 4 * npng + 4 * V,
         3: 4 * V + 16 * V + V // 4,
     }
     names = {1: "k_scatter_pc", 3: "k_gather", 4: "k_gather_pc"}
     hbm, peak_kind = peaks()
-    kinfo = {}
-    for i in (1, 3, 4):
-        avg_s, n_ = pr_kernel(i)
-        ach = per_kernel_bytes[i] / avg_s / 1e9 if avg_s > 0 else 0.0
-        kinfo[i] = {"kernel": names[i] + "<PageRank>", "achieved": ach, "frac": ach / hbm,
-                    "algorithmic_bytes_per_launch": int(per_kernel_bytes[i]), "avg_launch_ms": avg_s * 1e3,
-                    "launches": int(n_), "total_ms": avg_s * 1e3 * n_}
-    dom = max(kinfo, key=lambda i: kinfo[i]["total_ms"])
-    traffic = traffic_from_profile() if dom == 3 else None
+    roofline = None
+    if "pr" in parts:
+        kinfo = {}
+        for i in (1, 3, 4):
+            avg_s, n_ = pr_kernel(i)
+            ach = per_kernel_bytes[i] / avg_s / 1e9 if avg_s > 0 else 0.0
+            kinfo[i] = {"kernel": names[i] + "<PageRank>", "achieved": ach, "frac": ach / hbm,
+                        "algorithmic_bytes_per_launch": int(per_kernel_bytes[i]), "avg_launch_ms": avg_s * 1e3,
+                        "launches": int(n_), "total_ms": avg_s * 1e3 * n_}
+        dom = max(kinfo, key=lambda i: kinfo[i]["total_ms"])
+        roofline = {"bound": "hbm", "kernel": kinfo[dom]["kernel"], "achieved": kinfo[dom]["achieved"],
+                    "peak": hbm, "unit": "GB/s", "frac": kinfo[dom]["frac"],
+                    "traffic": traffic_from_profile(kinfo[dom]["kernel"]), "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_launch": kinfo[dom]["algorithmic_bytes_per_launch"],
+                    "avg_launch_ms": kinfo[dom]["avg_launch_ms"], "all_kernels": [kinfo[i] for i in (1, 3, 4)]}
 
     # end-to-end through the public API: host CSR in pinned memory -> build -> three runs -> host results
     e2e = None
-    if a.e2e_steps > 0:
+    if a.e2e_steps > 0 and set(parts) == {"pr", "bfs", "sssp"}:
         rp_h = torch.from_numpy(g.row_ptr.view(np.int64)).pin_memory()
         col_h = torch.from_numpy(g.col.view(np.int32)).pin_memory()
         w_h = torch.from_numpy(g.weights).pin_memory()
@@ -328,26 +354,17 @@ def run_ours(a, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/u32", "data": "synthetic",
-        "config": {"workload": f"rmat{a.scale}_pr_bfs_sssp", "scale": a.scale, "edge_factor": 16, "vertices": V,
+        "config": {"workload": f"rmat{a.scale}_" + "_".join(parts), "scale": a.scale, "edge_factor": 16, "vertices": V,
                    "edges": E, "partition_size": info["partition_size"], "partitions": k,
                    "png_entries": npng, "r": npng / max(E, 1), "pr_tol_l1": a.pr_tol,
                    "l2": f"inputs larger than L2 (layout {info['device_bytes'] / 1e9:.1f} GB vs 129 MB L2); no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "per_algo": {"pagerank": {"iterations": pr_it / a.steps, "gteps": E * pr_it / (pr_ms / 1e3) / 1e9,
-                                  "ms": pr_ms / a.steps, "residual": stats[-1]["pr"]["residual"]},
-                     "bfs": {"gteps": te / (bfs_ms / 1e3) / 1e9, "ms": bfs_ms / a.steps,
-                             "iterations": sum(s["bfs"]["iterations"] for s in stats) / a.steps},
-                     "sssp": {"gteps": te / (sssp_ms / 1e3) / 1e9, "ms": sssp_ms / a.steps,
-                              "iterations": sum(s["sssp"]["iterations"] for s in stats) / a.steps}},
-        "kernels_ms": {"plan": kern[0] / a.steps, "scatter_pc": kern[1] / a.steps, "scatter_sc": kern[2] / a.steps,
-                       "gather": kern[3] / a.steps, "gather_heavy": kern[4] / a.steps},
-        "roofline": {"bound": "hbm", "kernel": kinfo[dom]["kernel"], "achieved": kinfo[dom]["achieved"],
-                     "peak": hbm, "unit": "GB/s", "frac": kinfo[dom]["frac"], "traffic": traffic,
-                     "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": kinfo[dom]["algorithmic_bytes_per_launch"],
-                     "avg_launch_ms": kinfo[dom]["avg_launch_ms"],
-                     "all_kernels": [kinfo[i] for i in (1, 3, 4)]},
-        "gpu_launches": int(launches.sum() + 2 * 3 * a.steps),
+        "per_algo": per_algo,
+        "kernels_ms": {"k_plan": kern[0] / a.steps, "k_scatter_pc": kern[1] / a.steps,
+                       "k_scatter_sc": kern[2] / a.steps, "k_gather": kern[3] / a.steps,
+                       "k_gather_pc": kern[4] / a.steps},
+        "roofline": roofline,
+        "gpu_launches": int(launches.sum() + 2 * len(parts) * a.steps),  # + k_init and k_task_stats per run
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cpu,

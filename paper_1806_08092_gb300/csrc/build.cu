@@ -126,17 +126,32 @@ __global__ void k_heads(uint64_t E, uint32_t shift, uint32_t k, const uint32_t *
     }
 }
 
-// per sorted message j: bin boundary flags and histogram of messages / bins per row
-__global__ void k_msg_bins(uint64_t nmsg, uint32_t shift, uint32_t k, const uint64_t *skey, uint32_t *newbin,
-                           uint32_t *msgs_per_row, uint32_t *bins_per_row) {
+// per sorted message j: does it start a new bin?
+__global__ void k_msg_bins(uint64_t nmsg, uint32_t shift, const uint64_t *skey, uint32_t *newbin) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nmsg; j += stride) {
-        uint64_t pk = skey[j] >> shift;
-        uint32_t p = (uint32_t)(pk / k);
-        bool nbf = (j == 0) || ((skey[j - 1] >> shift) != pk);
-        newbin[j] = nbf;
-        atomicAdd(&msgs_per_row[p], 1u);
-        if (nbf) atomicAdd(&bins_per_row[p], 1u);
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nmsg; j += stride)
+        newbin[j] = (j == 0) || ((skey[j - 1] >> shift) != (skey[j] >> shift));
+}
+
+// Segment starts of keys sorted by seg(i) = (key[i] >> sh) / div, seg < nseg: start[s] = first index with
+// seg >= s for s in [0, nseg], start[nseg] = n.  Each boundary writes the starts it crosses (no atomics).
+__global__ void k_seg_starts(uint64_t n, const uint64_t *key, uint32_t sh, uint64_t div, uint32_t nseg,
+                             uint32_t *start) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= n; i += stride) {
+        const uint32_t hi = i < n ? (uint32_t)((key[i] >> sh) / div) : nseg;
+        const uint32_t lo = i == 0 ? 0u : (uint32_t)((key[i - 1] >> sh) / div) + 1;
+        for (uint32_t sg = lo; sg <= hi && sg <= nseg; ++sg) start[sg] = (uint32_t)i;
+    }
+}
+
+// per row p: messages and bins, from the row's message range and the inclusive scan of new-bin flags
+__global__ void k_row_counts(uint32_t k, const uint32_t *row_start, const uint32_t *binscan, uint32_t *msgs_row,
+                             uint32_t *bins_row) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x) {
+        const uint32_t a = row_start[p], b = row_start[p + 1];
+        msgs_row[p] = b - a;
+        bins_row[p] = b > a ? binscan[b - 1] - (a > 0 ? binscan[a - 1] : 0u) : 0u;
     }
 }
 
@@ -203,12 +218,9 @@ __global__ void k_pc_keys(uint64_t E, uint32_t shift, uint32_t P, const uint32_t
     }
 }
 
-__global__ void k_pc_unpack(uint64_t E, const uint64_t *key, uint32_t *pe, uint32_t *blk_hist) {
+__global__ void k_pc_unpack(uint64_t E, const uint64_t *key, uint32_t *pe) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < E; i += stride) {
-        pe[i] = (uint32_t)key[i];
-        atomicAdd(&blk_hist[key[i] >> 32], 1u);
-    }
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < E; i += stride) pe[i] = (uint32_t)key[i];
 }
 
 // SC bins are (source partition p, gather task t) pairs: key (p << 32) | t per edge
@@ -441,7 +453,8 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
     g->npng = nmsg;
 
     // 4. bins, rows, padded PNG slots
-    uint32_t *newbin, *binscan, *msgs_row, *msgs_row_pad;
+    uint32_t *newbin, *binscan, *msgs_row, *msgs_row_pad, *row_start;
+    GPOP_CUDA_TRY(t.alloc(&row_start, (uint64_t)k + 1));
     GPOP_CUDA_TRY(t.alloc(&newbin, nmsg));
     GPOP_CUDA_TRY(t.alloc(&binscan, nmsg));
     GPOP_CUDA_TRY(t.alloc(&msgs_row, (uint64_t)k + 1));
@@ -453,11 +466,14 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
     GPOP_CUDA_TRY(cudaMemsetAsync(msgs_row, 0, 4ull * (k + 1), s));
     GPOP_CUDA_TRY(cudaMemsetAsync(g->nbins_p, 0, 4ull * (k + 1), s));
     if (nmsg) {
-        k_msg_bins<<<blocks_for(nmsg), kThreads, 0, s>>>(nmsg, shift, k, skey, newbin, msgs_row, g->nbins_p);
+        k_msg_bins<<<blocks_for(nmsg), kThreads, 0, s>>>(nmsg, shift, skey, newbin);
         GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
             return cub::DeviceScan::InclusiveSum(tmp, bytes, newbin, binscan, nmsg, s);
         }));
     }
+    // messages are sorted by (row p, column q, source): row p = (key >> shift) / k
+    k_seg_starts<<<blocks_for(nmsg + 1), kThreads, 0, s>>>(nmsg, skey, shift, k, k, row_start);
+    k_row_counts<<<blocks_for(k), kThreads, 0, s>>>(k, row_start, binscan, msgs_row, g->nbins_p);
     GPOP_CUDA_TRY(cudaMemsetAsync(msgs_row + k, 0, 4, s));
     GPOP_CUDA_TRY(cudaMemcpyAsync(g->npng_p, msgs_row, 4ull * (k + 1), cudaMemcpyDeviceToDevice, s));
     GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
@@ -607,13 +623,11 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         if (nblocks)
             GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_blk_nval, blk_nval.data(), 4ull * nblocks, cudaMemcpyHostToDevice, s));
         // entries: sort keys (block, local destination, index in block)
-        uint32_t *d_cseq0, *d_colblk0, *blk_hist;
+        uint32_t *d_cseq0, *d_colblk0;
         GPOP_CUDA_TRY(t.alloc(&d_cseq0, nb + 1));
         GPOP_CUDA_TRY(t.alloc(&d_colblk0, (uint64_t)k + 1));
-        GPOP_CUDA_TRY(t.alloc(&blk_hist, (uint64_t)nblocks + 1));
         GPOP_CUDA_TRY(cudaMemcpyAsync(d_cseq0, cseq0.data(), 4ull * (nb + 1), cudaMemcpyHostToDevice, s));
         GPOP_CUDA_TRY(cudaMemcpyAsync(d_colblk0, col_blk0.data(), 4ull * (k + 1), cudaMemcpyHostToDevice, s));
-        GPOP_CUDA_TRY(cudaMemsetAsync(blk_hist, 0, 4ull * (nblocks + 1), s));
         if (E) {
             uint64_t *pk, *pk2;
             GPOP_CUDA_TRY(t.alloc(&pk, E));
@@ -630,11 +644,11 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
                     return cub::DeviceRadixSort::SortKeys(tmp, bytes, pk, pk2, E, 0, end_bit, s);
                 }));
             }
-            k_pc_unpack<<<blocks_for(E), kThreads, 0, s>>>(E, pk2, g->pe, blk_hist);
+            k_pc_unpack<<<blocks_for(E), kThreads, 0, s>>>(E, pk2, g->pe);
+            k_seg_starts<<<blocks_for(E + 1), kThreads, 0, s>>>(E, pk2, 32, 1, nblocks, g->pc_blk_ent);
+        } else {
+            GPOP_CUDA_TRY(cudaMemsetAsync(g->pc_blk_ent, 0, 4ull * (nblocks + 1), s));
         }
-        GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
-            return cub::DeviceScan::ExclusiveSum(tmp, bytes, blk_hist, g->pc_blk_ent, (uint64_t)nblocks + 1, s);
-        }));
         std::vector<uint32_t> hbe(nblocks + 1);
         GPOP_CUDA_TRY(cudaMemcpyAsync(hbe.data(), g->pc_blk_ent, 4ull * (nblocks + 1), cudaMemcpyDeviceToHost, s));
         GPOP_CUDA_TRY(cudaStreamSynchronize(s));
