@@ -34,6 +34,7 @@ constexpr int kGatherWarps = kGatherThreads / 32;
 constexpr int kScatterThreads = 256;
 constexpr int kPlanThreads = 1024;
 constexpr uint32_t kSent = 0xFFFFFFFFu;
+constexpr uint32_t kScUnitEdges = 1u << 16;  // active edges per SC scatter unit of a split partition
 constexpr uint32_t kBigScBin = 2048;     // SC bins at least this large are folded by the whole gather CTA
 constexpr uint32_t kMaxBigScBins = 64;
 constexpr int kPcWarps = kPcGatherWarps;          // k_gather_pc warps (one destination slice of a block each)
@@ -85,16 +86,18 @@ struct Params {
     double *t_res;
     uint32_t *t_stamp;
     uint8_t *mode, *action;
-    uint32_t *gflag, *gflag_pc, *sc_list, *counters;
+    uint32_t *gflag, *gflag_pc, *counters;
+    uint4 *sc_list;                   // SC scatter units: (partition, unit, units, active edges)
+    uint32_t *sc_gcur, *sc_udone;     // split SC partitions: bin cursors and finished units (zero at rest)
     Control *ctrl;
     const float *selector;  // learned selector parameters or null
     // work lists / timing used by the SC scatter and by the LOG_BOTH shadow launches
-    const uint32_t *list;        // partitions for k_scatter_sc
+    const uint4 *list;           // units for k_scatter_sc
     const uint32_t *list_count;  // number of entries in list
     uint32_t counter_slot;       // which counters[] entry the launch consumes
     uint32_t dry;                // shadow launch: do not publish bins or flags
     unsigned long long *t_task;  // per-task CTA durations (ns) or null
-    uint32_t *all_list;          // LOG_BOTH: every partition scattered this iteration
+    uint4 *all_list;             // LOG_BOTH: units of every partition scattered this iteration
     float *feat;                 // LOG_BOTH: per-partition selector features [k][8]
     uint32_t *part_va;           // LOG_BOTH: V_a per partition
     unsigned long long *part_ea; // LOG_BOTH: E_a per partition
@@ -376,13 +379,18 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
             nnull += (act == kActNull);
             p.action[q] = act;
         }
+        // SC scatter units: a partition with many active edges is split into ranges of about
+        // kScUnitEdges active edges, scattered by several CTAs
+        const uint32_t nu = Ea > 2ull * kScUnitEdges ? (uint32_t)min((unsigned long long)((Ea + kScUnitEdges - 1) / kScUnitEdges), 65535ull) : 1u;
         uint32_t total;
-        uint32_t off = block_excl_scan((valid && m == kModeSC) ? 1u : 0u, s_warp, &total);
-        if (valid && m == kModeSC) p.sc_list[sc_base + off] = q;
+        uint32_t off = block_excl_scan((valid && m == kModeSC) ? nu : 0u, s_warp, &total);
+        if (valid && m == kModeSC)
+            for (uint32_t j = 0; j < nu; ++j) p.sc_list[sc_base + off + j] = make_uint4(q, j, nu, (uint32_t)Ea);
         sc_base += total;
         if (p.log_both) {
-            uint32_t off2 = block_excl_scan((valid && m != kModeNone) ? 1u : 0u, s_warp, &total);
-            if (valid && m != kModeNone) p.all_list[all_base + off2] = q;
+            uint32_t off2 = block_excl_scan((valid && m != kModeNone) ? nu : 0u, s_warp, &total);
+            if (valid && m != kModeNone)
+                for (uint32_t j = 0; j < nu; ++j) p.all_list[all_base + off2 + j] = make_uint4(q, j, nu, (uint32_t)Ea);
             all_base += total;
         }
     }
@@ -416,7 +424,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         Control c;
         c.frontier_v = a; c.frontier_e = b; c.residual = r; c.model_bytes = by;
         c.n_pc = c0; c.n_sc = c1; c.n_null = c2; c.done = done; c.n_fallback = c3; c.error = p.ctrl->error;
-        c.pad[0] = c.pad[1] = 0;
+        c.n_sc_units = sc_base;
+        c.pad = 0;
         *p.ctrl = c;
         for (int i = 0; i < 8; ++i) p.counters[i] = 0;
         p.counters[7] = all_base;  // LOG_BOTH: size of all_list
@@ -484,29 +493,43 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_pc(Params p) {
 
 // --- SC scatter (Alg. 2 scatter in source-centric mode) ---------------------------------------
 
+// One CTA per work unit: a whole SC partition, or one range of about kScUnitEdges active edges of a
+// partition with many (split partitions).  The partition's active vertices are taken in ascending order,
+// 1024 at a time, and their out-edges expanded one per thread; each pair goes to the sub-bin of its
+// (partition, gather task) at a cursor bumped once per distinct sub-bin per warp.  Whole partitions keep
+// their cursors in shared memory and publish the counts at the end; split partitions bump global cursors
+// (zero at rest), and their last unit to finish publishes the counts and resets the cursors.
 template <int ALGO>
 __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
-    extern __shared__ uint32_t s_cursor[];  // one insertion point per bin of the row
+    extern __shared__ uint32_t s_cursor[];  // one insertion point per bin of the row (whole partitions)
     __shared__ uint32_t s_list[1024];       // active local IDs of the current 1024-vertex segment
     __shared__ uint32_t s_pref[1025];       // exclusive prefix of their out-degrees
     __shared__ uint32_t s_warp[33];
-    __shared__ uint32_t s_task, s_nact;
+    __shared__ uint32_t s_task, s_nact, s_last;
     __shared__ unsigned long long s_t0;
     const int lane = threadIdx.x & 31;
-    const uint32_t nsc = *p.list_count;
+    const uint32_t nunits = *p.list_count;
     for (;;) {
         if (threadIdx.x == 0) s_task = atomicAdd(&p.counters[p.counter_slot], 1u);
         __syncthreads();
         uint32_t t = s_task;
         __syncthreads();
-        if (t >= nsc) break;
-        const uint32_t part = p.list[t];
+        if (t >= nunits) break;
+        const uint4 un = p.list[t];  // partition, unit, units, active edges
+        const uint32_t part = un.x;
+        const bool split = un.z > 1;
+        // active-edge range of this unit (in the order of the partition's active vertices)
+        const uint64_t ua = split ? (uint64_t)un.w * un.y / un.z : 0ull;
+        const uint64_t ub = split ? (uint64_t)un.w * (un.y + 1) / un.z : ~0ull;
         if (p.t_task && threadIdx.x == 0) s_t0 = globaltimer();
         const uint32_t rb0 = p.row_sub[part], nbr = p.row_sub[part + 1] - rb0;
-        for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) s_cursor[i] = 0;
+        if (!split)
+            for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) s_cursor[i] = 0;
+        uint32_t *cur = split ? p.sc_gcur + rb0 : s_cursor;
         const uint32_t g0 = part << p.shift;
         const uint32_t gend = min(g0 + p.P, p.V);
-        for (uint32_t seg = g0; seg < gend; seg += 1024) {
+        uint64_t run0 = 0;  // active edges of the partition before this segment
+        for (uint32_t seg = g0; seg < gend && run0 < ub; seg += 1024) {
             // active vertices of this segment, ascending
             if (threadIdx.x < 32) {
                 uint32_t gw = seg + threadIdx.x * 32;
@@ -534,10 +557,14 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
             }
             if (threadIdx.x == 0) s_pref[nact] = total;
             __syncthreads();
+            // this segment's active edges [run0, run0 + total) that belong to the unit
+            const uint64_t seg_lo = max(ua, run0), seg_hi = min(ub, run0 + total);
+            const uint32_t e_lo = seg_lo < seg_hi ? (uint32_t)(seg_lo - run0) : 0u;
+            const uint32_t e_hi = seg_lo < seg_hi ? (uint32_t)(seg_hi - run0) : 0u;
             // expand the active edges, one thread per edge
-            for (uint32_t base = 0; base < total; base += blockDim.x) {
+            for (uint32_t base = e_lo; base < e_hi; base += blockDim.x) {
                 uint32_t e = base + threadIdx.x;
-                bool live = e < total;
+                bool live = e < e_hi;
                 uint32_t lb = 0xFFFFFFFFu, dloc = 0, val = 0, slot = 0;
                 if (live) {
                     uint32_t lo = 0, hi = nact;  // largest i with s_pref[i] <= e
@@ -558,30 +585,48 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
                 int leader = __ffs(peers) - 1;
                 uint32_t rank = __popc(peers & ((1u << lane) - 1));
                 uint32_t basepos = 0;
-                if (live && lane == leader) basepos = atomicAdd(&s_cursor[lb], (uint32_t)__popc(peers));
+                if (live && lane == leader) basepos = atomicAdd(&cur[lb], (uint32_t)__popc(peers));
                 basepos = __shfl_sync(0xffffffffu, basepos, leader);
                 if (live) {
                     slot = p.sub_cap[rb0 + lb] + basepos + rank;
                     p.scpair[slot] = make_uint2(dloc, val);
                 }
             }
+            run0 += total;
             __syncthreads();
         }
         // publish counts and the 2-level active list (gPartList = gflag, binPartList = the gather
-        // task's list of fresh SC bins)
-        for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) {
-            uint32_t c = s_cursor[i];
-            if (c && !p.dry) {
-                uint32_t b = rb0 + i;
-                p.sccnt[b] = c;
-                uint32_t tsk = p.sub_task[b];
-                p.gflag[p.gtask[tsk].q] = p.epoch;
-                uint32_t pos = atomicAdd(&p.task_sc_cnt[tsk], 1u);
-                p.task_sc_list[p.task_sub_ptr[tsk] + pos] = b;
+        // task's list of fresh SC bins); a split partition publishes once, from its last unit
+        bool publish = !split;
+        if (split) {
+            if (threadIdx.x == 0) {
+                __threadfence();
+                s_last = atomicAdd(&p.sc_udone[part], 1u) == un.z - 1;
             }
+            __syncthreads();
+            publish = s_last != 0;
+            if (publish) __threadfence();
+        }
+        if (publish) {
+            for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) {
+                const uint32_t c = split ? atomicExch(&cur[i], 0u) : cur[i];
+                if (c && !p.dry) {
+                    uint32_t b = rb0 + i;
+                    p.sccnt[b] = c;
+                    uint32_t tsk = p.sub_task[b];
+                    p.gflag[p.gtask[tsk].q] = p.epoch;
+                    uint32_t pos = atomicAdd(&p.task_sc_cnt[tsk], 1u);
+                    p.task_sc_list[p.task_sub_ptr[tsk] + pos] = b;
+                }
+            }
+            if (split && threadIdx.x == 0) p.sc_udone[part] = 0;
         }
         __syncthreads();
-        if (p.t_task && threadIdx.x == 0) p.t_task[part] = globaltimer() - s_t0;
+        if (p.t_task && threadIdx.x == 0) {  // CTA time of the partition (units add up)
+            const unsigned long long dt = globaltimer() - s_t0;
+            if (split) atomicAdd(&p.t_task[part], dt);
+            else p.t_task[part] = dt;
+        }
     }
 }
 
@@ -1161,18 +1206,21 @@ struct RunBuffers {
     unsigned long long *t_ea = nullptr;
     double *t_res = nullptr;
     uint8_t *mode = nullptr, *action = nullptr;
-    uint32_t *gflag = nullptr, *gflag_pc = nullptr, *sc_list = nullptr, *counters = nullptr;
+    uint32_t *gflag = nullptr, *gflag_pc = nullptr, *counters = nullptr;
+    uint4 *sc_list = nullptr;
+    uint32_t *sc_gcur = nullptr, *sc_udone = nullptr;
     uint32_t *task_sc_cnt = nullptr, *task_sc_list = nullptr, *pc_sum = nullptr;
     Control *ctrl = nullptr, *h_ctrl = nullptr;
     // LOG_BOTH only (allocated on first use)
-    uint32_t *shadow = nullptr, *all_list = nullptr, *part_va = nullptr;
+    uint32_t *shadow = nullptr, *part_va = nullptr;
+    uint4 *all_list = nullptr;
     unsigned long long *part_ea = nullptr, *t_pc = nullptr, *t_sc = nullptr, *t_ga = nullptr;
     float *feat = nullptr;
 };
 
 static void release_runbufs(RunBuffers *rb) {
     void *ptrs[] = {rb->val, rb->lvl, rb->sval, rb->bits, rb->t_va, rb->t_stamp, rb->t_ea, rb->t_res,
-                    rb->mode, rb->action, rb->gflag, rb->gflag_pc, rb->sc_list, rb->counters,
+                    rb->mode, rb->action, rb->gflag, rb->gflag_pc, rb->sc_list, rb->sc_gcur, rb->sc_udone, rb->counters,
                     rb->ctrl, rb->task_sc_cnt, rb->task_sc_list, rb->pc_sum, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_ga,
                     rb->feat};
     for (void *q : ptrs)
@@ -1180,6 +1228,9 @@ static void release_runbufs(RunBuffers *rb) {
     if (rb->h_ctrl) cudaFreeHost(rb->h_ctrl);
     delete rb;
 }
+
+// SC scatter units of one iteration: one per SC partition plus one per kScUnitEdges active edges
+static uint64_t sc_unit_capacity(const Graph *g) { return (uint64_t)g->k + g->E / kScUnitEdges + 2; }
 
 static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
     RunBuffers *rb = new RunBuffers();
@@ -1200,7 +1251,9 @@ static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
     A(&rb->action, g->k);
     A(&rb->gflag, g->k);
     A(&rb->gflag_pc, g->k);
-    A(&rb->sc_list, g->k);
+    A(&rb->sc_list, sc_unit_capacity(g));
+    A(&rb->sc_gcur, std::max<uint64_t>(g->nsub, 1));
+    A(&rb->sc_udone, g->k);
     A(&rb->counters, 8);
     A(&rb->task_sc_cnt, g->ngt);
     A(&rb->pc_sum, g->V);
@@ -1212,6 +1265,8 @@ static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
     if (e == cudaSuccess) e = cudaMemset(rb->gflag_pc, 0, 4ull * g->k);
     if (e == cudaSuccess) e = cudaMemset(rb->task_sc_cnt, 0, 4ull * std::max<uint32_t>(g->ngt, 1));
     if (e == cudaSuccess) e = cudaMemset(rb->bits, 0, 4ull * nw);
+    if (e == cudaSuccess) e = cudaMemset(rb->sc_gcur, 0, 4ull * std::max<uint64_t>(g->nsub, 1));
+    if (e == cudaSuccess) e = cudaMemset(rb->sc_udone, 0, 4ull * g->k);
     if (e != cudaSuccess) {
         release_runbufs(rb);
         return fail(e == cudaErrorMemoryAllocation ? GPOP_ERR_OOM : GPOP_ERR_CUDA,
@@ -1303,9 +1358,9 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     p.val = rb->val; p.lvl = rb->lvl; p.sval = rb->sval; p.bits = rb->bits;
     p.t_va = rb->t_va; p.t_ea = rb->t_ea; p.t_res = rb->t_res; p.t_stamp = rb->t_stamp;
     p.mode = rb->mode; p.action = rb->action; p.gflag = rb->gflag; p.gflag_pc = rb->gflag_pc;
-    p.sc_list = rb->sc_list; p.counters = rb->counters; p.ctrl = rb->ctrl;
+    p.sc_list = rb->sc_list; p.sc_gcur = rb->sc_gcur; p.sc_udone = rb->sc_udone; p.counters = rb->counters; p.ctrl = rb->ctrl;
     p.selector = (o->mode == GPOP_MODE_LEARNED) ? selector_device_params() : nullptr;
-    p.list = rb->sc_list; p.list_count = &rb->ctrl->n_sc; p.counter_slot = 0; p.dry = 0; p.t_task = nullptr;
+    p.list = rb->sc_list; p.list_count = &rb->ctrl->n_sc_units; p.counter_slot = 0; p.dry = 0; p.t_task = nullptr;
     p.log_both = o->mode == GPOP_MODE_LOG_BOTH && o->log_buffer && o->log_capacity;
     if (p.log_both && !rb->shadow) {
         cudaError_t ae = cudaSuccess;
@@ -1313,7 +1368,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
             if (ae == cudaSuccess) ae = dalloc(g, ptr, n);
         };
         A(&rb->shadow, g->npng_pad);
-        A(&rb->all_list, g->k);
+        A(&rb->all_list, sc_unit_capacity(g));
         A(&rb->part_va, g->k);
         A(&rb->part_ea, g->k);
         A(&rb->t_pc, g->nst);
@@ -1364,6 +1419,9 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
 
     // initial frontier (Alg. 4 driver: loadFrontier and initial values)
     p.epoch = ++g->epoch;
+    // split-SC cursors are zero at rest; reset them in case an earlier run stopped part-way
+    GPOP_CUDA_TRY(cudaMemsetAsync(rb->sc_gcur, 0, 4ull * std::max<uint64_t>(g->nsub, 1), s));
+    GPOP_CUDA_TRY(cudaMemsetAsync(rb->sc_udone, 0, 4ull * g->k, s));
     k_init<ALGO><<<std::max(1, std::min((int)((g->V / 32 + 255) / 256), 4096)), 256, 0, s>>>(p);
     k_task_stats<<<std::max(1, std::min((int)g->ngt, 8 * g->num_sms)), kGatherThreads, 0, s>>>(p);
     GPOP_CUDA_TRY(cudaGetLastError());
@@ -1443,6 +1501,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
             Params q2 = p;
             q2.dry = 1; q2.counter_slot = 4; q2.list = rb->all_list; q2.list_count = &rb->counters[7];
             q2.t_task = rb->t_sc;
+            cudaMemsetAsync(rb->t_sc, 0, 8ull * g->k, s);  // split partitions add their units' CTA times
             k_scatter_sc<ALGO><<<grid_sc, kScatterThreads, sc_smem, s>>>(q2);
         }
         Params ps = p;

@@ -44,7 +44,8 @@ struct Control {
     uint32_t done;                   // 1 = stop before scattering this iteration
     uint32_t n_fallback;             // learned mode: partitions that fell back to Eq. (mode)
     uint32_t error;                  // device check flags
-    uint32_t pad[2];
+    uint32_t n_sc_units;             // SC scatter work units (split hub partitions count several)
+    uint32_t pad;
 };
 
 // Static gather task: destinations [d0, d1) (local IDs) of column q.

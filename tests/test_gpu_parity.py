@@ -144,14 +144,15 @@ def test_large_partitions_multi_task_columns(case):
         g, P = gg.rmat(18).with_weights(), int(case.split("_p")[1])
     Gd = G(g, P)
     assert Gd.info()["num_pc_partials"] > 0
+    # force_sc also splits the hub partitions' SC scatter into edge-range units (> 131072 active edges)
     ref, _, _ = O.pagerank(g, 0.85, max_iters=5)
-    for pol in ("analytic", "force_pc"):
+    for pol in ("analytic", "force_pc", "force_sc"):
         r = Gd.run("pagerank", max_iters=5, mode=pol)
         assert pr_err(r.values.cpu().numpy(), ref) <= PR_TOL, pol
     root = int(gg.roots(g, 1)[0])
     level, parent = O.bfs(g, root)
     dist = u64_to_u32(O.sssp(g, root))
-    for pol in ("analytic", "force_pc"):
+    for pol in ("analytic", "force_pc", "force_sc"):
         r = Gd.run("bfs", source=root, mode=pol)
         assert np.array_equal(r.values.cpu().numpy(), level), pol
         assert np.array_equal(r.parent.cpu().numpy(), parent), pol
