@@ -25,7 +25,7 @@ gpop_status fail(gpop_status st, const std::string &msg) {
 void free_graph(Graph *g) {
     release_run_state(g);
     void *ptrs[] = {g->rowptr, g->col, g->w, g->esub, g->row_bin, g->bin_q, g->col_bin,
-                    g->col_bins, g->png, g->pdata, g->row_png, g->pc_runs, g->pc_blk_run, g->pc_blk_nval, g->pc_blk_ent,
+                    g->col_bins, g->png, g->pdata, g->row_png, g->pc_runs, g->pc_blk_run, g->pc_blk_nval, g->pc_blk_prange, g->pc_blk_ent,
                     g->pc_task, g->pc_tsp, g->pc_wsp, g->col_ntask, g->col_part0, g->pc_part, g->pe, g->pw,
                     g->scpair, g->sccnt, g->sub_cap, g->sub_task, g->row_sub, g->task_sub_ptr,
                     g->Ep, g->npng_p, g->nbins_p, g->gtask, g->col_task, g->stask, g->pc_state};
@@ -569,8 +569,9 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
     //    merged in column order by the filter.  Tasks are listed largest first.
     {
         const uint32_t nb = (uint32_t)g->nb;
-        std::vector<uint32_t> hj0(nb + 1), hslot0(nb), hcolbins(nb), hcolbin(k + 1);
+        std::vector<uint32_t> hj0(nb + 1), hslot0(nb), hcolbins(nb), hcolbin(k + 1), hbinp(nb);
         if (nb) {
+            GPOP_CUDA_TRY(cudaMemcpyAsync(hbinp.data(), bin_p, 4ull * nb, cudaMemcpyDeviceToHost, s));
             GPOP_CUDA_TRY(cudaMemcpyAsync(hj0.data(), bin_j0, 4ull * nb, cudaMemcpyDeviceToHost, s));
             GPOP_CUDA_TRY(cudaMemcpyAsync(hslot0.data(), bin_slot0, 4ull * nb, cudaMemcpyDeviceToHost, s));
             GPOP_CUDA_TRY(cudaMemcpyAsync(hcolbins.data(), g->col_bins, 4ull * nb, cudaMemcpyDeviceToHost, s));
@@ -581,6 +582,7 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         std::vector<uint32_t> cseq0(nb + 1, 0), col_blk0(k + 1, 0);
         std::vector<uint4> runs;
         std::vector<uint32_t> blk_nval;  // staged values (padded messages) of every block
+        std::vector<uint2> blk_prange;   // source partitions of every block's bins (first, last)
         uint32_t nblocks = 0;
         for (uint32_t q = 0; q < k; ++q) {
             col_blk0[q] = nblocks;
@@ -593,8 +595,10 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
                 while (done < cnt) {  // split the bin's run at block boundaries
                     uint64_t pos = cs + done;
                     uint32_t piece = (uint32_t)std::min<uint64_t>(cnt - done, kPcBlock - pos % kPcBlock);
-                    runs.push_back(make_uint4(hslot0[b] + done, piece, (uint32_t)(pos % kPcBlock),
-                                              nblocks + (uint32_t)(pos / kPcBlock)));
+                    const uint32_t blk = nblocks + (uint32_t)(pos / kPcBlock);
+                    runs.push_back(make_uint4(hslot0[b] + done, piece, (uint32_t)(pos % kPcBlock), blk));
+                    if (blk >= blk_prange.size()) blk_prange.push_back(make_uint2(hbinp[b], hbinp[b]));
+                    else blk_prange[blk].y = hbinp[b];  // bins of a column come in ascending source order
                     done += piece;
                 }
                 cs += cnt;
@@ -620,6 +624,10 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
             GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_runs, runs.data(), sizeof(uint4) * runs.size(), cudaMemcpyHostToDevice, s));
         GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_blk_run, blk_run0.data(), 4ull * (nblocks + 1), cudaMemcpyHostToDevice, s));
         GPOP_CUDA_TRY(dalloc(g, &g->pc_blk_nval, (uint64_t)nblocks + 1));
+        GPOP_CUDA_TRY(dalloc(g, &g->pc_blk_prange, (uint64_t)nblocks + 1));
+        if (blk_prange.size() != nblocks) return fail(GPOP_ERR_CUDA, "PC block layout: a block without runs");
+        if (nblocks)
+            GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_blk_prange, blk_prange.data(), sizeof(uint2) * nblocks, cudaMemcpyHostToDevice, s));
         if (nblocks)
             GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_blk_nval, blk_nval.data(), 4ull * nblocks, cudaMemcpyHostToDevice, s));
         // entries: sort keys (block, local destination, index in block)

@@ -66,6 +66,8 @@ struct Params {
     // PC gather blocks
     const uint4 *pc_runs, *pc_task;
     const uint32_t *pc_wsp, *pc_tsp;  // per task block: kPcWarps+1 entry splits; per task: first split row
+    const uint2 *pc_blk_prange;       // per block: first and last source partition of its bins
+    uint32_t *pc_prefix;              // per iteration: PC partitions before p (k+1 entries)
     const uint32_t *pc_blk_run, *pc_blk_nval, *pc_blk_ent, *col_ntask, *col_part0, *pe;
     const int32_t *pw;
     uint32_t *pc_part;
@@ -91,12 +93,15 @@ struct Params {
     uint32_t *sc_gcur, *sc_udone;     // split SC partitions: bin cursors and finished units (zero at rest)
     Control *ctrl;
     const float *selector;  // learned selector parameters or null
+    uint8_t *sel_mode;      // k_select's per-partition choice (learned policy)
     // work lists / timing used by the SC scatter and by the LOG_BOTH shadow launches
     const uint4 *list;           // units for k_scatter_sc
     const uint32_t *list_count;  // number of entries in list
     uint32_t counter_slot;       // which counters[] entry the launch consumes
     uint32_t dry;                // shadow launch: do not publish bins or flags
     unsigned long long *t_task;  // per-task CTA durations (ns) or null
+    unsigned long long *t_gpc;   // LOG_BOTH: CTA time of k_gather_pc (ns, all CTAs) or null
+    unsigned long long *t_gsc;   // LOG_BOTH: CTA time of k_gather's SC passes (ns) or null
     uint4 *all_list;             // LOG_BOTH: units of every partition scattered this iteration
     float *feat;                 // LOG_BOTH: per-partition selector features [k][8]
     uint32_t *part_va;           // LOG_BOTH: V_a per partition
@@ -209,8 +214,12 @@ __device__ __forceinline__ void partition_features(uint64_t Va, uint64_t Ea, uin
 // Learned selector: MLP 8->32->32->1 (ReLU), lane j computes hidden unit j.
 // Returns 2 (PC), 1 (SC) or 0xFF when the features are outside the training
 // range (the caller then falls back to Eq. (mode)).  All lanes must call it.
-__device__ uint8_t learned_mode(const float *sp, const float f[8], int lane) {
-    const float *W1 = sp, *b1 = W1 + 256, *W2 = b1 + 32, *b2 = W2 + 1024, *W3 = b2 + 32, *b3 = W3 + 32;
+// MLP selector forward pass for one partition by one warp (lane j = hidden unit j).  w is the parameter
+// vector (gpop_selector_set layout) with W1 and W2 stored transposed, so that lanes read consecutive
+// words.  Returns kModePC iff the predicted log(t_PC / t_SC) <= 0, or 0xFF when a feature lies outside
+// the range seen in training (the caller then falls back to Eq. (mode)).
+__device__ uint8_t learned_mode(const float *w, const float f[8], int lane) {
+    const float *W1t = w, *b1 = W1t + 256, *W2t = b1 + 32, *b2 = W2t + 1024, *W3 = b2 + 32, *b3 = W3 + 32;
     const float *mean = b3 + 1, *sd = mean + 8, *fmin = sd + 8, *fmax = fmin + 8;
     bool in_range = true;
     float z[8];
@@ -221,10 +230,11 @@ __device__ uint8_t learned_mode(const float *sp, const float f[8], int lane) {
     }
     float h1 = b1[lane];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) h1 = fmaf(W1[lane * 8 + i], z[i], h1);
+    for (int i = 0; i < 8; ++i) h1 = fmaf(W1t[i * 32 + lane], z[i], h1);
     h1 = fmaxf(h1, 0.f);
     float h2 = b2[lane];
-    for (int i = 0; i < 32; ++i) h2 = fmaf(W2[lane * 32 + i], __shfl_sync(0xffffffffu, h1, i), h2);
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) h2 = fmaf(W2t[i * 32 + lane], __shfl_sync(0xffffffffu, h1, i), h2);
     h2 = fmaxf(h2, 0.f);
     float y = W3[lane] * h2;
 #pragma unroll
@@ -232,6 +242,42 @@ __device__ uint8_t learned_mode(const float *sp, const float f[8], int lane) {
     y += b3[0];
     if (!in_range) return 0xFF;
     return y <= 0.f ? kModePC : kModeSC;
+}
+
+// Learned SC/PC choice for every partition, ahead of k_plan (spec selector, Sec. 3.2's decision
+// made by the MLP): one warp per partition computes V_a and E_a from the previous iteration's gather-task
+// statistics (as k_plan does), the features and the forward pass, with the network staged in shared
+// memory.  Writes kModePC / kModeSC, 0xFF for a fallback to Eq. (mode), or kModeNone.
+constexpr int kSelectWarps = 8;
+__global__ void __launch_bounds__(32 * kSelectWarps) k_select(Params p) {
+    __shared__ float s_w[GPOP_SELECTOR_PARAMS];
+    for (int i = threadIdx.x; i < GPOP_SELECTOR_PARAMS; i += blockDim.x) {
+        int j = i;
+        if (i < 256) j = (i % 8) * 32 + i / 8;                                   // W1 [32][8] -> [8][32]
+        else if (i >= 288 && i < 1312) j = 288 + ((i - 288) % 32) * 32 + (i - 288) / 32;  // W2 transposed
+        s_w[j] = p.selector[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t prev = p.epoch - 1;
+    for (uint32_t q = blockIdx.x * kSelectWarps + wid; q < p.k; q += gridDim.x * kSelectWarps) {
+        unsigned long long Va = 0, Ea = 0;
+        for (uint32_t t = p.col_task[q] + lane; t < p.col_task[q + 1]; t += 32)
+            if (p.t_stamp[t] == prev) { Va += p.t_va[t]; Ea += p.t_ea[t]; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            Va += __shfl_xor_sync(0xffffffffu, Va, o);
+            Ea += __shfl_xor_sync(0xffffffffu, Ea, o);
+        }
+        const uint64_t Ep = p.Ep[q], np = p.npng_p[q];
+        uint8_t m = kModeNone;
+        if (Va != 0 && Ep != 0) {
+            float f[8];
+            partition_features(Va, Ea, Ep, np, p.k, p.row_bin[q + 1] - p.row_bin[q], p.bw_num, p.bw_den, f);
+            m = learned_mode(s_w, f, lane);
+        }
+        if (lane == 0) p.sel_mode[q] = m;
+    }
 }
 
 // --- initial frontier --------------------------------------------------------------------------
@@ -325,7 +371,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
     const uint32_t prev = p.epoch - 1;
     unsigned long long tv = 0, te = 0;
     double tr = 0.0, tb = 0.0;
-    uint32_t npc = 0, nsc = 0, nnull = 0, nfb = 0, sc_base = 0;
+    uint32_t npc = 0, nsc = 0, nnull = 0, nfb = 0, sc_base = 0, pc_base = 0;
 
     uint32_t all_base = 0;
     // partitions in chunks of blockDim so the SC list can be compacted in order
@@ -346,7 +392,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
             else if (p.policy == GPOP_MODE_FORCE_SC) m = kModeSC;
             else if (p.policy == GPOP_MODE_FORCE_PC) m = kModePC;
             else m = analytic_mode(p.k, Ep, np, Va, Ea, p.bw_num, p.bw_den);
-            if (m != kModeNone && (p.log_both || p.selector))
+            if (m != kModeNone && p.log_both)
                 partition_features(Va, Ea, Ep, np, p.k, p.row_bin[q + 1] - p.row_bin[q], p.bw_num, p.bw_den, f);
             if (p.log_both) {
                 for (int i = 0; i < 8; ++i) p.feat[(uint64_t)q * 8 + i] = f[i];
@@ -354,20 +400,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
                 p.part_ea[q] = Ea;
             }
         }
-        if (p.policy == GPOP_MODE_LEARNED && p.selector) {
-            // one warp evaluates the MLP for each of its 32 partitions in turn (uniform loop)
-            for (int j = 0; j < 32; ++j) {
-                uint8_t jm = (uint8_t)__shfl_sync(0xffffffffu, (uint32_t)m, j);
-                float fj[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) fj[i] = __shfl_sync(0xffffffffu, f[i], j);
-                if (jm == kModeNone) continue;
-                uint8_t lm = learned_mode(p.selector, fj, lane);
-                if (lane == j) {
-                    if (lm == 0xFF) nfb++;
-                    else m = lm;
-                }
-            }
+        if (p.policy == GPOP_MODE_LEARNED && p.selector && valid && m != kModeNone) {
+            const uint8_t lm = p.sel_mode[q];  // k_select's choice; 0xFF: features outside the training range
+            if (lm == 0xFF) nfb++;
+            else if (lm != kModeNone) m = lm;
         }
         if (valid) {
             p.mode[q] = m;
@@ -378,6 +414,12 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
             uint8_t act = m == kModePC ? kActPC : (p.pc_state[q] ? kActNull : kActSkip);
             nnull += (act == kActNull);
             p.action[q] = act;
+        }
+        {  // PC partitions before q: the PC gather skips blocks whose source partitions are none of them
+            uint32_t totp;
+            uint32_t offp = block_excl_scan((valid && m == kModePC) ? 1u : 0u, s_warp, &totp);
+            if (valid) p.pc_prefix[q] = pc_base + offp;
+            pc_base += totp;
         }
         // SC scatter units: a partition with many active edges is split into ranges of about
         // kScUnitEdges active edges, scattered by several CTAs
@@ -425,6 +467,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         c.frontier_v = a; c.frontier_e = b; c.residual = r; c.model_bytes = by;
         c.n_pc = c0; c.n_sc = c1; c.n_null = c2; c.done = done; c.n_fallback = c3; c.error = p.ctrl->error;
         c.n_sc_units = sc_base;
+        p.pc_prefix[p.k] = pc_base;
         c.pad = 0;
         *p.ctrl = c;
         for (int i = 0; i < 8; ++i) p.counters[i] = 0;
@@ -846,6 +889,7 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
     __shared__ uint32_t s_tsp;
     __shared__ uint32_t s_run[kPcTaskBlocks + 1], s_nval[kPcTaskBlocks];
     __shared__ uint32_t s_sp[kPcTaskBlocks * kSp];
+    __shared__ uint32_t s_blist[kPcTaskBlocks], s_na;  // blocks with a PC source this iteration
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t ns = p.pc_slots;
     uint32_t *ring = rings + (uint32_t)wid * ns * kSlotWords;
@@ -859,6 +903,7 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
         stage[kPcPadIdx] = kNull;  // value slot of the padding entries; the copies never write it
         stage[kStageWords + kPcPadIdx] = kNull;
     }
+    const unsigned long long t_start = p.t_gpc ? globaltimer() : 0ull;
     uint32_t gb = 0;         // blocks this CTA has passed through (buffer = gb & 1, use = gb >> 1)
     uint32_t ph = 0;         // this warp's ring slot phases (bit per slot)
     uint32_t head_slot = 0;  // this warp's next slot to fold; rounds in flight follow it
@@ -888,23 +933,46 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
         for (uint32_t i = threadIdx.x; i < nb * kSp; i += kPcThreads) s_sp[i] = p.pc_wsp[(uint64_t)s_tsp * kSp + i];
         const uint32_t gq = tk.x << p.shift;
         const uint32_t wq = min(p.P, p.V - gq);
+        // a block only holds NULLs unless one of its source partitions sent PC messages this iteration
+        if (threadIdx.x < nb) {
+            const uint2 pr = p.pc_blk_prange[tk.y + threadIdx.x];
+            s_blist[threadIdx.x] = p.pc_prefix[pr.y + 1] != p.pc_prefix[pr.x];
+        }
         for (uint32_t i = threadIdx.x; i < wq; i += kPcThreads) acc[i] = O::identity();
         __syncthreads();
-        pc_issue_values(p, s_run[0], s_run[1], s_nval[0], pc_first_run(p, s_run[0], s_run[1], lane, wid),
-                        stage + (gb & 1) * kStageWords, &s_full[gb & 1], lane, wid);
-        uint4 next_run = nb > 1 ? pc_first_run(p, s_run[1], s_run[2], lane, wid) : make_uint4(0, 0, 0, 0);
+        if (threadIdx.x == 0) {  // list the active blocks in order; empty the warp ranges of the others
+            uint32_t na = 0;
+            for (uint32_t i = 0; i < nb; ++i) {
+                if (s_blist[i]) {
+                    s_blist[na++] = i;
+                } else {
+                    for (uint32_t w = 1; w < kSp; ++w) s_sp[i * kSp + w] = s_sp[i * kSp];
+                }
+            }
+            s_na = na;
+        }
+        __syncthreads();
+        const uint32_t na = s_na;
+        if (na > 0)
+            pc_issue_values(p, s_run[s_blist[0]], s_run[s_blist[0] + 1], s_nval[s_blist[0]],
+                            pc_first_run(p, s_run[s_blist[0]], s_run[s_blist[0] + 1], lane, wid),
+                            stage + (gb & 1) * kStageWords, &s_full[gb & 1], lane, wid);
+        uint4 next_run = na > 1 ? pc_first_run(p, s_run[s_blist[1]], s_run[s_blist[1] + 1], lane, wid)
+                                : make_uint4(0, 0, 0, 0);
         PcCursor pc{0, s_sp[wid]};
         pc_skip_empty(s_sp, nb, wid, pc);
         PcCursor cc = pc;
         uint32_t inflight = 0;  // rounds issued and not yet folded
         bool ok = true, abort = false;
-        uint32_t i = 0;
-        for (; i < nb && !abort; ++i) {
-            const uint32_t g = gb + i, buf = g & 1, use = g >> 1;
-            if (i + 1 < nb) {  // the next block's values go to the other buffer, freed by the last barrier
-                pc_issue_values(p, s_run[i + 1], s_run[i + 2], s_nval[i + 1], next_run,
+        uint32_t j = 0;  // active blocks only: each one takes a value buffer and a barrier phase
+        for (; j < na && !abort; ++j) {
+            const uint32_t i = s_blist[j];
+            const uint32_t g = gb + j, buf = g & 1, use = g >> 1;
+            if (j + 1 < na) {  // the next block's values go to the other buffer, freed by the last barrier
+                const uint32_t i1 = s_blist[j + 1];
+                pc_issue_values(p, s_run[i1], s_run[i1 + 1], s_nval[i1], next_run,
                                 stage + (buf ^ 1) * kStageWords, &s_full[buf ^ 1], lane, wid);
-                if (i + 2 < nb) next_run = pc_first_run(p, s_run[i + 2], s_run[i + 3], lane, wid);
+                if (j + 2 < na) next_run = pc_first_run(p, s_run[s_blist[j + 2]], s_run[s_blist[j + 2] + 1], lane, wid);
             }
             if (ok && cc.i == i && !mbar_wait(&s_full[buf], use & 1, &s_abort, &p.ctrl->error)) ok = false;
             while (ok && cc.i == i) {
@@ -942,23 +1010,24 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
             abort = __syncthreads_or(!ok) != 0;
         }
         if (abort) {  // let every copy still in flight land, then leave
-            const uint32_t last = gb + i - 1;  // block whose barrier saw the abort
+            const uint32_t last = gb + j - 1;  // block whose barrier saw the abort
             for (uint32_t k = 0; k < inflight; ++k) {
                 const uint32_t sl = head_slot + k >= ns ? head_slot + k - ns : head_slot + k;
                 mbar_drain(&sbar[sl], (ph >> sl) & 1u);
             }
             if (threadIdx.x == 0) {
                 mbar_drain(&s_full[last & 1], (last >> 1) & 1u);
-                if (i < nb) mbar_drain(&s_full[(last + 1) & 1], ((last + 1) >> 1) & 1u);
+                if (j < na) mbar_drain(&s_full[(last + 1) & 1], ((last + 1) >> 1) & 1u);
             }
             __syncthreads();
             break;
         }
-        gb += nb;
+        gb += na;
         __syncthreads();
         uint32_t *out = (tk.w == kNull) ? p.pc_sum + gq : p.pc_part + (uint64_t)tk.w * p.P;
         for (uint32_t i = threadIdx.x; i < wq; i += kPcThreads) out[i] = acc[i];
     }
+    if (p.t_gpc && threadIdx.x == 0) atomicAdd(p.t_gpc, globaltimer() - t_start);
 }
 
 // Folds one SC pair's value into a shared accumulator slot: an atomic minimum (BFS parents, CC labels,
@@ -1025,6 +1094,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
         // CTA-wide pass so that no single warp carries a hub partition's bin alone
         const uint32_t nfresh = p.task_sc_cnt[t];
         if (nfresh) {
+            const unsigned long long tsc0 = (p.t_gsc && tid == 0) ? globaltimer() : 0ull;
             const uint32_t lbase = p.task_sub_ptr[t];
             if (tid == 0) {
                 s_next = 0;
@@ -1063,6 +1133,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                 }
             }
             __syncthreads();
+            if (p.t_gsc && tid == 0) atomicAdd(p.t_gsc, globaltimer() - tsc0);
         }
 
         // reInit (init of previously active vertices), gather apply, filter, next frontier.
@@ -1205,23 +1276,24 @@ struct RunBuffers {
     uint32_t *t_va = nullptr, *t_stamp = nullptr;
     unsigned long long *t_ea = nullptr;
     double *t_res = nullptr;
-    uint8_t *mode = nullptr, *action = nullptr;
+    uint8_t *mode = nullptr, *action = nullptr, *sel_mode = nullptr;
     uint32_t *gflag = nullptr, *gflag_pc = nullptr, *counters = nullptr;
     uint4 *sc_list = nullptr;
-    uint32_t *sc_gcur = nullptr, *sc_udone = nullptr;
+    uint32_t *sc_gcur = nullptr, *sc_udone = nullptr, *pc_prefix = nullptr;
     uint32_t *task_sc_cnt = nullptr, *task_sc_list = nullptr, *pc_sum = nullptr;
     Control *ctrl = nullptr, *h_ctrl = nullptr;
     // LOG_BOTH only (allocated on first use)
     uint32_t *shadow = nullptr, *part_va = nullptr;
     uint4 *all_list = nullptr;
-    unsigned long long *part_ea = nullptr, *t_pc = nullptr, *t_sc = nullptr, *t_ga = nullptr;
+    unsigned long long *part_ea = nullptr, *t_pc = nullptr, *t_sc = nullptr, *t_gpc = nullptr, *t_gsc = nullptr;
+    double rate_pc = 0.0, rate_sc = 0.0;  // LOG_BOTH: gather ns per modelled byte, last measured per mode
     float *feat = nullptr;
 };
 
 static void release_runbufs(RunBuffers *rb) {
     void *ptrs[] = {rb->val, rb->lvl, rb->sval, rb->bits, rb->t_va, rb->t_stamp, rb->t_ea, rb->t_res,
-                    rb->mode, rb->action, rb->gflag, rb->gflag_pc, rb->sc_list, rb->sc_gcur, rb->sc_udone, rb->counters,
-                    rb->ctrl, rb->task_sc_cnt, rb->task_sc_list, rb->pc_sum, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_ga,
+                    rb->mode, rb->action, rb->sel_mode, rb->gflag, rb->gflag_pc, rb->sc_list, rb->sc_gcur, rb->sc_udone, rb->pc_prefix, rb->counters,
+                    rb->ctrl, rb->task_sc_cnt, rb->task_sc_list, rb->pc_sum, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_gpc, rb->t_gsc,
                     rb->feat};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -1249,11 +1321,13 @@ static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
     A(&rb->t_res, g->ngt);
     A(&rb->mode, g->k);
     A(&rb->action, g->k);
+    A(&rb->sel_mode, g->k);
     A(&rb->gflag, g->k);
     A(&rb->gflag_pc, g->k);
     A(&rb->sc_list, sc_unit_capacity(g));
     A(&rb->sc_gcur, std::max<uint64_t>(g->nsub, 1));
     A(&rb->sc_udone, g->k);
+    A(&rb->pc_prefix, (uint64_t)g->k + 1);
     A(&rb->counters, 8);
     A(&rb->task_sc_cnt, g->ngt);
     A(&rb->pc_sum, g->V);
@@ -1297,7 +1371,7 @@ static gpop_status log_iteration(Graph *g, RunBuffers *rb, const gpop_run_opts *
     const uint32_t k = g->k;
     std::vector<float> feat(8ull * k);
     std::vector<uint32_t> va(k);
-    std::vector<unsigned long long> ea(k), tpc(g->nst), tsc(k), tga(g->ngt);
+    std::vector<unsigned long long> ea(k), tpc(g->nst), tsc(k), tgpc(1, 0), tgsc(1, 0);
     std::vector<uint8_t> mode(k);
     std::vector<ScatterTask> stask(g->nst);
     GPOP_CUDA_TRY(cudaMemcpyAsync(feat.data(), rb->feat, 4ull * 8 * k, cudaMemcpyDeviceToHost, s));
@@ -1309,25 +1383,33 @@ static gpop_status log_iteration(Graph *g, RunBuffers *rb, const gpop_run_opts *
         GPOP_CUDA_TRY(cudaMemcpyAsync(stask.data(), g->stask, sizeof(ScatterTask) * g->nst, cudaMemcpyDeviceToHost, s));
     }
     GPOP_CUDA_TRY(cudaMemcpyAsync(tsc.data(), rb->t_sc, 8ull * k, cudaMemcpyDeviceToHost, s));
-    GPOP_CUDA_TRY(cudaMemcpyAsync(tga.data(), rb->t_ga, 8ull * g->ngt, cudaMemcpyDeviceToHost, s));
+    GPOP_CUDA_TRY(cudaMemcpyAsync(tgpc.data(), rb->t_gpc, 8, cudaMemcpyDeviceToHost, s));
+    GPOP_CUDA_TRY(cudaMemcpyAsync(tgsc.data(), rb->t_gsc, 8, cudaMemcpyDeviceToHost, s));
     GPOP_CUDA_TRY(cudaStreamSynchronize(s));
     std::vector<double> pc_ns(k, 0.0);
     for (uint32_t t = 0; t < g->nst; ++t)
         if (mode[stask[t].p] != kModeNone) pc_ns[stask[t].p] += (double)tpc[t];
-    double ga_ns = 0.0, ga_bytes = 0.0;
-    for (uint32_t t = 0; t < g->ngt; ++t) ga_ns += (double)tga[t];
+    // gather time per mode, attributed to the partitions of that mode by the bytes their messages make
+    // the gather read (PC: 4 B per message value + 4 B per destination entry, folded by k_gather_pc; SC:
+    // 8 B per pair, folded by k_gather's SC pass); the mode Eq. (mode) did not pick is charged at the last
+    // rate measured for it in this run (the other mode's rate until one is)
     auto gb = [&](uint32_t q, int m) {
-        return m == kModePC ? 4.0 * (double)g->h_npng[q] + 6.0 * (double)g->h_Ep[q] : 8.0 * (double)ea[q];
+        return m == kModePC ? 4.0 * (double)g->h_npng[q] + 4.0 * (double)g->h_Ep[q] : 8.0 * (double)ea[q];
     };
-    for (uint32_t q = 0; q < k; ++q)
-        if (mode[q] != kModeNone) ga_bytes += gb(q, mode[q]);
-    const double nspb = ga_bytes > 0 ? ga_ns / ga_bytes : 0.0;
+    double bytes_pc = 0.0, bytes_sc = 0.0;
+    for (uint32_t q = 0; q < k; ++q) {
+        if (mode[q] == kModePC) bytes_pc += gb(q, kModePC);
+        if (mode[q] == kModeSC) bytes_sc += gb(q, kModeSC);
+    }
+    if (bytes_pc > 0) rb->rate_pc = (double)tgpc[0] / bytes_pc;
+    if (bytes_sc > 0) rb->rate_sc = (double)tgsc[0] / bytes_sc;
+    const double rpc = rb->rate_pc > 0 ? rb->rate_pc : rb->rate_sc, rsc = rb->rate_sc > 0 ? rb->rate_sc : rb->rate_pc;
     for (uint32_t q = 0; q < k; ++q) {
         if (mode[q] == kModeNone || st->log_records >= o->log_capacity) continue;
         float *r = o->log_buffer + st->log_records * GPOP_LOG_RECORD_FLOATS;
         for (int i = 0; i < 8; ++i) r[i] = feat[8ull * q + i];
-        r[8] = (float)((pc_ns[q] + nspb * gb(q, kModePC)) / 1e3);
-        r[9] = (float)(((double)tsc[q] + nspb * gb(q, kModeSC)) / 1e3);
+        r[8] = (float)((pc_ns[q] + rpc * gb(q, kModePC)) / 1e3);
+        r[9] = (float)(((double)tsc[q] + rsc * gb(q, kModeSC)) / 1e3);
         r[10] = (float)mode[q];
         r[11] = (float)q;
         r[12] = (float)iter;
@@ -1340,13 +1422,13 @@ static gpop_status log_iteration(Graph *g, RunBuffers *rb, const gpop_run_opts *
 template <int ALGO>
 static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cudaStream_t s, void *out_values,
                             uint32_t *out_parent, int out_is_device, gpop_run_stats *stats) {
-    Params p;
+    Params p{};  // every field starts at zero / null
     memset(&p, 0, sizeof p);
     p.V = g->V; p.P = g->P; p.shift = g->shift; p.k = g->k;
     p.rowptr = g->rowptr; p.col = g->col; p.w = g->w; p.esub = g->esub;
     p.row_bin = g->row_bin; p.bin_q = g->bin_q; p.col_bin = g->col_bin; p.col_bins = g->col_bins;
     p.png = g->png; p.pdata = g->pdata; p.row_png = g->row_png;
-    p.pc_runs = g->pc_runs; p.pc_task = g->pc_task; p.pc_wsp = g->pc_wsp; p.pc_tsp = g->pc_tsp; p.pc_blk_run = g->pc_blk_run; p.pc_blk_nval = g->pc_blk_nval; p.pc_blk_ent = g->pc_blk_ent;
+    p.pc_runs = g->pc_runs; p.pc_task = g->pc_task; p.pc_wsp = g->pc_wsp; p.pc_tsp = g->pc_tsp; p.pc_blk_run = g->pc_blk_run; p.pc_blk_nval = g->pc_blk_nval; p.pc_blk_prange = g->pc_blk_prange; p.pc_blk_ent = g->pc_blk_ent;
     p.scpair = g->scpair; p.sccnt = g->sccnt;
     p.sub_cap = g->sub_cap; p.sub_task = g->sub_task; p.row_sub = g->row_sub; p.task_sub_ptr = g->task_sub_ptr;
     p.task_sc_cnt = rb->task_sc_cnt; p.task_sc_list = rb->task_sc_list;
@@ -1357,10 +1439,11 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     p.stask = g->stask; p.nst = g->nst; p.pc_state = g->pc_state;
     p.val = rb->val; p.lvl = rb->lvl; p.sval = rb->sval; p.bits = rb->bits;
     p.t_va = rb->t_va; p.t_ea = rb->t_ea; p.t_res = rb->t_res; p.t_stamp = rb->t_stamp;
-    p.mode = rb->mode; p.action = rb->action; p.gflag = rb->gflag; p.gflag_pc = rb->gflag_pc;
-    p.sc_list = rb->sc_list; p.sc_gcur = rb->sc_gcur; p.sc_udone = rb->sc_udone; p.counters = rb->counters; p.ctrl = rb->ctrl;
+    p.mode = rb->mode; p.action = rb->action; p.sel_mode = rb->sel_mode; p.gflag = rb->gflag; p.gflag_pc = rb->gflag_pc;
+    p.sc_list = rb->sc_list; p.sc_gcur = rb->sc_gcur; p.sc_udone = rb->sc_udone; p.pc_prefix = rb->pc_prefix; p.counters = rb->counters; p.ctrl = rb->ctrl;
     p.selector = (o->mode == GPOP_MODE_LEARNED) ? selector_device_params() : nullptr;
     p.list = rb->sc_list; p.list_count = &rb->ctrl->n_sc_units; p.counter_slot = 0; p.dry = 0; p.t_task = nullptr;
+    p.t_gpc = nullptr;
     p.log_both = o->mode == GPOP_MODE_LOG_BOTH && o->log_buffer && o->log_capacity;
     if (p.log_both && !rb->shadow) {
         cudaError_t ae = cudaSuccess;
@@ -1373,7 +1456,8 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         A(&rb->part_ea, g->k);
         A(&rb->t_pc, g->nst);
         A(&rb->t_sc, g->k);
-        A(&rb->t_ga, g->ngt);
+        A(&rb->t_gpc, 1);
+        A(&rb->t_gsc, 1);
         A(&rb->feat, 8ull * g->k);
         if (ae != cudaSuccess) return fail(GPOP_ERR_OOM, std::string("LOG_BOTH buffers: ") + cudaGetErrorString(ae));
     }
@@ -1422,6 +1506,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     // split-SC cursors are zero at rest; reset them in case an earlier run stopped part-way
     GPOP_CUDA_TRY(cudaMemsetAsync(rb->sc_gcur, 0, 4ull * std::max<uint64_t>(g->nsub, 1), s));
     GPOP_CUDA_TRY(cudaMemsetAsync(rb->sc_udone, 0, 4ull * g->k, s));
+    rb->rate_pc = rb->rate_sc = 0.0;
     k_init<ALGO><<<std::max(1, std::min((int)((g->V / 32 + 255) / 256), 4096)), 256, 0, s>>>(p);
     k_task_stats<<<std::max(1, std::min((int)g->ngt, 8 * g->num_sms)), kGatherThreads, 0, s>>>(p);
     GPOP_CUDA_TRY(cudaGetLastError());
@@ -1462,7 +1547,13 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     for (;;) {
         p.iter = iter + 1;
         p.epoch = ++g->epoch;
-        timed(0, [&] { k_plan<<<1, kPlanThreads, 0, s>>>(p); });
+        timed(0, [&] {
+            if (p.policy == GPOP_MODE_LEARNED && p.selector)
+                k_select<<<std::min<uint32_t>((g->k + kSelectWarps - 1) / kSelectWarps, 8u * g->num_sms),
+                           32 * kSelectWarps, 0, s>>>(p);
+            k_plan<<<1, kPlanThreads, 0, s>>>(p);
+        });
+        if (prof && p.policy == GPOP_MODE_LEARNED && p.selector) st.kernel_launches[0] += 1;  // k_select
         cudaError_t ce = cudaMemcpyAsync(rb->h_ctrl, rb->ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("plan: ") + cudaGetErrorString(ce)); break; }
@@ -1494,7 +1585,8 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         if (p.log_both) {
             // time both modes for every partition picked this iteration (shadow launches first:
             // the real SC scatter below rewrites the same bins with the same pairs)
-            cudaMemsetAsync(rb->t_ga, 0, 8ull * g->ngt, s);
+            cudaMemsetAsync(rb->t_gpc, 0, 8, s);
+            cudaMemsetAsync(rb->t_gsc, 0, 8, s);
             Params q1 = p;
             q1.pdata = rb->shadow; q1.dry = 1; q1.counter_slot = 3; q1.t_task = rb->t_pc;
             k_scatter_pc<<<grid_pc, kScatterThreads, 0, s>>>(q1);
@@ -1507,10 +1599,12 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         Params ps = p;
         ps.counter_slot = 1;
         Params pg = p;
-        pg.t_task = p.log_both ? rb->t_ga : nullptr;
+        pg.t_gsc = p.log_both ? rb->t_gsc : nullptr;
+        Params pgc = p;
+        pgc.t_gpc = p.log_both ? rb->t_gpc : nullptr;
         if (c.n_pc + c.n_null > 0) timed(1, [&] { k_scatter_pc<<<grid_pc, kScatterThreads, 0, s>>>(p); });
         if (c.n_sc > 0) timed(2, [&] { k_scatter_sc<ALGO><<<grid_sc, kScatterThreads, sc_smem, s>>>(ps); });
-        if (c.n_pc > 0) timed(4, [&] { k_gather_pc<ALGO><<<grid_gh, kPcThreads, gpc_smem, s>>>(p); });
+        if (c.n_pc > 0) timed(4, [&] { k_gather_pc<ALGO><<<grid_gh, kPcThreads, gpc_smem, s>>>(pgc); });
         timed(3, [&] { k_gather<ALGO><<<grid_ga, kGatherThreads, 0, s>>>(pg); });
         ce = cudaGetLastError();
         if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(ce)); break; }

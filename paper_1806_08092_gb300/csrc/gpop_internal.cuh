@@ -87,6 +87,7 @@ struct Graph {
     uint4 *pc_runs = nullptr;     // (row-major source slot, length, offset in block, block)
     uint32_t *pc_blk_run = nullptr;  // npcb+1: runs of each block
     uint32_t *pc_blk_nval = nullptr; // npcb: staged values of each block (a multiple of kBinAlign)
+    uint2 *pc_blk_prange = nullptr;  // npcb: first and last source partition of each block's bins
     uint32_t *pc_blk_ent = nullptr;  // npcb+1: entries of each block
     uint4 *pc_task = nullptr;     // npct: (column, first block, end block, partial slot or kNull), largest first
     uint32_t *pc_tsp = nullptr;   // npct: first row of the task's blocks in pc_wsp

@@ -131,6 +131,33 @@ def test_learned_mode_leaves_results_unchanged(gp):
         gp.selector_set(None)
 
 
+@pytest.mark.gpu
+def test_learned_policy_with_a_network_equal_to_the_model(gp):
+    # hand-set network whose output is feature 7 (the log of Eq. (mode)'s cost ratio) through off-diagonal
+    # weights: h1_0 = relu(f7), h1_1 = relu(-f7), h2_2 = relu(h1_0), h2_5 = relu(h1_1), y = h2_2 - h2_5; the
+    # learned policy must then pick Eq. (mode)'s modes in every iteration (a misplaced weight would not)
+    W1 = np.zeros((32, 8)); W1[0, 7], W1[1, 7] = 1.0, -1.0
+    W2 = np.zeros((32, 32)); W2[2, 0], W2[5, 1] = 1.0, 1.0
+    W3 = np.zeros(32); W3[2], W3[5] = 1.0, -1.0
+    params = np.zeros(gp.SELECTOR_PARAMS, dtype=np.float32)
+    params[:mlp.NW] = np.concatenate([W1.ravel(), np.zeros(32), W2.ravel(), np.zeros(32), W3, [0.0]])
+    params[mlp.NW + 8:mlp.NW + 16] = 1.0                 # std (mean 0)
+    params[mlp.NW + 16:mlp.NW + 24] = -1e30              # fmin
+    params[mlp.NW + 24:mlp.NW + 32] = 1e30               # fmax
+    g = gg.rmat(15).with_weights()
+    G = gp.Graph.from_csr(g.row_ptr, g.col, g.weights, partition_size=256)
+    gp.selector_set(params)
+    try:
+        for root in gg.roots(g, 2):
+            for algo in ("bfs", "sssp"):
+                a = G.run(algo, source=int(root), trace=True)
+                b = G.run(algo, source=int(root), mode="learned", trace=True)
+                assert np.array_equal(a.modes, b.modes), algo
+                assert b.stats["pc_partition_steps"] + b.stats["sc_partition_steps"] > 0
+    finally:
+        gp.selector_set(None)
+
+
 def features_np(Va, Ea, Ep, npng, k, row_bins, num=2, den=1):
     """Selector features in float64 (the engine computes the same quantities in FP32/FP64 on the device)."""
     cpc = 4.0 * (3 * npng + k + Ep) * den
