@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "GTEPS & % of HBM peak (RMAT-24 PR/BFS/SSSP); learned vs analytic mode speedup"
 PROFILES = os.path.join(ROOT, "profiles")
 ENGINE_SRC = os.path.join(ROOT, "paper_1806_08092_gb300", "csrc", "engine.cu")
+SELECTOR = os.path.join(ROOT, "paper_1806_08092_gb300", "selector_rmat.f32")
 
 
 def args_parse():
@@ -343,6 +344,30 @@ def run_ours(a, rank, world, local_rank):
                "d2h_bytes_per_step": int(d2h), "steps": a.e2e_steps,
                "includes": "H2D of the CSR from pinned memory, gpop_graph_build, three gpop_run calls, D2H of results"}
 
+    # learned vs analytic mode choice (outside the timed region): BFS and SSSP from two roots on this
+    # graph, median of 3 runs each, with the selector trained by selector_train.py
+    sel = None
+    if rank == 0 and os.path.exists(SELECTOR) and ("bfs" in parts or "sssp" in parts):
+        params = np.fromfile(SELECTOR, dtype=np.float32)
+        gp.selector_set(params)
+        try:
+            t = {"analytic": 0.0, "learned": 0.0}
+            same = True
+            for r in roots[:2]:
+                for algo in ("bfs", "sssp"):
+                    modes = {}
+                    for mode in ("analytic", "learned"):
+                        ms_ = [G.run(algo, source=int(r), mode=mode, trace=True) for _ in range(3)]
+                        t[mode] += float(np.median([x.stats["device_ms"] for x in ms_]))
+                        modes[mode] = ms_[-1].modes
+                    same &= bool(np.array_equal(modes["analytic"], modes["learned"]))
+            sel = {"speedup": t["analytic"] / t["learned"], "analytic_ms": t["analytic"], "learned_ms": t["learned"],
+                   "same_modes": same, "workload": f"rmat{a.scale} BFS + SSSP, 2 roots, median of 3 runs each",
+                   "selector": "selector_rmat.f32: MLP 8-32-32-1 trained by selector_train.py on LOG_BOTH timings "
+                               "of BFS/SSSP on RMAT 20-23 and uniform graphs"}
+        finally:
+            gp.selector_set(None)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -364,6 +389,7 @@ def run_ours(a, rank, world, local_rank):
                        "k_scatter_sc": kern[2] / a.steps, "k_gather": kern[3] / a.steps,
                        "k_gather_pc": kern[4] / a.steps},
         "roofline": roofline,
+        "learned_vs_analytic": sel,
         "gpu_launches": int(launches.sum() + 2 * len(parts) * a.steps),  # + k_init and k_task_stats per run
         "clocks": clk,
         "e2e": e2e,

@@ -93,7 +93,9 @@ struct Params {
     uint32_t *sc_gcur, *sc_udone;     // split SC partitions: bin cursors and finished units (zero at rest)
     Control *ctrl;
     const float *selector;  // learned selector parameters or null
-    uint8_t *sel_mode;      // k_select's per-partition choice (learned policy)
+    uint8_t *sel_mode;      // learned policy: per-partition choice for the next plan (k_select / k_gather tail)
+    uint32_t *col_done;     // learned policy: finished gather tasks per column (zero at rest)
+    uint32_t pc_skip;       // k_gather_pc: skip blocks without PC sources (some partition is not PC)
     // work lists / timing used by the SC scatter and by the LOG_BOTH shadow launches
     const uint4 *list;           // units for k_scatter_sc
     const uint32_t *list_count;  // number of entries in list
@@ -215,11 +217,15 @@ __device__ __forceinline__ void partition_features(uint64_t Va, uint64_t Ea, uin
 // Returns 2 (PC), 1 (SC) or 0xFF when the features are outside the training
 // range (the caller then falls back to Eq. (mode)).  All lanes must call it.
 // MLP selector forward pass for one partition by one warp (lane j = hidden unit j).  w is the parameter
-// vector (gpop_selector_set layout) with W1 and W2 stored transposed, so that lanes read consecutive
-// words.  Returns kModePC iff the predicted log(t_PC / t_SC) <= 0, or 0xFF when a feature lies outside
+// vector in the gpop_selector_set layout, with W1 and W2 transposed when kTransposed (a shared-memory
+// copy, so that lanes read consecutive words).  Returns kModePC iff the predicted log(t_PC / t_SC) <= 0, or 0xFF when a feature lies outside
 // the range seen in training (the caller then falls back to Eq. (mode)).
+template <bool kTransposed>
 __device__ uint8_t learned_mode(const float *w, const float f[8], int lane) {
     const float *W1t = w, *b1 = W1t + 256, *W2t = b1 + 32, *b2 = W2t + 1024, *W3 = b2 + 32, *b3 = W3 + 32;
+    // element (row j, column i) of W1 [32][8] / W2 [32][32] in the chosen layout
+    auto w1 = [&](int j, int i) { return kTransposed ? W1t[i * 32 + j] : W1t[j * 8 + i]; };
+    auto w2 = [&](int j, int i) { return kTransposed ? W2t[i * 32 + j] : W2t[j * 32 + i]; };
     const float *mean = b3 + 1, *sd = mean + 8, *fmin = sd + 8, *fmax = fmin + 8;
     bool in_range = true;
     float z[8];
@@ -230,11 +236,11 @@ __device__ uint8_t learned_mode(const float *w, const float f[8], int lane) {
     }
     float h1 = b1[lane];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) h1 = fmaf(W1t[i * 32 + lane], z[i], h1);
+    for (int i = 0; i < 8; ++i) h1 = fmaf(w1(lane, i), z[i], h1);
     h1 = fmaxf(h1, 0.f);
     float h2 = b2[lane];
 #pragma unroll 8
-    for (int i = 0; i < 32; ++i) h2 = fmaf(W2t[i * 32 + lane], __shfl_sync(0xffffffffu, h1, i), h2);
+    for (int i = 0; i < 32; ++i) h2 = fmaf(w2(lane, i), __shfl_sync(0xffffffffu, h1, i), h2);
     h2 = fmaxf(h2, 0.f);
     float y = W3[lane] * h2;
 #pragma unroll
@@ -244,10 +250,32 @@ __device__ uint8_t learned_mode(const float *w, const float f[8], int lane) {
     return y <= 0.f ? kModePC : kModeSC;
 }
 
-// Learned SC/PC choice for every partition, ahead of k_plan (spec selector, Sec. 3.2's decision
-// made by the MLP): one warp per partition computes V_a and E_a from the previous iteration's gather-task
-// statistics (as k_plan does), the features and the forward pass, with the network staged in shared
-// memory.  Writes kModePC / kModeSC, 0xFF for a fallback to Eq. (mode), or kModeNone.
+// Learned choice for partition q by one warp, from the gather-task statistics stamped `stamp` (the
+// network read from global memory); writes sel_mode[q].
+__device__ void select_partition(const Params &p, uint32_t q, uint32_t stamp, int lane) {
+    unsigned long long Va = 0, Ea = 0;
+    for (uint32_t t = p.col_task[q] + lane; t < p.col_task[q + 1]; t += 32)
+        if (__ldcg(&p.t_stamp[t]) == stamp) { Va += __ldcg(&p.t_va[t]); Ea += __ldcg(&p.t_ea[t]); }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Va += __shfl_xor_sync(0xffffffffu, Va, o);
+        Ea += __shfl_xor_sync(0xffffffffu, Ea, o);
+    }
+    const uint64_t Ep = p.Ep[q], np = p.npng_p[q];
+    uint8_t m = kModeNone;
+    if (Va != 0 && Ep != 0) {
+        float f[8];
+        partition_features(Va, Ea, Ep, np, p.k, p.row_bin[q + 1] - p.row_bin[q], p.bw_num, p.bw_den, f);
+        m = learned_mode<false>(p.selector, f, lane);
+    }
+    if (lane == 0) p.sel_mode[q] = m;
+}
+
+// Learned SC/PC choice for every partition (spec selector, Sec. 3.2's decision made by the MLP),
+// for the first iteration of a run: one warp per partition computes V_a and E_a from the initial
+// gather-task statistics (as k_plan does), the features and the forward pass, with the network staged
+// in shared memory.  Writes kModePC / kModeSC, 0xFF for a fallback to Eq. (mode), or kModeNone.  Later
+// iterations get their choices from the tail of k_gather (the last task of each column to finish).
 constexpr int kSelectWarps = 8;
 __global__ void __launch_bounds__(32 * kSelectWarps) k_select(Params p) {
     __shared__ float s_w[GPOP_SELECTOR_PARAMS];
@@ -274,7 +302,7 @@ __global__ void __launch_bounds__(32 * kSelectWarps) k_select(Params p) {
         if (Va != 0 && Ep != 0) {
             float f[8];
             partition_features(Va, Ea, Ep, np, p.k, p.row_bin[q + 1] - p.row_bin[q], p.bw_num, p.bw_den, f);
-            m = learned_mode(s_w, f, lane);
+            m = learned_mode<true>(s_w, f, lane);
         }
         if (lane == 0) p.sel_mode[q] = m;
     }
@@ -935,8 +963,8 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
         const uint32_t wq = min(p.P, p.V - gq);
         // a block only holds NULLs unless one of its source partitions sent PC messages this iteration
         if (threadIdx.x < nb) {
-            const uint2 pr = p.pc_blk_prange[tk.y + threadIdx.x];
-            s_blist[threadIdx.x] = p.pc_prefix[pr.y + 1] != p.pc_prefix[pr.x];
+            const uint2 pr = p.pc_skip ? p.pc_blk_prange[tk.y + threadIdx.x] : make_uint2(0, 0);
+            s_blist[threadIdx.x] = !p.pc_skip || p.pc_prefix[pr.y + 1] != p.pc_prefix[pr.x];
         }
         for (uint32_t i = threadIdx.x; i < wq; i += kPcThreads) acc[i] = O::identity();
         __syncthreads();
@@ -1047,7 +1075,7 @@ template <int ALGO>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
     using O = Op<ALGO>;
     __shared__ uint32_t s_acc[kGatherWidth];
-    __shared__ uint32_t s_task, s_next, s_nbig, s_big[kMaxBigScBins];
+    __shared__ uint32_t s_task, s_next, s_nbig, s_big[kMaxBigScBins], s_last;
     __shared__ uint32_t s_va[kGatherWarps];
     __shared__ unsigned long long s_ea[kGatherWarps];
     __shared__ double s_res[kGatherWarps];
@@ -1264,8 +1292,18 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
             p.t_res[t] = r;
             p.t_stamp[t] = p.epoch;
             if (p.t_task) p.t_task[t] = globaltimer() - t0;
+            s_last = 0;
+            if (p.col_done) {  // learned policy: the column's last task to finish picks its next mode
+                __threadfence();
+                s_last = atomicAdd(&p.col_done[q], 1u) == p.col_task[q + 1] - p.col_task[q] - 1;
+            }
         }
         __syncthreads();
+        if (s_last && wid == 0) {
+            __threadfence();
+            select_partition(p, q, p.epoch, lane);
+            if (lane == 0) p.col_done[q] = 0;
+        }
     }
 }
 
@@ -1277,6 +1315,7 @@ struct RunBuffers {
     unsigned long long *t_ea = nullptr;
     double *t_res = nullptr;
     uint8_t *mode = nullptr, *action = nullptr, *sel_mode = nullptr;
+    uint32_t *col_done = nullptr;
     uint32_t *gflag = nullptr, *gflag_pc = nullptr, *counters = nullptr;
     uint4 *sc_list = nullptr;
     uint32_t *sc_gcur = nullptr, *sc_udone = nullptr, *pc_prefix = nullptr;
@@ -1292,7 +1331,7 @@ struct RunBuffers {
 
 static void release_runbufs(RunBuffers *rb) {
     void *ptrs[] = {rb->val, rb->lvl, rb->sval, rb->bits, rb->t_va, rb->t_stamp, rb->t_ea, rb->t_res,
-                    rb->mode, rb->action, rb->sel_mode, rb->gflag, rb->gflag_pc, rb->sc_list, rb->sc_gcur, rb->sc_udone, rb->pc_prefix, rb->counters,
+                    rb->mode, rb->action, rb->sel_mode, rb->col_done, rb->gflag, rb->gflag_pc, rb->sc_list, rb->sc_gcur, rb->sc_udone, rb->pc_prefix, rb->counters,
                     rb->ctrl, rb->task_sc_cnt, rb->task_sc_list, rb->pc_sum, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_gpc, rb->t_gsc,
                     rb->feat};
     for (void *q : ptrs)
@@ -1322,6 +1361,7 @@ static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
     A(&rb->mode, g->k);
     A(&rb->action, g->k);
     A(&rb->sel_mode, g->k);
+    A(&rb->col_done, g->k);
     A(&rb->gflag, g->k);
     A(&rb->gflag_pc, g->k);
     A(&rb->sc_list, sc_unit_capacity(g));
@@ -1341,6 +1381,7 @@ static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
     if (e == cudaSuccess) e = cudaMemset(rb->bits, 0, 4ull * nw);
     if (e == cudaSuccess) e = cudaMemset(rb->sc_gcur, 0, 4ull * std::max<uint64_t>(g->nsub, 1));
     if (e == cudaSuccess) e = cudaMemset(rb->sc_udone, 0, 4ull * g->k);
+    if (e == cudaSuccess) e = cudaMemset(rb->col_done, 0, 4ull * g->k);
     if (e != cudaSuccess) {
         release_runbufs(rb);
         return fail(e == cudaErrorMemoryAllocation ? GPOP_ERR_OOM : GPOP_ERR_CUDA,
@@ -1507,6 +1548,9 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     GPOP_CUDA_TRY(cudaMemsetAsync(rb->sc_gcur, 0, 4ull * std::max<uint64_t>(g->nsub, 1), s));
     GPOP_CUDA_TRY(cudaMemsetAsync(rb->sc_udone, 0, 4ull * g->k, s));
     rb->rate_pc = rb->rate_sc = 0.0;
+    const bool learned = p.policy == GPOP_MODE_LEARNED && p.selector;
+    p.col_done = learned ? rb->col_done : nullptr;
+    if (learned) GPOP_CUDA_TRY(cudaMemsetAsync(rb->col_done, 0, 4ull * g->k, s));
     k_init<ALGO><<<std::max(1, std::min((int)((g->V / 32 + 255) / 256), 4096)), 256, 0, s>>>(p);
     k_task_stats<<<std::max(1, std::min((int)g->ngt, 8 * g->num_sms)), kGatherThreads, 0, s>>>(p);
     GPOP_CUDA_TRY(cudaGetLastError());
@@ -1547,13 +1591,16 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     for (;;) {
         p.iter = iter + 1;
         p.epoch = ++g->epoch;
+        // learned policy: the first plan's choices come from k_select, later ones from the previous
+        // gather's tail (the last task of each column)
+        const bool first_select = learned && iter == 0;
         timed(0, [&] {
-            if (p.policy == GPOP_MODE_LEARNED && p.selector)
+            if (first_select)
                 k_select<<<std::min<uint32_t>((g->k + kSelectWarps - 1) / kSelectWarps, 8u * g->num_sms),
                            32 * kSelectWarps, 0, s>>>(p);
             k_plan<<<1, kPlanThreads, 0, s>>>(p);
         });
-        if (prof && p.policy == GPOP_MODE_LEARNED && p.selector) st.kernel_launches[0] += 1;  // k_select
+        if (prof && first_select) st.kernel_launches[0] += 1;  // k_select
         cudaError_t ce = cudaMemcpyAsync(rb->h_ctrl, rb->ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("plan: ") + cudaGetErrorString(ce)); break; }
@@ -1602,6 +1649,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         pg.t_gsc = p.log_both ? rb->t_gsc : nullptr;
         Params pgc = p;
         pgc.t_gpc = p.log_both ? rb->t_gpc : nullptr;
+        pgc.pc_skip = c.n_pc < g->k;  // some partition is not PC: skip blocks whose sources all are not
         if (c.n_pc + c.n_null > 0) timed(1, [&] { k_scatter_pc<<<grid_pc, kScatterThreads, 0, s>>>(p); });
         if (c.n_sc > 0) timed(2, [&] { k_scatter_sc<ALGO><<<grid_sc, kScatterThreads, sc_smem, s>>>(ps); });
         if (c.n_pc > 0) timed(4, [&] { k_gather_pc<ALGO><<<grid_gh, kPcThreads, gpc_smem, s>>>(pgc); });

@@ -7,8 +7,10 @@
    (learned) on a held-out graph, same GPU, median over repetitions; plus the mispredicted-bytes regret
    of each policy judged by Eq. (mode)'s own byte model on held-out records.
 
-    python -m paper_1806_08092_gb300.selector_train --out selector.f32            # train on RMAT 20-23 + uniform
-    python -m paper_1806_08092_gb300.selector_train --params selector.f32 --eval-scale 25
+    python -m paper_1806_08092_gb300.selector_train --out paper_1806_08092_gb300/selector_rmat.f32   # train + eval
+    python -m paper_1806_08092_gb300.selector_train --params paper_1806_08092_gb300/selector_rmat.f32 --eval-scale 25
+
+`selector_rmat.f32` in this package was written by the first command; bench.py reads it.
 """
 from __future__ import annotations
 
