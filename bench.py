@@ -268,8 +268,8 @@ def run_ours(a, rank, world, local_rank):
     def total(key, field):
         return sum(s[key][field] for s in stats if key in s)
     te = sum(te_of.get(my_roots[a.warmup + i], 0) for i in range(a.steps))
-    kern = np.zeros(5)
-    launches = np.zeros(5, dtype=np.int64)
+    kern = np.zeros(6)
+    launches = np.zeros(6, dtype=np.int64)
     for s in stats:
         for key in s:
             kern += np.array(s[key]["kernel_ms"])
@@ -387,7 +387,7 @@ def run_ours(a, rank, world, local_rank):
         "per_algo": per_algo,
         "kernels_ms": {"k_plan": kern[0] / a.steps, "k_scatter_pc": kern[1] / a.steps,
                        "k_scatter_sc": kern[2] / a.steps, "k_gather": kern[3] / a.steps,
-                       "k_gather_pc": kern[4] / a.steps},
+                       "k_gather_pc": kern[4] / a.steps, "k_merge_pc": kern[5] / a.steps},
         "roofline": roofline,
         "learned_vs_analytic": sel,
         "gpu_launches": int(launches.sum() + 2 * len(parts) * a.steps),  # + k_init and k_task_stats per run

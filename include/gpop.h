@@ -152,10 +152,11 @@ typedef struct {
     double model_bytes;           /* sum of Sec. 3.2 bytes of the chosen modes */
     double device_ms;             /* CUDA-event time of the iteration loop */
     uint64_t log_records;         /* LOG_BOTH records written */
-    /* with opts.profile_kernels: per kernel (0 plan, 1 PC scatter, 2 SC scatter, 3 gather,
-       4 heavy-destination gather) the summed CUDA-event duration and the number of launches */
-    double kernel_ms[5];
-    uint64_t kernel_launches[5];
+    /* with opts.profile_kernels: per kernel kind (0 plan (+ learned selection), 1 PC scatter,
+       2 SC scatter, 3 task gather + filter, 4 PC gather, 5 merge of split columns' PC partials) the
+       summed CUDA-event duration and the number of launches */
+    double kernel_ms[6];
+    uint64_t kernel_launches[6];
 } gpop_run_stats;
 
 /* Fills opts with defaults: PageRank, d = 0.85, max_iters 1000, tol 0,

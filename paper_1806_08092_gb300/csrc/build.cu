@@ -26,7 +26,7 @@ void free_graph(Graph *g) {
     release_run_state(g);
     void *ptrs[] = {g->rowptr, g->col, g->w, g->esub, g->row_bin, g->bin_q, g->col_bin,
                     g->col_bins, g->png, g->pdata, g->row_png, g->pc_runs, g->pc_blk_run, g->pc_blk_nval, g->pc_blk_prange, g->pc_blk_ent,
-                    g->pc_task, g->pc_tsp, g->pc_wsp, g->col_ntask, g->col_part0, g->pc_part, g->pe, g->pw,
+                    g->pc_task, g->pc_tsp, g->pc_wsp, g->pc_merge, g->col_ntask, g->col_part0, g->pc_part, g->pe, g->pw,
                     g->scpair, g->sccnt, g->sub_cap, g->sub_task, g->row_sub, g->task_sub_ptr,
                     g->Ep, g->npng_p, g->nbins_p, g->gtask, g->col_task, g->stask, g->pc_state};
     for (void *p : ptrs)
@@ -563,7 +563,7 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
     //    that the gather stages in shared memory by coalesced copies of bin runs ("runs": row-major
     //    source offset, length, offset in the block).  Every PC in-entry becomes a 4-byte word
     //    (local destination << 16 | index in its block), sorted by (block, destination, index).
-    //    Gather tasks cover consecutive entries of one column: about max(kPcTaskMinEntries, E / (8 x
+    //    Gather tasks cover consecutive entries of one column: about max(kPcTaskMinEntries, E / (4 x
     //    SMs)) entries and at most kPcTaskBlocks blocks each, a block's entries split over several
     //    tasks when it is larger; a column with several tasks leaves one partial vector per task,
     //    merged in column order by the filter.  Tasks are listed largest first.
@@ -662,7 +662,7 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         GPOP_CUDA_TRY(cudaStreamSynchronize(s));
 
         // gather tasks over each column's entries
-        const uint64_t target = std::max<uint64_t>(kPcTaskMinEntries, E / (8ull * (uint64_t)std::max(1, g->num_sms)));
+        const uint64_t target = std::max<uint64_t>(kPcTaskMinEntries, E / (4ull * (uint64_t)std::max(1, g->num_sms)));
         std::vector<uint4> ptasks;
         std::vector<uint2> prng;
         std::vector<uint32_t> col_ntask(k, 0), col_part0(k, 0);
@@ -793,6 +793,19 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
                 g->device_bytes -= 4ull * (E + 4);
                 g->pw = pw2;
             }
+        }
+        // merge items: 1024-destination chunks of every column split over several tasks
+        {
+            std::vector<uint2> items;
+            for (uint32_t q = 0; q < k; ++q)
+                if (col_ntask[q] > 1) {
+                    const uint32_t wq = (uint32_t)std::min<uint64_t>(P, V - ((uint64_t)q << shift));
+                    for (uint32_t d0 = 0; d0 < wq; d0 += 1024) items.push_back(make_uint2(q, d0));
+                }
+            g->nmerge = (uint32_t)items.size();
+            GPOP_CUDA_TRY(dalloc(g, &g->pc_merge, items.size()));
+            if (!items.empty())
+                GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_merge, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice, s));
         }
         g->npct = (uint32_t)stasks.size();
         g->npart = nparts;

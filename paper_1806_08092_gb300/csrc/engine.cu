@@ -72,6 +72,8 @@ struct Params {
     const int32_t *pw;
     uint32_t *pc_part;
     uint32_t npct;
+    const uint2 *pc_merge;  // merge items of split columns
+    uint32_t nmerge;
     uint32_t pc_slots;  // entry ring slots per consumer warp of k_gather_pc (2..kPcMaxSlots)
     uint32_t *pc_sum;  // per vertex: combined PC message of the iteration (single-task columns)
     const uint32_t *Ep, *npng_p;
@@ -512,6 +514,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
 // --- PC scatter (Alg. 3) -----------------------------------------------------------------------
 
 __global__ void __launch_bounds__(kScatterThreads) k_scatter_pc(Params p) {
+    extern __shared__ __align__(16) uint32_t s_val[];  // the partition's P message values (PC rows)
     __shared__ uint32_t s_task;
     __shared__ unsigned long long s_t0;
     for (;;) {
@@ -535,18 +538,29 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_pc(Params p) {
             }
         }
         const uint32_t vbase = st.p << p.shift;
+        if (act == kActPC) {  // stage the partition's values (NULL for inactive sources), 16 B per load
+            const uint32_t wv = min(p.P, p.V - vbase);
+            for (uint32_t i = threadIdx.x * 4; i < wv; i += blockDim.x * 4) {
+                if (i + 4 <= wv) {
+                    *reinterpret_cast<uint4 *>(s_val + i) = *reinterpret_cast<const uint4 *>(p.sval + vbase + i);
+                } else {
+                    for (uint32_t c = i; c < wv; ++c) s_val[c] = p.sval[vbase + c];
+                }
+            }
+            __syncthreads();
+        }
         for (uint32_t i = st.beg + threadIdx.x * 8; i < st.end; i += blockDim.x * 8) {
             uint4 o0, o1;
-            if (act == kActPC) {
+            if (act == kActPC) {  // padding slots hold source 0: staged, never gathered
                 uint4 s = *reinterpret_cast<const uint4 *>(p.png + i);
-                o0.x = p.sval[vbase + (s.x & 0xFFFFu)];
-                o0.y = p.sval[vbase + (s.x >> 16)];
-                o0.z = p.sval[vbase + (s.y & 0xFFFFu)];
-                o0.w = p.sval[vbase + (s.y >> 16)];
-                o1.x = p.sval[vbase + (s.z & 0xFFFFu)];
-                o1.y = p.sval[vbase + (s.z >> 16)];
-                o1.z = p.sval[vbase + (s.w & 0xFFFFu)];
-                o1.w = p.sval[vbase + (s.w >> 16)];
+                o0.x = s_val[s.x & 0xFFFFu];
+                o0.y = s_val[s.x >> 16];
+                o0.z = s_val[s.y & 0xFFFFu];
+                o0.w = s_val[s.y >> 16];
+                o1.x = s_val[s.z & 0xFFFFu];
+                o1.y = s_val[s.z >> 16];
+                o1.z = s_val[s.w & 0xFFFFu];
+                o1.w = s_val[s.w >> 16];
             } else {
                 o0 = make_uint4(kNull, kNull, kNull, kNull);
                 o1 = o0;
@@ -1058,6 +1072,37 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
     if (p.t_gpc && threadIdx.x == 0) atomicAdd(p.t_gpc, globaltimer() - t_start);
 }
 
+// Result of the PC gather for the columns split over several k_gather_pc tasks: each 1024-destination
+// chunk of such a column combines the column's partial vectors in task order (a fixed order, so sums are
+// reproducible) into pc_sum; one chunk per CTA, 16-byte accesses.
+template <int ALGO>
+__global__ void __launch_bounds__(256) k_merge_pc(Params p) {
+    using O = Op<ALGO>;
+    for (uint32_t it = blockIdx.x; it < p.nmerge; it += gridDim.x) {
+        const uint2 m = p.pc_merge[it];  // column, first destination
+        if (p.gflag_pc[m.x] != p.epoch) continue;
+        const uint32_t gq = m.x << p.shift, wq = min(p.P, p.V - gq);
+        const uint32_t nt = p.col_ntask[m.x], part0 = p.col_part0[m.x];
+        const uint32_t i = m.y + threadIdx.x * 4;
+        if (i >= min(wq, m.y + 1024)) continue;
+        const uint32_t *src = p.pc_part + (uint64_t)part0 * p.P + i;
+        if (i + 4 <= wq) {
+            uint4 r = make_uint4(O::identity(), O::identity(), O::identity(), O::identity());
+            for (uint32_t j = 0; j < nt; ++j) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(src + (uint64_t)j * p.P);
+                r = make_uint4(O::combine(r.x, v.x), O::combine(r.y, v.y), O::combine(r.z, v.z), O::combine(r.w, v.w));
+            }
+            *reinterpret_cast<uint4 *>(p.pc_sum + gq + i) = r;
+        } else {
+            for (uint32_t c = i; c < wq; ++c) {
+                uint32_t r = O::identity();
+                for (uint32_t j = 0; j < nt; ++j) r = O::combine(r, src[(uint64_t)j * p.P + (c - i)]);
+                p.pc_sum[gq + c] = r;
+            }
+        }
+    }
+}
+
 // Folds one SC pair's value into a shared accumulator slot: an atomic minimum (BFS parents, CC labels,
 // SSSP distances: the result does not depend on the order) or a float addition (PR / PPR).
 template <int ALGO>
@@ -1067,8 +1112,8 @@ __device__ __forceinline__ void sc_fold(uint32_t *slot, uint32_t v) {
 }
 
 // Gather of one (column q, destination range) task, after k_gather_pc:
-//  1. PC messages: the column's PC result (pc_sum, or its tasks' partial vectors combined in column
-//     order), only when some partition sent PC messages to the column this iteration;
+//  1. PC messages: the column's PC result (pc_sum), only when some partition sent PC messages to the
+//     column this iteration;
 //  2. SC pairs of the task's fresh SC bins, folded with shared atomics;
 //  3. reInit / gather apply / filter of every destination of the range and the next frontier (Alg. 2).
 template <int ALGO>
@@ -1096,21 +1141,10 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
         const uint32_t gbase = gq + gt.d0;
         const uint32_t wv = min(width, p.V - gbase);  // destinations that exist
         if (p.gflag_pc[q] == p.epoch) {
-            // the column's PC result: one vector (pc_sum), several partial vectors merged in task
-            // order, or none (no PC in-edges)
-            const uint32_t nt = p.col_ntask[q], part0 = p.col_part0[q];
-            for (uint32_t i = tid; i < width; i += nthr) {
-                uint32_t r = O::identity();
-                if (i < wv) {
-                    if (nt == 1) {
-                        r = p.pc_sum[gbase + i];
-                    } else {
-                        for (uint32_t j = 0; j < nt; ++j)
-                            r = O::combine(r, p.pc_part[(uint64_t)(part0 + j) * p.P + gt.d0 + i]);
-                    }
-                }
-                s_acc[i] = r;
-            }
+            // the column's PC result (pc_sum: written by its k_gather_pc task, or merged by k_merge_pc
+            // from the partial vectors of a split column); none when the column has no PC in-edges
+            const bool has_pc = p.col_ntask[q] > 0;
+            for (uint32_t i = tid; i < width; i += nthr) s_acc[i] = (has_pc && i < wv) ? p.pc_sum[gbase + i] : O::identity();
         } else {
             for (uint32_t i = tid; i < width; i += nthr) s_acc[i] = O::identity();
         }
@@ -1469,7 +1503,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     p.rowptr = g->rowptr; p.col = g->col; p.w = g->w; p.esub = g->esub;
     p.row_bin = g->row_bin; p.bin_q = g->bin_q; p.col_bin = g->col_bin; p.col_bins = g->col_bins;
     p.png = g->png; p.pdata = g->pdata; p.row_png = g->row_png;
-    p.pc_runs = g->pc_runs; p.pc_task = g->pc_task; p.pc_wsp = g->pc_wsp; p.pc_tsp = g->pc_tsp; p.pc_blk_run = g->pc_blk_run; p.pc_blk_nval = g->pc_blk_nval; p.pc_blk_prange = g->pc_blk_prange; p.pc_blk_ent = g->pc_blk_ent;
+    p.pc_runs = g->pc_runs; p.pc_task = g->pc_task; p.pc_wsp = g->pc_wsp; p.pc_tsp = g->pc_tsp; p.pc_blk_run = g->pc_blk_run; p.pc_blk_nval = g->pc_blk_nval; p.pc_blk_prange = g->pc_blk_prange; p.pc_merge = g->pc_merge; p.nmerge = g->nmerge; p.pc_blk_ent = g->pc_blk_ent;
     p.scpair = g->scpair; p.sccnt = g->sccnt;
     p.sub_cap = g->sub_cap; p.sub_task = g->sub_task; p.row_sub = g->row_sub; p.task_sub_ptr = g->task_sub_ptr;
     p.task_sc_cnt = rb->task_sc_cnt; p.task_sc_list = rb->task_sc_list;
@@ -1518,7 +1552,10 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     const size_t sc_smem = sizeof(uint32_t) * std::max<uint32_t>(g->max_row_subs, 1);
     GPOP_CUDA_TRY(cudaFuncSetAttribute(k_scatter_sc<ALGO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sc_smem));
-    grid_pc = persistent_grid(k_scatter_pc, kScatterThreads, 0, g->num_sms);
+    // k_scatter_pc stages one partition's values (P words) in dynamic shared memory
+    const size_t spc_smem = sizeof(uint32_t) * (size_t)g->P;
+    GPOP_CUDA_TRY(cudaFuncSetAttribute(k_scatter_pc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spc_smem));
+    grid_pc = persistent_grid(k_scatter_pc, kScatterThreads, spc_smem, g->num_sms);
     grid_sc = persistent_grid(k_scatter_sc<ALGO>, kScatterThreads, sc_smem, g->num_sms);
     grid_ga = persistent_grid(k_gather<ALGO>, kGatherThreads, 0, g->num_sms);
     // k_gather_pc: column accumulator, two block value buffers and as many entry-chunk slots as the
@@ -1564,12 +1601,12 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     // optional per-kernel CUDA-event timing: a start/stop pair per kernel kind, resolved at the
     // next host synchronisation (which the plan's control read provides every iteration)
     const bool prof = o->profile_kernels != 0;
-    cudaEvent_t kev[10] = {};
-    bool pend[5] = {false, false, false, false, false};
+    cudaEvent_t kev[12] = {};
+    bool pend[6] = {false, false, false, false, false, false};
     if (prof)
         for (auto &ev : kev) GPOP_CUDA_TRY(cudaEventCreate(&ev));
     auto resolve = [&]() {
-        for (int i = 0; i < 5; ++i)
+        for (int i = 0; i < 6; ++i)
             if (pend[i]) {
                 float kms = 0.f;
                 cudaEventElapsedTime(&kms, kev[2 * i], kev[2 * i + 1]);
@@ -1636,7 +1673,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
             cudaMemsetAsync(rb->t_gsc, 0, 8, s);
             Params q1 = p;
             q1.pdata = rb->shadow; q1.dry = 1; q1.counter_slot = 3; q1.t_task = rb->t_pc;
-            k_scatter_pc<<<grid_pc, kScatterThreads, 0, s>>>(q1);
+            k_scatter_pc<<<grid_pc, kScatterThreads, spc_smem, s>>>(q1);
             Params q2 = p;
             q2.dry = 1; q2.counter_slot = 4; q2.list = rb->all_list; q2.list_count = &rb->counters[7];
             q2.t_task = rb->t_sc;
@@ -1650,9 +1687,13 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         Params pgc = p;
         pgc.t_gpc = p.log_both ? rb->t_gpc : nullptr;
         pgc.pc_skip = c.n_pc < g->k;  // some partition is not PC: skip blocks whose sources all are not
-        if (c.n_pc + c.n_null > 0) timed(1, [&] { k_scatter_pc<<<grid_pc, kScatterThreads, 0, s>>>(p); });
+        if (c.n_pc + c.n_null > 0) timed(1, [&] { k_scatter_pc<<<grid_pc, kScatterThreads, spc_smem, s>>>(p); });
         if (c.n_sc > 0) timed(2, [&] { k_scatter_sc<ALGO><<<grid_sc, kScatterThreads, sc_smem, s>>>(ps); });
-        if (c.n_pc > 0) timed(4, [&] { k_gather_pc<ALGO><<<grid_gh, kPcThreads, gpc_smem, s>>>(pgc); });
+        if (c.n_pc > 0) {
+            timed(4, [&] { k_gather_pc<ALGO><<<grid_gh, kPcThreads, gpc_smem, s>>>(pgc); });
+            if (g->nmerge)
+                timed(5, [&] { k_merge_pc<ALGO><<<std::min<uint32_t>(g->nmerge, 16u * g->num_sms), 256, 0, s>>>(p); });
+        }
         timed(3, [&] { k_gather<ALGO><<<grid_ga, kGatherThreads, 0, s>>>(pg); });
         ce = cudaGetLastError();
         if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(ce)); break; }

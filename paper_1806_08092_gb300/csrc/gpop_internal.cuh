@@ -22,14 +22,14 @@ constexpr int kPngAlign = 8;           // PNG rows padded to 8 entries (16-byte 
 constexpr uint32_t kBinAlign = 4;      // every bin padded to 4 slots: 16-byte aligned bulk copies of bin runs
 constexpr uint32_t kGatherWidth = 4096;  // max destinations per gather task (smem accumulator)
 constexpr uint32_t kGatherEntries = 32768;  // target in-entries per gather task
-constexpr uint32_t kScatterChunk = 16384;   // PNG entries per static PC scatter task
+constexpr uint32_t kScatterChunk = 131072;  // PNG slots per PC scatter task (one staging of the partition's values)
 constexpr uint32_t kMaxRowBins = 40960;     // SC scatter keeps one cursor per row bin in smem
 constexpr uint32_t kPcBlock = 8192;         // messages staged in shared memory per PC gather block
-constexpr uint32_t kPcTaskBlocks = 8;       // at most this many blocks per PC gather task
+constexpr uint32_t kPcTaskBlocks = 24;      // at most this many blocks per PC gather task (static smem: 17 words each)
 constexpr uint32_t kPcGatherWarps = 16;     // warps of the PC gather, one destination slice of a block each
 constexpr uint32_t kPcPad = 16;             // each warp's entry range of a block is padded to a multiple of this
 constexpr uint32_t kPcPadIdx = kPcBlock;    // block index of the padding entries (a value slot that holds NULL)
-constexpr uint32_t kPcTaskMinEntries = 65536;  // PC gather tasks hold about max(this, E / (8 SMs)) entries
+constexpr uint32_t kPcTaskMinEntries = 65536;  // PC gather tasks hold about max(this, E / (4 SMs)) entries
 
 enum Mode : uint8_t { kModeNone = 0, kModeSC = 1, kModePC = 2 };
 enum Action : uint8_t { kActSkip = 0, kActPC = 1, kActNull = 2 };
@@ -96,6 +96,9 @@ struct Graph {
     uint32_t *col_ntask = nullptr;   // k: PC gather tasks of the column (0 = no PC in-edges)
     uint32_t *col_part0 = nullptr;   // k: first partial slot of a multi-task column
     uint32_t *pc_part = nullptr;  // npart x P partial results
+    uint2 *pc_merge = nullptr;    // nmerge: (column, first destination) of each 1024-destination chunk of a
+                                  // column split over several tasks (its partials are merged into pc_sum)
+    uint32_t nmerge = 0;
     uint32_t *pe = nullptr;       // entries, sorted by (block, destination, index); each warp range of a task
                                   // block starts 16-aligned and is padded to a multiple of kPcPad
     int32_t *pw = nullptr;        // null or weights aligned with pe (padding: 0)
