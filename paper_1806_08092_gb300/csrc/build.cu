@@ -281,7 +281,11 @@ __global__ void k_warp_splits(uint32_t nrow, const uint32_t *lo, const uint32_t 
 }
 
 // Copies each warp range [old0, old0 + len) of the destination entries to new0, padded to a multiple of
-// kPcPad with entries that repeat the range's last destination and point to the NULL value slot.
+// kPcPad with entries that repeat the range's last destination and point to the padding value slot
+// (which holds the monoid identity in the gather).  Within
+// every 16-entry group g of a range, the four 16-byte quads are stored in the order quad ^ ((g >> 1) & 3):
+// a gather lane reads one group with 16-byte loads, and the swizzle spreads the eight lanes of each load
+// phase over distinct banks.
 __global__ void k_pad_entries(uint32_t nrange, const uint32_t *old0, const uint32_t *len, const uint32_t *new0,
                               const uint32_t *pe, const int32_t *pw, uint32_t *pe2, int32_t *pw2) {
     for (uint32_t r = blockIdx.x; r < nrange; r += gridDim.x) {
@@ -296,8 +300,10 @@ __global__ void k_pad_entries(uint32_t nrange, const uint32_t *old0, const uint3
             } else {
                 v = (pe[a + L - 1] & 0xFFFF0000u) | kPcPadIdx;
             }
-            pe2[b + i] = v;
-            if (pw2) pw2[b + i] = w;
+            const uint32_t grp = i / 16, quad = (i / 4) % 4;
+            const uint32_t o = grp * 16 + ((quad ^ ((grp >> 1) & 3u)) * 4) + (i % 4);
+            pe2[b + o] = v;
+            if (pw2) pw2[b + o] = w;
         }
     }
 }

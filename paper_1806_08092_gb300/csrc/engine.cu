@@ -793,22 +793,27 @@ __device__ __forceinline__ uint32_t pc_round_end(const uint32_t *sp, int w, cons
 // in registers, and the complete inner runs are folded into acc with batched, branch-free
 // read-modify-writes (inner runs of a lane have distinct destinations, and no other lane or warp touches
 // them; positions that end no inner run update the scratch word sink).  Padding entries repeat their
-// range's last destination and read the NULL value slot, so they fold as the identity.
+// range's last destination and read the padding value slot (the identity), so they fold as no-ops.
 template <int ALGO>
 __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt, uint32_t j0, const uint32_t *stage,
-                                        uint32_t *acc, uint32_t *sink, uint32_t &fd, uint32_t &head,
-                                        uint32_t &run_d, uint32_t &run_v, bool &in_head) {
+                                        uint32_t *acc, uint32_t *sink, bool check_null, uint32_t &fd,
+                                        uint32_t &head, uint32_t &run_d, uint32_t &run_v, bool &in_head) {
     using O = Op<ALGO>;
     constexpr uint32_t K = PcShape<ALGO>::K;
+    // quads of a 16-entry group are stored swizzled by (group >> 1) & 3 (see the build); the lane's
+    // entries start at round position j0, in group j0 / 16
+    const uint32_t gbase = j0 & ~15u, qsw = ((j0 >> 5) & 3u), q0 = (j0 & 15u) >> 2;
+    const bool nullable = ALGO == ALG_SSSP || ALGO == ALG_PPR || (ALGO == ALG_PR && check_null);
 #pragma unroll
     for (uint32_t hb = 0; hb < K; hb += 8) {
-        const uint4 e0 = *reinterpret_cast<const uint4 *>(ent + j0 + hb);
-        const uint4 e1 = *reinterpret_cast<const uint4 *>(ent + j0 + hb + 4);
+        const uint32_t o0 = gbase + (((q0 + hb / 4) ^ qsw) << 2), o1 = gbase + (((q0 + hb / 4 + 1) ^ qsw) << 2);
+        const uint4 e0 = *reinterpret_cast<const uint4 *>(ent + o0);
+        const uint4 e1 = *reinterpret_cast<const uint4 *>(ent + o1);
         const uint32_t ee[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
         int32_t ww[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (ALGO == ALG_SSSP) {
-            const int4 w0 = *reinterpret_cast<const int4 *>(wgt + j0 + hb);
-            const int4 w1 = *reinterpret_cast<const int4 *>(wgt + j0 + hb + 4);
+            const int4 w0 = *reinterpret_cast<const int4 *>(wgt + o0);
+            const int4 w1 = *reinterpret_cast<const int4 *>(wgt + o1);
             ww[0] = w0.x; ww[1] = w0.y; ww[2] = w0.z; ww[3] = w0.w;
             ww[4] = w1.x; ww[5] = w1.y; ww[6] = w1.z; ww[7] = w1.w;
         }
@@ -822,7 +827,8 @@ __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt
         uint32_t fk[8], fv[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const uint32_t v = (x[i] != kNull) ? O::weigh(x[i], ww[i]) : O::identity();
+            // NULL (0xFFFFFFFF) is the min identity, so BFS and CC fold it as is
+            const uint32_t v = (!nullable || x[i] != kNull) ? O::weigh(x[i], ww[i]) : O::identity();
             if (hb == 0 && i == 0) {
                 fd = run_d = d[0];
                 run_v = v;
@@ -856,13 +862,13 @@ __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt
 // a run cut by the round's end continues in the warp's next round, folded after this part.
 template <int ALGO>
 __device__ __forceinline__ void pc_round(const uint32_t *ent, const uint32_t *wgt, uint32_t n, const uint32_t *stage,
-                                         uint32_t *acc, uint32_t *sink, int lane) {
+                                         uint32_t *acc, uint32_t *sink, bool check_null, int lane) {
     using O = Op<ALGO>;
     constexpr uint32_t K = PcShape<ALGO>::K;
     const uint32_t j0 = lane * K;
     uint32_t fd = kSent, head = O::identity(), run_d = kSent, run_v = O::identity();
     bool in_head = true;
-    if (j0 < n) pc_lane<ALGO>(ent, wgt, j0, stage, acc, sink, fd, head, run_d, run_v, in_head);
+    if (j0 < n) pc_lane<ALGO>(ent, wgt, j0, stage, acc, sink, check_null, fd, head, run_d, run_v, in_head);
     const bool uni = in_head;  // all K positions share one destination
     const uint32_t ld = run_d;
     uint32_t S = run_v;
@@ -942,8 +948,10 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
         for (int i = 0; i < kPcWarps * (int)kPcMaxSlots; ++i) mbar_init(&s_slot[i], 1);
         fence_mbar_init();
         s_abort = 0;
-        stage[kPcPadIdx] = kNull;  // value slot of the padding entries; the copies never write it
-        stage[kStageWords + kPcPadIdx] = kNull;
+        // value slot of the padding entries (the copies never write it): the monoid identity, so padding
+        // folds as a no-op whether or not NULLs are checked
+        stage[kPcPadIdx] = O::identity();
+        stage[kStageWords + kPcPadIdx] = O::identity();
     }
     const unsigned long long t_start = p.t_gpc ? globaltimer() : 0ull;
     uint32_t gb = 0;         // blocks this CTA has passed through (buffer = gb & 1, use = gb >> 1)
@@ -1040,7 +1048,8 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
                 ph ^= 1u << head_slot;
                 const uint32_t e = pc_round_end<C>(s_sp, wid, cc);
                 const uint32_t *slot = ring + head_slot * kSlotWords;
-                pc_round<ALGO>(slot, slot + C, e - cc.s, stage + buf * kStageWords, acc, &s_sink, lane);
+                pc_round<ALGO>(slot, slot + C, e - cc.s, stage + buf * kStageWords, acc, &s_sink, p.pc_skip != 0,
+                               lane);
                 __syncwarp();  // the slot is refilled only after every lane has read it
                 --inflight;
                 head_slot = head_slot + 1 == ns ? 0 : head_slot + 1;

@@ -28,6 +28,7 @@ constexpr uint32_t kPcBlock = 8192;         // messages staged in shared memory 
 constexpr uint32_t kPcTaskBlocks = 24;      // at most this many blocks per PC gather task (static smem: 17 words each)
 constexpr uint32_t kPcGatherWarps = 16;     // warps of the PC gather, one destination slice of a block each
 constexpr uint32_t kPcPad = 16;             // each warp's entry range of a block is padded to a multiple of this
+                                            // (16-entry groups, quads swizzled by (group >> 1) & 3)
 constexpr uint32_t kPcPadIdx = kPcBlock;    // block index of the padding entries (a value slot that holds NULL)
 constexpr uint32_t kPcTaskMinEntries = 65536;  // PC gather tasks hold about max(this, E / (4 SMs)) entries
 
