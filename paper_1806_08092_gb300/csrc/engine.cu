@@ -39,7 +39,7 @@ constexpr uint32_t kBigScBin = 2048;     // SC bins at least this large are fold
 constexpr uint32_t kMaxBigScBins = 64;
 constexpr int kPcWarps = kPcGatherWarps;          // k_gather_pc warps (one destination slice of a block each)
 constexpr int kPcThreads = 32 * kPcWarps;
-constexpr uint32_t kPcMaxSlots = 4;               // entry ring depth per consumer warp
+constexpr uint32_t kPcMaxSlots = 3;               // entry ring depth limit per warp
 constexpr uint32_t kPcSpinLimit = 1u << 24;       // bounded mbarrier waits
 // destination entries a lane folds serially per round (SSSP also stages weights: half as many)
 template <int ALGO>

@@ -25,8 +25,8 @@ constexpr uint32_t kGatherEntries = 32768;  // target in-entries per gather task
 constexpr uint32_t kScatterChunk = 131072;  // PNG slots per PC scatter task (one staging of the partition's values)
 constexpr uint32_t kMaxRowBins = 40960;     // SC scatter keeps one cursor per row bin in smem
 constexpr uint32_t kPcBlock = 8192;         // messages staged in shared memory per PC gather block
-constexpr uint32_t kPcTaskBlocks = 24;      // at most this many blocks per PC gather task (static smem: 17 words each)
-constexpr uint32_t kPcGatherWarps = 16;     // warps of the PC gather, one destination slice of a block each
+constexpr uint32_t kPcTaskBlocks = 20;      // at most this many blocks per PC gather task (static smem per block)
+constexpr uint32_t kPcGatherWarps = 24;     // warps of the PC gather, one destination slice of a block each
 constexpr uint32_t kPcPad = 16;             // each warp's entry range of a block is padded to a multiple of this
                                             // (16-entry groups, quads swizzled by (group >> 1) & 3)
 constexpr uint32_t kPcPadIdx = kPcBlock;    // block index of the padding entries (a value slot that holds NULL)
