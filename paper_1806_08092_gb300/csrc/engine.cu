@@ -94,7 +94,7 @@ struct Params {
     uint4 *sc_list;                   // SC scatter units: (partition, unit, units, active edges)
     uint32_t *sc_gcur, *sc_udone;     // split SC partitions: bin cursors and finished units (zero at rest)
     Control *ctrl;
-    const float *selector;  // learned selector parameters or null
+    const float *selector;  // learned selector parameters (W1, W2 transposed) or null
     uint8_t *sel_mode;      // learned policy: per-partition choice for the next plan (k_select / k_gather tail)
     uint32_t *col_done;     // learned policy: finished gather tasks per column (zero at rest)
     uint32_t pc_skip;       // k_gather_pc: skip blocks without PC sources (some partition is not PC)
@@ -219,15 +219,10 @@ __device__ __forceinline__ void partition_features(uint64_t Va, uint64_t Ea, uin
 // Returns 2 (PC), 1 (SC) or 0xFF when the features are outside the training
 // range (the caller then falls back to Eq. (mode)).  All lanes must call it.
 // MLP selector forward pass for one partition by one warp (lane j = hidden unit j).  w is the parameter
-// vector in the gpop_selector_set layout, with W1 and W2 transposed when kTransposed (a shared-memory
-// copy, so that lanes read consecutive words).  Returns kModePC iff the predicted log(t_PC / t_SC) <= 0, or 0xFF when a feature lies outside
+// vector in the gpop_selector_set layout with W1 and W2 transposed, so that lanes read consecutive words.  Returns kModePC iff the predicted log(t_PC / t_SC) <= 0, or 0xFF when a feature lies outside
 // the range seen in training (the caller then falls back to Eq. (mode)).
-template <bool kTransposed>
 __device__ uint8_t learned_mode(const float *w, const float f[8], int lane) {
     const float *W1t = w, *b1 = W1t + 256, *W2t = b1 + 32, *b2 = W2t + 1024, *W3 = b2 + 32, *b3 = W3 + 32;
-    // element (row j, column i) of W1 [32][8] / W2 [32][32] in the chosen layout
-    auto w1 = [&](int j, int i) { return kTransposed ? W1t[i * 32 + j] : W1t[j * 8 + i]; };
-    auto w2 = [&](int j, int i) { return kTransposed ? W2t[i * 32 + j] : W2t[j * 32 + i]; };
     const float *mean = b3 + 1, *sd = mean + 8, *fmin = sd + 8, *fmax = fmin + 8;
     bool in_range = true;
     float z[8];
@@ -238,11 +233,11 @@ __device__ uint8_t learned_mode(const float *w, const float f[8], int lane) {
     }
     float h1 = b1[lane];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) h1 = fmaf(w1(lane, i), z[i], h1);
+    for (int i = 0; i < 8; ++i) h1 = fmaf(W1t[i * 32 + lane], z[i], h1);
     h1 = fmaxf(h1, 0.f);
     float h2 = b2[lane];
 #pragma unroll 8
-    for (int i = 0; i < 32; ++i) h2 = fmaf(w2(lane, i), __shfl_sync(0xffffffffu, h1, i), h2);
+    for (int i = 0; i < 32; ++i) h2 = fmaf(W2t[i * 32 + lane], __shfl_sync(0xffffffffu, h1, i), h2);
     h2 = fmaxf(h2, 0.f);
     float y = W3[lane] * h2;
 #pragma unroll
@@ -253,7 +248,7 @@ __device__ uint8_t learned_mode(const float *w, const float f[8], int lane) {
 }
 
 // Learned choice for partition q by one warp, from the gather-task statistics stamped `stamp` (the
-// network read from global memory); writes sel_mode[q].
+// network read from global memory, transposed layout: coalesced); writes sel_mode[q].
 __device__ void select_partition(const Params &p, uint32_t q, uint32_t stamp, int lane) {
     unsigned long long Va = 0, Ea = 0;
     for (uint32_t t = p.col_task[q] + lane; t < p.col_task[q + 1]; t += 32)
@@ -268,7 +263,7 @@ __device__ void select_partition(const Params &p, uint32_t q, uint32_t stamp, in
     if (Va != 0 && Ep != 0) {
         float f[8];
         partition_features(Va, Ea, Ep, np, p.k, p.row_bin[q + 1] - p.row_bin[q], p.bw_num, p.bw_den, f);
-        m = learned_mode<false>(p.selector, f, lane);
+        m = learned_mode(p.selector, f, lane);
     }
     if (lane == 0) p.sel_mode[q] = m;
 }
@@ -281,12 +276,7 @@ __device__ void select_partition(const Params &p, uint32_t q, uint32_t stamp, in
 constexpr int kSelectWarps = 8;
 __global__ void __launch_bounds__(32 * kSelectWarps) k_select(Params p) {
     __shared__ float s_w[GPOP_SELECTOR_PARAMS];
-    for (int i = threadIdx.x; i < GPOP_SELECTOR_PARAMS; i += blockDim.x) {
-        int j = i;
-        if (i < 256) j = (i % 8) * 32 + i / 8;                                   // W1 [32][8] -> [8][32]
-        else if (i >= 288 && i < 1312) j = 288 + ((i - 288) % 32) * 32 + (i - 288) / 32;  // W2 transposed
-        s_w[j] = p.selector[i];
-    }
+    for (int i = threadIdx.x; i < GPOP_SELECTOR_PARAMS; i += blockDim.x) s_w[i] = p.selector[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t prev = p.epoch - 1;
@@ -304,7 +294,7 @@ __global__ void __launch_bounds__(32 * kSelectWarps) k_select(Params p) {
         if (Va != 0 && Ep != 0) {
             float f[8];
             partition_features(Va, Ea, Ep, np, p.k, p.row_bin[q + 1] - p.row_bin[q], p.bw_num, p.bw_den, f);
-            m = learned_mode<true>(s_w, f, lane);
+            m = learned_mode(s_w, f, lane);
         }
         if (lane == 0) p.sel_mode[q] = m;
     }
@@ -1525,7 +1515,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     p.t_va = rb->t_va; p.t_ea = rb->t_ea; p.t_res = rb->t_res; p.t_stamp = rb->t_stamp;
     p.mode = rb->mode; p.action = rb->action; p.sel_mode = rb->sel_mode; p.gflag = rb->gflag; p.gflag_pc = rb->gflag_pc;
     p.sc_list = rb->sc_list; p.sc_gcur = rb->sc_gcur; p.sc_udone = rb->sc_udone; p.pc_prefix = rb->pc_prefix; p.counters = rb->counters; p.ctrl = rb->ctrl;
-    p.selector = (o->mode == GPOP_MODE_LEARNED) ? selector_device_params() : nullptr;
+    p.selector = (o->mode == GPOP_MODE_LEARNED) ? selector_device_params_transposed() : nullptr;
     p.list = rb->sc_list; p.list_count = &rb->ctrl->n_sc_units; p.counter_slot = 0; p.dry = 0; p.t_task = nullptr;
     p.t_gpc = nullptr;
     p.log_both = o->mode == GPOP_MODE_LOG_BOTH && o->log_buffer && o->log_capacity;

@@ -156,7 +156,8 @@ cudaError_t dalloc(Graph *g, T **p, uint64_t count) {
 
 void free_graph(Graph *g);
 void release_run_state(Graph *g);   // engine.cu
-const float *selector_device_params();  // selector.cu: installed MLP parameters or null
+const float *selector_device_params();             // selector.cu: installed MLP parameters or null
+const float *selector_device_params_transposed();  // the same with W1, W2 transposed (inference layout)
 
 }  // namespace gpop
 

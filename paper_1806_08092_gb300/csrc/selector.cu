@@ -29,7 +29,8 @@ constexpr int oW1 = 0, ob1 = oW1 + H * F, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 
 static_assert(ob3 + 1 == NW, "selector layout");
 
 std::mutex g_mu;
-float *g_dparams = nullptr;  // installed parameters (device), NP floats
+float *g_dparams = nullptr;    // installed parameters (device), NP floats
+float *g_dparams_t = nullptr;  // the same with W1 and W2 transposed (engine inference)
 
 // Forward pass, loss gradient and parameter gradients for samples
 // [blockIdx.x*S, +S); writes this block's gradient sums to part[blockIdx.x].
@@ -169,6 +170,11 @@ const float *selector_device_params() {
     return g_dparams;
 }
 
+const float *selector_device_params_transposed() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_dparams_t;
+}
+
 }  // namespace gpop
 
 using namespace gpop;
@@ -178,15 +184,25 @@ extern "C" gpop_status gpop_selector_set(const float *params) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!params) {
         if (g_dparams) cudaFree(g_dparams);
-        g_dparams = nullptr;
+        if (g_dparams_t) cudaFree(g_dparams_t);
+        g_dparams = g_dparams_t = nullptr;
         return GPOP_OK;
     }
     for (int i = 0; i < NP; ++i)
         if (!std::isfinite(params[i])) return fail(GPOP_ERR_INVALID_ARG, "selector parameters must be finite");
     for (int i = 0; i < F; ++i)
         if (!(params[NW + F + i] > 0.f)) return fail(GPOP_ERR_INVALID_ARG, "feature std must be positive");
+    // the engine's inference reads W1 [H][F] and W2 [H][H] column by column (lane j = hidden unit j), so it
+    // gets a copy with both matrices transposed; gpop_selector_get returns the layout that was set
+    std::vector<float> t(params, params + NP);
+    for (int j = 0; j < H; ++j) {
+        for (int i = 0; i < F; ++i) t[i * H + j] = params[j * F + i];
+        for (int i = 0; i < H; ++i) t[H * F + H + i * H + j] = params[H * F + H + j * H + i];
+    }
     if (!g_dparams) GPOP_CUDA_TRY(cudaMalloc((void **)&g_dparams, sizeof(float) * NP));
+    if (!g_dparams_t) GPOP_CUDA_TRY(cudaMalloc((void **)&g_dparams_t, sizeof(float) * NP));
     GPOP_CUDA_TRY(cudaMemcpy(g_dparams, params, sizeof(float) * NP, cudaMemcpyHostToDevice));
+    GPOP_CUDA_TRY(cudaMemcpy(g_dparams_t, t.data(), sizeof(float) * NP, cudaMemcpyHostToDevice));
     return GPOP_OK;
 }
 
