@@ -1,0 +1,164 @@
+"""Measurements of the synthetic configurations on one GPU, one JSON line per result.
+
+    python -m paper_1806_08092_gb300.report [--configs c1,c2,c3,ablation]
+
+c1        PageRank, 10 iterations, d = 0.85, RMAT-16 (P = 1024): time and GTEPS = 10 E / t.  The graph
+          and its bins fit in L2, so no HBM fraction is meaningful for it.
+c2        RMAT-22: BFS and SSSP (weights in [1, 255]) from 16 roots, TEPS = traversed edges / t (the
+          out-degrees of the reached vertices, Graph500 style), harmonic mean over the roots; CC on the
+          symmetrised graph, E_sym / t.  The partition size is swept over {2K, 4K, 8K, 16K} and every
+          setting is reported, the fastest marked.
+c3        PageRank to an L1 residual below 1e-9 on RMAT-24 and on a uniform random directed graph of the
+          same size and average degree: GTEPS = E x iterations / t and per-kernel times.
+ablation  RMAT-24 BFS and SSSP and symmetrised RMAT-24 CC with every partition forced to SC, forced to
+          PC, and with Eq. (mode): time, iterations and the number of PC / SC partition-steps.
+
+Times are CUDA-event device times of gpop_run (inputs resident on the GPU), median of three runs after
+a warm-up run unless stated.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+import torch
+
+from . import Graph
+
+KERNELS = ["k_plan", "k_scatter_pc", "k_scatter_sc", "k_gather", "k_gather_pc", "k_merge_pc"]
+
+
+def _gen():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import graphgen
+    return graphgen
+
+
+def _emit(d):
+    print(json.dumps(d), flush=True)
+
+
+def _median_run(G, algo, reps=3, **kw):
+    G.run(algo, **kw)  # warm-up
+    runs = [G.run(algo, profile=True, **kw) for _ in range(reps)]
+    runs.sort(key=lambda r: r.stats["device_ms"])
+    return runs[len(runs) // 2]
+
+
+def _traversed(g, values):
+    """Out-degree sum of the vertices a BFS reached (Graph500 traversed edges)."""
+    deg = torch.from_numpy(np.diff(g.row_ptr).astype(np.int64)).cuda()
+    return int(deg[values.to(torch.int64) != 0xFFFFFFFF].sum().item())
+
+
+def _kernels(stats):
+    return {k: round(v, 3) for k, v in zip(KERNELS, stats["kernel_ms"])}
+
+
+def c1():
+    gg = _gen()
+    g = gg.rmat(16)
+    G = Graph.from_csr(g.row_ptr, g.col, None, partition_size=1024)
+    r = _median_run(G, "pagerank", max_iters=10, tol=0.0)
+    ms = r.stats["device_ms"]
+    _emit({"config": "c1", "graph": "rmat16", "vertices": g.num_vertices, "edges": g.num_edges,
+           "partition_size": 1024, "algo": "pagerank", "iterations": r.stats["iterations"], "ms": ms,
+           "gteps": g.num_edges * r.stats["iterations"] / (ms / 1e3) / 1e9, "kernels_ms": _kernels(r.stats),
+           "note": "graph and bins are L2-resident"})
+    G.close()
+
+
+def c2(sizes=(2048, 4096, 8192, 16384), nroots=16):
+    gg = _gen()
+    g = gg.rmat(22).with_weights()
+    gs = gg.symmetrized(gg.rmat(22))
+    roots = [int(x) for x in gg.roots(g, nroots)]
+    results = []
+    for P in sizes:
+        G = Graph.from_csr(g.row_ptr, g.col, g.weights, partition_size=P)
+        out = {"config": "c2", "graph": "rmat22", "vertices": g.num_vertices, "edges": g.num_edges,
+               "partition_size": P}
+        total = 0.0
+        for algo in ("bfs", "sssp"):
+            teps, ms_all = [], 0.0
+            for r in roots:
+                res = _median_run(G, algo, reps=1, source=r)
+                te = _traversed(g, G.run("bfs", source=r).values) if algo == "sssp" else _traversed(g, res.values)
+                teps.append(te / (res.stats["device_ms"] / 1e3))
+                ms_all += res.stats["device_ms"]
+            out[algo] = {"gteps_harmonic_mean": len(teps) / sum(1.0 / t for t in teps) / 1e9,
+                         "ms_mean": ms_all / len(roots), "roots": len(roots)}
+            total += ms_all
+        G.close()
+        Gs = Graph.from_csr(gs.row_ptr, gs.col, None, partition_size=P)
+        rc = _median_run(Gs, "cc")
+        out["cc"] = {"edges_sym": gs.num_edges, "ms": rc.stats["device_ms"], "iterations": rc.stats["iterations"],
+                     "gteps": gs.num_edges / (rc.stats["device_ms"] / 1e3) / 1e9}
+        total += rc.stats["device_ms"]
+        Gs.close()
+        out["total_ms"] = total
+        results.append(out)
+    best = min(results, key=lambda o: o["total_ms"])
+    for o in results:
+        o["fastest"] = o is best
+        _emit(o)
+
+
+def c3():
+    gg = _gen()
+    n = 1 << 24
+    for name, g in (("rmat24", gg.rmat(24)), ("uniform24", gg.uniform(n, 16 * n))):
+        G = Graph.from_csr(g.row_ptr, g.col, None, partition_size=16384)
+        r = _median_run(G, "pagerank", max_iters=300, tol=1e-9)
+        ms, it = r.stats["device_ms"], r.stats["iterations"]
+        info = G.info()
+        _emit({"config": "c3", "graph": name, "vertices": g.num_vertices, "edges": g.num_edges,
+               "partition_size": 16384, "r": info["num_png"] / g.num_edges, "algo": "pagerank",
+               "iterations": it, "residual": r.stats["residual"], "converged": r.stats["converged"], "ms": ms,
+               "gteps": g.num_edges * it / (ms / 1e3) / 1e9, "kernels_ms": _kernels(r.stats)})
+        G.close()
+        del g
+
+
+def ablation():
+    gg = _gen()
+    g = gg.rmat(24).with_weights()
+    root = int(gg.roots(g, 1)[0])
+    G = Graph.from_csr(g.row_ptr, g.col, g.weights, partition_size=16384)
+    for algo in ("bfs", "sssp"):
+        for mode in ("force_sc", "force_pc", "analytic"):
+            r = _median_run(G, algo, source=root, mode=mode)
+            _emit({"config": "ablation", "graph": "rmat24", "algo": algo, "mode": mode, "root": root,
+                   "ms": r.stats["device_ms"], "iterations": r.stats["iterations"],
+                   "pc_partition_steps": r.stats["pc_partition_steps"],
+                   "sc_partition_steps": r.stats["sc_partition_steps"], "model_bytes": r.stats["model_bytes"],
+                   "kernels_ms": _kernels(r.stats)})
+    G.close()
+    del g
+    gs = gg.symmetrized(gg.rmat(24))
+    Gs = Graph.from_csr(gs.row_ptr, gs.col, None, partition_size=16384)
+    for mode in ("force_sc", "force_pc", "analytic"):
+        r = _median_run(Gs, "cc", mode=mode)
+        _emit({"config": "ablation", "graph": "rmat24_sym", "algo": "cc", "mode": mode, "edges": gs.num_edges,
+               "ms": r.stats["device_ms"], "iterations": r.stats["iterations"],
+               "pc_partition_steps": r.stats["pc_partition_steps"],
+               "sc_partition_steps": r.stats["sc_partition_steps"], "kernels_ms": _kernels(r.stats)})
+    Gs.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--configs", default="c1,c2,c3,ablation")
+    a = ap.parse_args()
+    fns = {"c1": c1, "c2": c2, "c3": c3, "ablation": ablation}
+    for c in a.configs.split(","):
+        fns[c]()
+
+
+if __name__ == "__main__":
+    main()
