@@ -126,7 +126,8 @@ typedef struct {
     int32_t mode;              /* gpop_mode_policy */
     uint32_t bw_ratio_num;     /* BW_PC / BW_SC = num / den (Sec. 3.2 default 2/1) */
     uint32_t bw_ratio_den;
-    int32_t msg_bf16;          /* reserved, must be 0 (FP32 messages) */
+    int32_t msg_bf16;          /* PageRank / PPR only: non-zero sends messages through the bins as BF16
+                                  (round to nearest even), gathered in FP32; other algorithms: must be 0 */
     int32_t profile_kernels;   /* non-zero: time every kernel launch with CUDA events (stats.kernel_*) */
     void *cuda_stream;         /* stream for all kernels of the run */
     uint8_t *trace_modes;      /* optional HOST buffer of max_iters * k bytes: per iteration and

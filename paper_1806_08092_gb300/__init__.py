@@ -126,8 +126,10 @@ class Graph:
 
     def run(self, algo: str, source: int = 0, damping: float = 0.85, max_iters: int = 1000, tol: float = 0.0,
             mode: str = "analytic", bw_ratio=(2, 1), device_out: bool = True, trace: bool = False,
-            log_capacity: int = 0, stream=None, out=None, out_parent=None, profile: bool = False) -> RunResult:
-        """Runs one application; outputs are torch tensors on cuda (device_out) or host numpy arrays."""
+            log_capacity: int = 0, stream=None, out=None, out_parent=None, profile: bool = False,
+            msg_bf16: bool = False) -> RunResult:
+        """Runs one application; outputs are torch tensors on cuda (device_out) or host numpy arrays.
+        msg_bf16: PageRank / PPR messages travel through the bins as BF16 (gathered in FP32)."""
         torch = _torch()
         lib = _lib.load()
         info = self.info()
@@ -143,6 +145,7 @@ class Graph:
         o.bw_ratio_num, o.bw_ratio_den = bw_ratio
         o.cuda_stream = _stream_handle(stream)
         o.profile_kernels = int(profile)
+        o.msg_bf16 = int(msg_bf16)
         modes = frontier = log = None
         if trace:
             modes = np.zeros(max(max_iters, 1) * k, dtype=np.uint8)

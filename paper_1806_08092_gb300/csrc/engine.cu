@@ -15,6 +15,7 @@
 //                 atomics on vertex data), SC pairs with per-warp destination
 //                 ownership, then reInit/gather/filter user functions and the
 //                 next frontier (Alg. 2 gather + filter; Sec. 4).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -123,6 +124,14 @@ struct Params {
 
 __device__ __forceinline__ float u2f(uint32_t x) { return __uint_as_float(x); }
 __device__ __forceinline__ uint32_t f2u(float x) { return __float_as_uint(x); }
+// BF16 message bins (PR / PPR with msg_bf16): a message value rounds to BF16 (nearest even) on its way into
+// a bin and widens back to FP32 in the gather; NULL is 0xFFFF (a NaN no rounding produces from the
+// non-negative values these applications send)
+constexpr uint32_t kNull16 = 0xFFFFu;
+__device__ __forceinline__ uint32_t to_bf16(uint32_t x) {
+    return x == kNull ? kNull16 : (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(__uint_as_float(x)));
+}
+__device__ __forceinline__ uint32_t from_bf16(uint32_t h) { return h << 16; }  // FP32 bits of a BF16 value
 
 template <int ALGO>
 struct Op {
@@ -503,6 +512,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
 
 // --- PC scatter (Alg. 3) -----------------------------------------------------------------------
 
+template <bool B16>
 __global__ void __launch_bounds__(kScatterThreads) k_scatter_pc(Params p) {
     extern __shared__ __align__(16) uint32_t s_val[];  // the partition's P message values (PC rows)
     __shared__ uint32_t s_task;
@@ -555,9 +565,15 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_pc(Params p) {
                 o0 = make_uint4(kNull, kNull, kNull, kNull);
                 o1 = o0;
             }
-            uint4 *dst = reinterpret_cast<uint4 *>(p.pdata + i);
-            dst[0] = o0;
-            dst[1] = o1;
+            if (B16) {  // 8 BF16 slots in one 16-byte store (slot 2k in the low half of word k)
+                const uint4 h = make_uint4(to_bf16(o0.x) | (to_bf16(o0.y) << 16), to_bf16(o0.z) | (to_bf16(o0.w) << 16),
+                                           to_bf16(o1.x) | (to_bf16(o1.y) << 16), to_bf16(o1.z) | (to_bf16(o1.w) << 16));
+                *reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(p.pdata) + i) = h;
+            } else {
+                uint4 *dst = reinterpret_cast<uint4 *>(p.pdata + i);
+                dst[0] = o0;
+                dst[1] = o1;
+            }
         }
         if (p.t_task) {
             __syncthreads();
@@ -574,7 +590,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_pc(Params p) {
 // (partition, gather task) at a cursor bumped once per distinct sub-bin per warp.  Whole partitions keep
 // their cursors in shared memory and publish the counts at the end; split partitions bump global cursors
 // (zero at rest), and their last unit to finish publishes the counts and resets the cursors.
-template <int ALGO>
+template <int ALGO, bool B16>
 __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
     extern __shared__ uint32_t s_cursor[];  // one insertion point per bin of the row (whole partitions)
     __shared__ uint32_t s_list[1024];       // active local IDs of the current 1024-vertex segment
@@ -664,7 +680,8 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
                 basepos = __shfl_sync(0xffffffffu, basepos, leader);
                 if (live) {
                     slot = p.sub_cap[rb0 + lb] + basepos + rank;
-                    p.scpair[slot] = make_uint2(dloc, val);
+                    if (B16) reinterpret_cast<uint32_t *>(p.scpair)[slot] = dloc | (to_bf16(val) << 16);
+                    else p.scpair[slot] = make_uint2(dloc, val);
                 }
             }
             run0 += total;
@@ -784,7 +801,7 @@ __device__ __forceinline__ uint32_t pc_round_end(const uint32_t *sp, int w, cons
 // read-modify-writes (inner runs of a lane have distinct destinations, and no other lane or warp touches
 // them; positions that end no inner run update the scratch word sink).  Padding entries repeat their
 // range's last destination and read the padding value slot (the identity), so they fold as no-ops.
-template <int ALGO>
+template <int ALGO, bool B16>
 __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt, uint32_t j0, const uint32_t *stage,
                                         uint32_t *acc, uint32_t *sink, bool check_null, uint32_t &fd,
                                         uint32_t &head, uint32_t &run_d, uint32_t &run_v, bool &in_head) {
@@ -811,7 +828,12 @@ __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             d[i] = ee[i] >> 16;
-            x[i] = stage[ee[i] & 0xFFFFu];
+            if (B16) {  // BF16 values staged as 16-bit words
+                const uint32_t h = reinterpret_cast<const uint16_t *>(stage)[ee[i] & 0xFFFFu];
+                x[i] = (nullable && h == kNull16) ? kNull : from_bf16(h);
+            } else {
+                x[i] = stage[ee[i] & 0xFFFFu];
+            }
         }
         bool fl[8];
         uint32_t fk[8], fv[8];
@@ -850,7 +872,7 @@ __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt
 // scan, keyed by destination, joins the lanes' last runs, and a lane's first run takes the scan value of
 // the lane before it when they share the destination.  Every complete run is folded into acc directly:
 // a run cut by the round's end continues in the warp's next round, folded after this part.
-template <int ALGO>
+template <int ALGO, bool B16>
 __device__ __forceinline__ void pc_round(const uint32_t *ent, const uint32_t *wgt, uint32_t n, const uint32_t *stage,
                                          uint32_t *acc, uint32_t *sink, bool check_null, int lane) {
     using O = Op<ALGO>;
@@ -858,7 +880,7 @@ __device__ __forceinline__ void pc_round(const uint32_t *ent, const uint32_t *wg
     const uint32_t j0 = lane * K;
     uint32_t fd = kSent, head = O::identity(), run_d = kSent, run_v = O::identity();
     bool in_head = true;
-    if (j0 < n) pc_lane<ALGO>(ent, wgt, j0, stage, acc, sink, check_null, fd, head, run_d, run_v, in_head);
+    if (j0 < n) pc_lane<ALGO, B16>(ent, wgt, j0, stage, acc, sink, check_null, fd, head, run_d, run_v, in_head);
     const bool uni = in_head;  // all K positions share one destination
     const uint32_t ld = run_d;
     uint32_t S = run_v;
@@ -882,13 +904,17 @@ __device__ __forceinline__ void pc_round(const uint32_t *ent, const uint32_t *wg
 // slot, length, offset in the block; all multiples of 4 values, so 16-byte aligned) are dealt to the
 // warps round-robin, one run per lane; thread 0 arms the buffer's "full" mbarrier with the block's byte
 // count.  first is this lane's descriptor of the first batch, loaded one block ahead.
+template <bool B16>
 __device__ __forceinline__ void pc_issue_values(const Params &p, uint32_t r0, uint32_t r1, uint32_t nval, uint4 first,
                                                 uint32_t *st, uint64_t *full, int lane, int wid) {
-    if (threadIdx.x == 0) mbar_arrive_expect_tx(full, nval * 4u);
+    constexpr uint32_t kB = B16 ? 2u : 4u;  // bytes per staged value
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(full, nval * kB);
     for (uint32_t rb = r0 + wid, it = 0; rb < r1; rb += 32u * kPcWarps, ++it) {
         const uint32_t rr = rb + (uint32_t)lane * kPcWarps;
         const uint4 run = it == 0 ? first : (rr < r1 ? p.pc_runs[rr] : make_uint4(0, 0, 0, 0));
-        if (rr < r1) bulk_g2s(st + run.z, p.pdata + run.x, run.y * 4u, full);
+        if (rr < r1)
+            bulk_g2s(reinterpret_cast<char *>(st) + (size_t)run.z * kB,
+                     reinterpret_cast<const char *>(p.pdata) + (size_t)run.x * kB, run.y * kB, full);
     }
 }
 __device__ __forceinline__ uint4 pc_first_run(const Params &p, uint32_t r0, uint32_t r1, int lane, int wid) {
@@ -911,7 +937,7 @@ __device__ __forceinline__ uint4 pc_first_run(const Params &p, uint32_t r0, uint
 // The accumulator stays in shared memory for the whole task; a column split over several tasks writes
 // one partial vector per task.  Every mbarrier wait is bounded: when one runs out, the run's error flag
 // is raised and all warps leave.
-template <int ALGO>
+template <int ALGO, bool B16>
 __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
     using O = Op<ALGO>;
     constexpr uint32_t C = PcShape<ALGO>::kRound, kSlotWords = PcShape<ALGO>::kSlotWords;
@@ -940,8 +966,13 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
         s_abort = 0;
         // value slot of the padding entries (the copies never write it): the monoid identity, so padding
         // folds as a no-op whether or not NULLs are checked
-        stage[kPcPadIdx] = O::identity();
-        stage[kStageWords + kPcPadIdx] = O::identity();
+        if (B16) {  // BF16 only carries sums: the identity is +0
+            reinterpret_cast<uint16_t *>(stage)[kPcPadIdx] = 0;
+            reinterpret_cast<uint16_t *>(stage + kStageWords)[kPcPadIdx] = 0;
+        } else {
+            stage[kPcPadIdx] = O::identity();
+            stage[kStageWords + kPcPadIdx] = O::identity();
+        }
     }
     const unsigned long long t_start = p.t_gpc ? globaltimer() : 0ull;
     uint32_t gb = 0;         // blocks this CTA has passed through (buffer = gb & 1, use = gb >> 1)
@@ -994,7 +1025,7 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
         __syncthreads();
         const uint32_t na = s_na;
         if (na > 0)
-            pc_issue_values(p, s_run[s_blist[0]], s_run[s_blist[0] + 1], s_nval[s_blist[0]],
+            pc_issue_values<B16>(p, s_run[s_blist[0]], s_run[s_blist[0] + 1], s_nval[s_blist[0]],
                             pc_first_run(p, s_run[s_blist[0]], s_run[s_blist[0] + 1], lane, wid),
                             stage + (gb & 1) * kStageWords, &s_full[gb & 1], lane, wid);
         uint4 next_run = na > 1 ? pc_first_run(p, s_run[s_blist[1]], s_run[s_blist[1] + 1], lane, wid)
@@ -1010,7 +1041,7 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
             const uint32_t g = gb + j, buf = g & 1, use = g >> 1;
             if (j + 1 < na) {  // the next block's values go to the other buffer, freed by the last barrier
                 const uint32_t i1 = s_blist[j + 1];
-                pc_issue_values(p, s_run[i1], s_run[i1 + 1], s_nval[i1], next_run,
+                pc_issue_values<B16>(p, s_run[i1], s_run[i1 + 1], s_nval[i1], next_run,
                                 stage + (buf ^ 1) * kStageWords, &s_full[buf ^ 1], lane, wid);
                 if (j + 2 < na) next_run = pc_first_run(p, s_run[s_blist[j + 2]], s_run[s_blist[j + 2] + 1], lane, wid);
             }
@@ -1038,7 +1069,7 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
                 ph ^= 1u << head_slot;
                 const uint32_t e = pc_round_end<C>(s_sp, wid, cc);
                 const uint32_t *slot = ring + head_slot * kSlotWords;
-                pc_round<ALGO>(slot, slot + C, e - cc.s, stage + buf * kStageWords, acc, &s_sink, p.pc_skip != 0,
+                pc_round<ALGO, B16>(slot, slot + C, e - cc.s, stage + buf * kStageWords, acc, &s_sink, p.pc_skip != 0,
                                lane);
                 __syncwarp();  // the slot is refilled only after every lane has read it
                 --inflight;
@@ -1115,7 +1146,17 @@ __device__ __forceinline__ void sc_fold(uint32_t *slot, uint32_t v) {
 //     column this iteration;
 //  2. SC pairs of the task's fresh SC bins, folded with shared atomics;
 //  3. reInit / gather apply / filter of every destination of the range and the next frontier (Alg. 2).
-template <int ALGO>
+// SC pair j of a bin region: (local destination, message value bits), 8 bytes, or 4 bytes with BF16 values
+template <bool B16>
+__device__ __forceinline__ uint2 sc_pair(const Params &p, uint32_t j) {
+    if (B16) {
+        const uint32_t w = reinterpret_cast<const uint32_t *>(p.scpair)[j];
+        return make_uint2(w & 0xFFFFu, from_bf16(w >> 16));
+    }
+    return p.scpair[j];
+}
+
+template <int ALGO, bool B16>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
     using O = Op<ALGO>;
     __shared__ uint32_t s_acc[kGatherWidth];
@@ -1179,7 +1220,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                     }
                 }
                 for (uint32_t j = lane; j < cnt; j += 32) {
-                    const uint2 pr = p.scpair[sb + j];
+                    const uint2 pr = sc_pair<B16>(p, sb + j);
                     sc_fold<ALGO>(&s_acc[pr.x - gt.d0], pr.y);
                 }
             }
@@ -1189,7 +1230,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                 const uint32_t bn = s_big[k];
                 const uint32_t cnt = p.sccnt[bn], sb = p.sub_cap[bn];
                 for (uint32_t j = tid; j < cnt; j += nthr) {
-                    const uint2 pr = p.scpair[sb + j];
+                    const uint2 pr = sc_pair<B16>(p, sb + j);
                     sc_fold<ALGO>(&s_acc[pr.x - gt.d0], pr.y);
                 }
             }
@@ -1493,7 +1534,7 @@ static gpop_status log_iteration(Graph *g, RunBuffers *rb, const gpop_run_opts *
     return GPOP_OK;
 }
 
-template <int ALGO>
+template <int ALGO, bool B16>
 static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cudaStream_t s, void *out_values,
                             uint32_t *out_parent, int out_is_device, gpop_run_stats *stats) {
     Params p{};  // every field starts at zero / null
@@ -1549,20 +1590,20 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
 
     int grid_pc = 0, grid_sc = 0, grid_ga = 0;
     const size_t sc_smem = sizeof(uint32_t) * std::max<uint32_t>(g->max_row_subs, 1);
-    GPOP_CUDA_TRY(cudaFuncSetAttribute(k_scatter_sc<ALGO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GPOP_CUDA_TRY(cudaFuncSetAttribute(k_scatter_sc<ALGO, B16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sc_smem));
     // k_scatter_pc stages one partition's values (P words) in dynamic shared memory
     const size_t spc_smem = sizeof(uint32_t) * (size_t)g->P;
-    GPOP_CUDA_TRY(cudaFuncSetAttribute(k_scatter_pc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spc_smem));
-    grid_pc = persistent_grid(k_scatter_pc, kScatterThreads, spc_smem, g->num_sms);
-    grid_sc = persistent_grid(k_scatter_sc<ALGO>, kScatterThreads, sc_smem, g->num_sms);
-    grid_ga = persistent_grid(k_gather<ALGO>, kGatherThreads, 0, g->num_sms);
+    GPOP_CUDA_TRY(cudaFuncSetAttribute(k_scatter_pc<B16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spc_smem));
+    grid_pc = persistent_grid(k_scatter_pc<B16>, kScatterThreads, spc_smem, g->num_sms);
+    grid_sc = persistent_grid(k_scatter_sc<ALGO, B16>, kScatterThreads, sc_smem, g->num_sms);
+    grid_ga = persistent_grid(k_gather<ALGO, B16>, kGatherThreads, 0, g->num_sms);
     // k_gather_pc: column accumulator, two block value buffers and as many entry-chunk slots as the
     // opt-in shared memory holds (at most kPcMaxSlots); dynamic shared memory is opted in explicitly
     size_t gpc_smem = 0;
     {
         cudaFuncAttributes fa;
-        GPOP_CUDA_TRY(cudaFuncGetAttributes(&fa, k_gather_pc<ALGO>));
+        GPOP_CUDA_TRY(cudaFuncGetAttributes(&fa, k_gather_pc<ALGO, B16>));
         int optin = 0, dev = 0;
         GPOP_CUDA_TRY(cudaGetDevice(&dev));
         GPOP_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -1573,10 +1614,10 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         if (ns < 2) return fail(GPOP_ERR_INVALID_ARG, "partition size too large for the PC gather's shared memory");
         p.pc_slots = ns;
         gpc_smem = fixed + ns * slot;
-        GPOP_CUDA_TRY(cudaFuncSetAttribute(k_gather_pc<ALGO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        GPOP_CUDA_TRY(cudaFuncSetAttribute(k_gather_pc<ALGO, B16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)gpc_smem));
     }
-    const int grid_gh = persistent_grid(k_gather_pc<ALGO>, kPcThreads, gpc_smem, g->num_sms);
+    const int grid_gh = persistent_grid(k_gather_pc<ALGO, B16>, kPcThreads, gpc_smem, g->num_sms);
 
     // initial frontier (Alg. 4 driver: loadFrontier and initial values)
     p.epoch = ++g->epoch;
@@ -1672,12 +1713,12 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
             cudaMemsetAsync(rb->t_gsc, 0, 8, s);
             Params q1 = p;
             q1.pdata = rb->shadow; q1.dry = 1; q1.counter_slot = 3; q1.t_task = rb->t_pc;
-            k_scatter_pc<<<grid_pc, kScatterThreads, spc_smem, s>>>(q1);
+            k_scatter_pc<B16><<<grid_pc, kScatterThreads, spc_smem, s>>>(q1);
             Params q2 = p;
             q2.dry = 1; q2.counter_slot = 4; q2.list = rb->all_list; q2.list_count = &rb->counters[7];
             q2.t_task = rb->t_sc;
             cudaMemsetAsync(rb->t_sc, 0, 8ull * g->k, s);  // split partitions add their units' CTA times
-            k_scatter_sc<ALGO><<<grid_sc, kScatterThreads, sc_smem, s>>>(q2);
+            k_scatter_sc<ALGO, B16><<<grid_sc, kScatterThreads, sc_smem, s>>>(q2);
         }
         Params ps = p;
         ps.counter_slot = 1;
@@ -1686,14 +1727,14 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         Params pgc = p;
         pgc.t_gpc = p.log_both ? rb->t_gpc : nullptr;
         pgc.pc_skip = c.n_pc < g->k;  // some partition is not PC: skip blocks whose sources all are not
-        if (c.n_pc + c.n_null > 0) timed(1, [&] { k_scatter_pc<<<grid_pc, kScatterThreads, spc_smem, s>>>(p); });
-        if (c.n_sc > 0) timed(2, [&] { k_scatter_sc<ALGO><<<grid_sc, kScatterThreads, sc_smem, s>>>(ps); });
+        if (c.n_pc + c.n_null > 0) timed(1, [&] { k_scatter_pc<B16><<<grid_pc, kScatterThreads, spc_smem, s>>>(p); });
+        if (c.n_sc > 0) timed(2, [&] { k_scatter_sc<ALGO, B16><<<grid_sc, kScatterThreads, sc_smem, s>>>(ps); });
         if (c.n_pc > 0) {
-            timed(4, [&] { k_gather_pc<ALGO><<<grid_gh, kPcThreads, gpc_smem, s>>>(pgc); });
+            timed(4, [&] { k_gather_pc<ALGO, B16><<<grid_gh, kPcThreads, gpc_smem, s>>>(pgc); });
             if (g->nmerge)
                 timed(5, [&] { k_merge_pc<ALGO><<<std::min<uint32_t>(g->nmerge, 16u * g->num_sms), 256, 0, s>>>(p); });
         }
-        timed(3, [&] { k_gather<ALGO><<<grid_ga, kGatherThreads, 0, s>>>(pg); });
+        timed(3, [&] { k_gather<ALGO, B16><<<grid_ga, kGatherThreads, 0, s>>>(pg); });
         ce = cudaGetLastError();
         if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(ce)); break; }
         if (p.log_both) {
@@ -1755,12 +1796,18 @@ extern "C" gpop_status gpop_run(gpop_graph *h, const gpop_run_opts *o, void *out
     if (o->algo == GPOP_SSSP && !g->weighted) return fail(GPOP_ERR_INVALID_ARG, "SSSP needs a weighted graph");
     if (o->mode < GPOP_MODE_ANALYTIC || o->mode > GPOP_MODE_LOG_BOTH) return fail(GPOP_ERR_INVALID_ARG, "unknown mode policy");
     if (o->bw_ratio_num == 0 || o->bw_ratio_den == 0) return fail(GPOP_ERR_INVALID_ARG, "bandwidth ratio must be positive");
-    if (o->msg_bf16) return fail(GPOP_ERR_INVALID_ARG, "BF16 messages are not supported");
+    if (o->msg_bf16 && o->algo != GPOP_PAGERANK && o->algo != GPOP_PPR)
+        return fail(GPOP_ERR_INVALID_ARG, "BF16 messages are for PageRank and PPR (the other algorithms stay exact)");
     if ((o->algo == GPOP_PAGERANK || o->algo == GPOP_PPR) && !(o->damping > 0.0 && o->damping < 1.0))
         return fail(GPOP_ERR_INVALID_ARG, "damping must be in (0, 1)");
     if (o->mode == GPOP_MODE_LEARNED && !selector_device_params())
         return fail(GPOP_ERR_NO_SELECTOR, "learned mode requested but no selector is installed");
     cudaStream_t s = (cudaStream_t)o->cuda_stream;
+    const int fmt = o->msg_bf16 ? 1 : 0;
+    if (fmt != g->pdata_fmt) {  // rows written in the other message format must not be read as this one
+        g->pdata_dirty = true;
+        g->pdata_fmt = fmt;
+    }
     if (g->pdata_dirty) {
         // a failed run may have left PC data rows partially written: restore the all-NULL state
         GPOP_CUDA_TRY(cudaMemsetAsync(g->pdata, 0xFF, 4ull * std::max<uint64_t>(g->npng_pad, 1), s));
@@ -1774,10 +1821,14 @@ extern "C" gpop_status gpop_run(gpop_graph *h, const gpop_run_opts *o, void *out
         g->run = rb;
     }
     switch (o->algo) {
-    case GPOP_PAGERANK: return run_algo<ALG_PR>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
-    case GPOP_BFS: return run_algo<ALG_BFS>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
-    case GPOP_CC: return run_algo<ALG_CC>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
-    case GPOP_SSSP: return run_algo<ALG_SSSP>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
-    default: return run_algo<ALG_PPR>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
+    case GPOP_PAGERANK:
+        return fmt ? run_algo<ALG_PR, true>(g, rb, o, s, out_values, out_parent, out_is_device, stats)
+                   : run_algo<ALG_PR, false>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
+    case GPOP_BFS: return run_algo<ALG_BFS, false>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
+    case GPOP_CC: return run_algo<ALG_CC, false>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
+    case GPOP_SSSP: return run_algo<ALG_SSSP, false>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
+    default:
+        return fmt ? run_algo<ALG_PPR, true>(g, rb, o, s, out_values, out_parent, out_is_device, stats)
+                   : run_algo<ALG_PPR, false>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
     }
 }

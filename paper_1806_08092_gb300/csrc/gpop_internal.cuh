@@ -19,7 +19,7 @@ constexpr uint32_t kNull = 0xFFFFFFFFu;
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 
 constexpr int kPngAlign = 8;           // PNG rows padded to 8 entries (16-byte u16 vectors)
-constexpr uint32_t kBinAlign = 4;      // every bin padded to 4 slots: 16-byte aligned bulk copies of bin runs
+constexpr uint32_t kBinAlign = 8;      // every bin padded to 8 slots: 16-byte aligned bulk copies of bin runs (BF16)
 constexpr uint32_t kGatherWidth = 4096;  // max destinations per gather task (smem accumulator)
 constexpr uint32_t kGatherEntries = 32768;  // target in-entries per gather task
 constexpr uint32_t kScatterChunk = 131072;  // PNG slots per PC scatter task (one staging of the partition's values)
@@ -128,6 +128,7 @@ struct Graph {
     uint8_t *pc_state = nullptr;  // k: row of pdata holds non-NULL values
     uint32_t epoch = 0;           // iteration stamp, never reused within the handle
     bool pdata_dirty = false;
+    int pdata_fmt = 0;  // message format of the data rows: 0 FP32/u32, 1 BF16
 
     uint64_t device_bytes = 0;
     int device = 0, num_sms = 0;

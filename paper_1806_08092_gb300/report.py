@@ -9,7 +9,8 @@ c2        RMAT-22: BFS and SSSP (weights in [1, 255]) from 16 roots, TEPS = trav
           symmetrised graph, E_sym / t.  The partition size is swept over {2K, 4K, 8K, 16K} and every
           setting is reported, the fastest marked.
 c3        PageRank to an L1 residual below 1e-9 on RMAT-24 and on a uniform random directed graph of the
-          same size and average degree: GTEPS = E x iterations / t and per-kernel times.
+          same size and average degree, with FP32 and with BF16 bin messages: GTEPS = E x iterations / t
+          and per-kernel times (the errors against the FP64 oracle come from the GPU tests).
 ablation  RMAT-24 BFS and SSSP and symmetrised RMAT-24 CC with every partition forced to SC, forced to
           PC, and with Eq. (mode): time, iterations and the number of PC / SC partition-steps.
 
@@ -114,13 +115,15 @@ def c3():
     n = 1 << 24
     for name, g in (("rmat24", gg.rmat(24)), ("uniform24", gg.uniform(n, 16 * n))):
         G = Graph.from_csr(g.row_ptr, g.col, None, partition_size=16384)
-        r = _median_run(G, "pagerank", max_iters=300, tol=1e-9)
-        ms, it = r.stats["device_ms"], r.stats["iterations"]
         info = G.info()
-        _emit({"config": "c3", "graph": name, "vertices": g.num_vertices, "edges": g.num_edges,
-               "partition_size": 16384, "r": info["num_png"] / g.num_edges, "algo": "pagerank",
-               "iterations": it, "residual": r.stats["residual"], "converged": r.stats["converged"], "ms": ms,
-               "gteps": g.num_edges * it / (ms / 1e3) / 1e9, "kernels_ms": _kernels(r.stats)})
+        for bf16 in (False, True):
+            r = _median_run(G, "pagerank", max_iters=300, tol=1e-9, msg_bf16=bf16)
+            ms, it = r.stats["device_ms"], r.stats["iterations"]
+            _emit({"config": "c3", "graph": name, "vertices": g.num_vertices, "edges": g.num_edges,
+                   "partition_size": 16384, "r": info["num_png"] / g.num_edges, "algo": "pagerank",
+                   "messages": "bf16" if bf16 else "fp32", "iterations": it, "residual": r.stats["residual"],
+                   "converged": r.stats["converged"], "ms": ms, "gteps": g.num_edges * it / (ms / 1e3) / 1e9,
+                   "kernels_ms": _kernels(r.stats)})
         G.close()
         del g
 

@@ -68,7 +68,12 @@ def test_rmat24_pagerank_10_iterations(rmat24):
     g, G = rmat24
     ref, _, _ = O.pagerank(g, 0.85, max_iters=10)
     x = G.run("pagerank", max_iters=10).values.cpu().numpy().astype(np.float64)
-    assert np.max(np.abs(x - ref) / ref) <= 1e-5
+    e32 = np.max(np.abs(x - ref) / ref)
+    # BF16 messages (FP32 gather): bound derived in test_gpu_parity (2^-9 per message, x d/(1-d))
+    x16 = G.run("pagerank", max_iters=10, msg_bf16=True).values.cpu().numpy().astype(np.float64)
+    e16 = np.max(np.abs(x16 - ref) / ref)
+    print(f"RMAT-24 PageRank 10 iterations, L-inf rel error vs FP64 oracle: FP32 {e32:.2e}, BF16 messages {e16:.2e}")
+    assert e32 <= 1e-5 and e16 <= 2e-2
 
 
 def test_rmat24_pagerank_converged_fixed_point_sampled(rmat24):

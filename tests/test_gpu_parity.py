@@ -160,6 +160,43 @@ def test_large_partitions_multi_task_columns(case):
         assert np.array_equal(r.values.cpu().numpy(), dist), pol
 
 
+# BF16 messages: each message is rounded to 8 mantissa bits (relative error <= 2^-9), and the PageRank
+# fixed point amplifies a uniform relative perturbation of the messages by at most d / (1 - d) = 5.7
+BF16_TOL = 2e-2
+
+
+@pytest.mark.parametrize("pol", POLICIES)
+def test_bf16_messages_pagerank_and_ppr(pol):
+    g = gg.rmat(14)
+    Gd = G(g, 256)
+    ref, _, _ = O.pagerank(g, 0.85, max_iters=30)
+    x32 = Gd.run("pagerank", max_iters=30, mode=pol).values.cpu().numpy()
+    x16 = Gd.run("pagerank", max_iters=30, mode=pol, msg_bf16=True).values.cpu().numpy()
+    e16, e32 = pr_err(x16, ref), pr_err(x32, ref)
+    print(f"PageRank {pol}: L-inf rel error FP32 {e32:.2e}, BF16 messages {e16:.2e}")
+    assert e32 <= PR_TOL and e16 <= BF16_TOL
+    # an FP32 run after a BF16 run on the same graph is unaffected (bit-exact for all-PC PageRank)
+    y32 = Gd.run("pagerank", max_iters=30, mode=pol).values.cpu().numpy()
+    assert pr_err(y32, ref) <= PR_TOL
+    if pol == "force_pc":
+        assert np.array_equal(x32, y32)
+    s = int(gg.roots(g, 1)[0])
+    pref, _, _ = O.ppr(g, s, 0.15, max_iters=30)
+    x = Gd.run("ppr", source=s, damping=0.85, max_iters=30, mode=pol, msg_bf16=True).values.cpu().numpy()
+    sup = pref > 0
+    assert np.max(np.abs(x[sup] - pref[sup]) / pref[sup]) <= BF16_TOL
+    assert np.all(np.abs(x[~sup]) <= 1e-12)
+
+
+def test_bf16_messages_only_for_pagerank_and_ppr():
+    import paper_1806_08092_gb300 as gp
+    g = gg.rmat(8).with_weights()
+    Gd = G(g, 32)
+    for algo in ("bfs", "sssp", "cc"):
+        with pytest.raises(gp.GpopError, match="BF16"):
+            Gd.run(algo, source=1, msg_bf16=True)
+
+
 def test_pagerank_rmat16_p1024_10_iterations():
     # PageRank, 10 iterations, d = 0.85, RMAT scale 16, partitions of 1024 vertices
     g = gg.rmat(16)
