@@ -1180,21 +1180,21 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
         const uint32_t gq = q << p.shift;
         const uint32_t gbase = gq + gt.d0;
         const uint32_t wv = min(width, p.V - gbase);  // destinations that exist
-        if (p.gflag_pc[q] == p.epoch) {
-            // the column's PC result (pc_sum: written by its k_gather_pc task, or merged by k_merge_pc
-            // from the partial vectors of a split column); none when the column has no PC in-edges
-            const bool has_pc = p.col_ntask[q] > 0;
+        // the column's PC result (pc_sum: written by its k_gather_pc task, or merged by k_merge_pc from the
+        // partial vectors of a split column); none when no partition sent PC messages to the column this
+        // iteration or the column has no PC in-edges.  Without SC pairs the filter reads it directly.
+        const bool has_pc = p.gflag_pc[q] == p.epoch && p.col_ntask[q] > 0;
+        const uint32_t nfresh = p.task_sc_cnt[t];
+        const bool direct = nfresh == 0;
+        if (!direct) {
             for (uint32_t i = tid; i < width; i += nthr) s_acc[i] = (has_pc && i < wv) ? p.pc_sum[gbase + i] : O::identity();
-        } else {
-            for (uint32_t i = tid; i < width; i += nthr) s_acc[i] = O::identity();
+            __syncthreads();
         }
-        __syncthreads();
 
         // SC messages: the task's fresh SC bins (binPartList) are dealt to the warps dynamically, a
         // lane per pair, each pair folded into the accumulator with one shared atomic (min for BFS /
         // CC / SSSP, float add for PR / PPR); bins of at least kBigScBin pairs are left to a second,
         // CTA-wide pass so that no single warp carries a hub partition's bin alone
-        const uint32_t nfresh = p.task_sc_cnt[t];
         if (nfresh) {
             const unsigned long long tsc0 = (p.t_gsc && tid == 0) ? globaltimer() : 0ull;
             const uint32_t lbase = p.task_sub_ptr[t];
@@ -1264,6 +1264,17 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                 uint32_t lv[4] = {kInf, kInf, kInf, kInf};
                 if (!full)
                     for (int c = 0; c < 4; ++c) vals[c] = (i0 + c < wv) ? p.val[g0 + c] : 0u;
+                uint32_t msg[4] = {O::identity(), O::identity(), O::identity(), O::identity()};
+                if (!direct) {
+                    for (int c = 0; c < 4; ++c) msg[c] = s_acc[min(i0 + c, width - 1)];
+                } else if (has_pc) {
+                    if (full) {
+                        const uint4 m4 = *reinterpret_cast<const uint4 *>(p.pc_sum + g0);
+                        msg[0] = m4.x; msg[1] = m4.y; msg[2] = m4.z; msg[3] = m4.w;
+                    } else {
+                        for (int c = 0; c < 4; ++c) msg[c] = (i0 + c < wv) ? p.pc_sum[g0 + c] : O::identity();
+                    }
+                }
                 if (ALGO == ALG_BFS) {
                     if (full) {
                         uint4 l4 = *reinterpret_cast<const uint4 *>(p.lvl + g0);
@@ -1281,7 +1292,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                     ns[c] = kNull;
                     if (i0 + c >= wv) continue;
                     const bool was = (was_word >> (g & 31)) & 1u;
-                    const uint32_t m = s_acc[i0 + c];
+                    const uint32_t m = msg[c];
                     const uint32_t deg = rpv[c + 1] - rpv[c];
                     bool act = false;
                     if (ALGO == ALG_PR) {
