@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "gpop_internal.cuh"
@@ -799,8 +800,9 @@ __device__ __forceinline__ uint32_t pc_round_end(const uint32_t *sp, int w, cons
 // message values are loaded first (independent shared loads), runs of equal destination are then found
 // in registers, and the complete inner runs are folded into acc with batched, branch-free
 // read-modify-writes (inner runs of a lane have distinct destinations, and no other lane or warp touches
-// them; positions that end no inner run update the scratch word sink).  Padding entries repeat their
-// range's last destination and read the padding value slot (the identity), so they fold as no-ops.
+// them; positions that end no inner run update the scratch word sink; shared atomics measured slower).
+// Padding entries repeat their range's last destination and read the padding value slot (the identity),
+// so they fold as no-ops.
 template <int ALGO, bool B16>
 __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt, uint32_t j0, const uint32_t *stage,
                                         uint32_t *acc, uint32_t *sink, bool check_null, uint32_t &fd,
@@ -857,6 +859,7 @@ __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt
             run_v = ch ? v : joined;
             run_d = d[i];
         }
+        // branch-free read-modify-writes: positions that end no inner run update a scratch word
         uint32_t *dst[8], old[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) dst[i] = fl[i] ? acc + fk[i] : sink;
@@ -1133,13 +1136,28 @@ __global__ void __launch_bounds__(256) k_merge_pc(Params p) {
     }
 }
 
-// Folds one SC pair's value into a shared accumulator slot: an atomic minimum (BFS parents, CC labels,
-// SSSP distances: the result does not depend on the order) or a float addition (PR / PPR).
+// Task accumulator of the SC pass: a 32-bit word per destination for the min monoids, an FP64 sum per
+// destination for PR / PPR (a hub destination can receive very many pairs, folded in arbitrary order:
+// FP64 keeps their sum within rounding of the exact one, and the filter rounds it to FP32 once).
 template <int ALGO>
-__device__ __forceinline__ void sc_fold(uint32_t *slot, uint32_t v) {
-    if (ALGO == ALG_PR || ALGO == ALG_PPR) atomicAdd(reinterpret_cast<float *>(slot), u2f(v));
-    else atomicMin(slot, v);
-}
+struct ScAcc {
+    static constexpr bool kSum = ALGO == ALG_PR || ALGO == ALG_PPR;
+    using T = typename std::conditional<kSum, double, uint32_t>::type;
+    static __device__ __forceinline__ T from_msg(uint32_t m) {
+        if constexpr (kSum) return (double)u2f(m);
+        else return m;
+    }
+    static __device__ __forceinline__ uint32_t to_msg(T a) {
+        if constexpr (kSum) return f2u((float)a);
+        else return a;
+    }
+    // folds one SC pair's value: atomic minimum (BFS parents, CC labels, SSSP distances: the result does
+    // not depend on the order) or FP64 atomic addition
+    static __device__ __forceinline__ void fold(T *slot, uint32_t v) {
+        if constexpr (kSum) atomicAdd(slot, (double)u2f(v));
+        else atomicMin(slot, v);
+    }
+};
 
 // Gather of one (column q, destination range) task, after k_gather_pc:
 //  1. PC messages: the column's PC result (pc_sum), only when some partition sent PC messages to the
@@ -1159,7 +1177,8 @@ __device__ __forceinline__ uint2 sc_pair(const Params &p, uint32_t j) {
 template <int ALGO, bool B16>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
     using O = Op<ALGO>;
-    __shared__ uint32_t s_acc[kGatherWidth];
+    using A = ScAcc<ALGO>;
+    __shared__ typename A::T s_acc[kGatherWidth];
     __shared__ uint32_t s_task, s_next, s_nbig, s_big[kMaxBigScBins], s_last;
     __shared__ uint32_t s_va[kGatherWarps];
     __shared__ unsigned long long s_ea[kGatherWarps];
@@ -1187,7 +1206,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
         const uint32_t nfresh = p.task_sc_cnt[t];
         const bool direct = nfresh == 0;
         if (!direct) {
-            for (uint32_t i = tid; i < width; i += nthr) s_acc[i] = (has_pc && i < wv) ? p.pc_sum[gbase + i] : O::identity();
+            for (uint32_t i = tid; i < width; i += nthr)
+                s_acc[i] = A::from_msg((has_pc && i < wv) ? p.pc_sum[gbase + i] : O::identity());
             __syncthreads();
         }
 
@@ -1221,7 +1241,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                 }
                 for (uint32_t j = lane; j < cnt; j += 32) {
                     const uint2 pr = sc_pair<B16>(p, sb + j);
-                    sc_fold<ALGO>(&s_acc[pr.x - gt.d0], pr.y);
+                    A::fold(&s_acc[pr.x - gt.d0], pr.y);
                 }
             }
             __syncthreads();
@@ -1231,7 +1251,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                 const uint32_t cnt = p.sccnt[bn], sb = p.sub_cap[bn];
                 for (uint32_t j = tid; j < cnt; j += nthr) {
                     const uint2 pr = sc_pair<B16>(p, sb + j);
-                    sc_fold<ALGO>(&s_acc[pr.x - gt.d0], pr.y);
+                    A::fold(&s_acc[pr.x - gt.d0], pr.y);
                 }
             }
             __syncthreads();
@@ -1266,7 +1286,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                     for (int c = 0; c < 4; ++c) vals[c] = (i0 + c < wv) ? p.val[g0 + c] : 0u;
                 uint32_t msg[4] = {O::identity(), O::identity(), O::identity(), O::identity()};
                 if (!direct) {
-                    for (int c = 0; c < 4; ++c) msg[c] = s_acc[min(i0 + c, width - 1)];
+                    for (int c = 0; c < 4; ++c) msg[c] = A::to_msg(s_acc[min(i0 + c, width - 1)]);
                 } else if (has_pc) {
                     if (full) {
                         const uint4 m4 = *reinterpret_cast<const uint4 *>(p.pc_sum + g0);
