@@ -182,6 +182,33 @@ gpop_status gpop_run(gpop_graph *g, const gpop_run_opts *opts, void *out_values,
                      int out_is_device, gpop_run_stats *stats);
 
 /*
+ * Multi-source BFS: the levels of Alg. 5 from every source in one call, up to
+ * 32 sources per pass through the engine.  A pass carries, per vertex, the set
+ * of its sources that reached the vertex (bit j = sources[b + j]); a vertex's
+ * message in SC and PC bins is the complement of the sources that reached it
+ * in the previous iteration, combined with bitwise AND, so the NULL of an
+ * inactive source (all ones) is the identity and every pass keeps the single
+ * BFS's exact results.  Partition modes follow opts.mode as in gpop_run, from
+ * the union frontier of the pass.
+ *   sources      HOST array of num_sources vertex IDs (< V; repeats allowed)
+ *   out_levels   num_sources x V uint32, row j = levels from sources[j]
+ *                (0xFFFFFFFF = unreached), caller-owned; device memory if
+ *                out_is_device, else host memory (staged through a 32 x V
+ *                device buffer owned by the graph)
+ *   opts         mode, bw ratio, max_iters (per pass), profile_kernels and
+ *                cuda_stream are used; algo, source and damping are ignored;
+ *                msg_bf16 must be 0; trace buffers hold the last pass
+ *   stats        optional: sums over the passes (iterations, device_ms,
+ *                kernel times, ...), converged = every pass converged
+ * No parents are produced.  Errors: GPOP_ERR_INVALID_ARG (NULL pointers with
+ * num_sources > 0, a source >= V, msg_bf16), GPOP_ERR_NO_SELECTOR,
+ * GPOP_ERR_OOM, GPOP_ERR_CUDA, GPOP_ERR_TIMEOUT.  num_sources = 0 returns
+ * GPOP_OK without work.
+ */
+gpop_status gpop_run_msbfs(gpop_graph *g, const gpop_run_opts *opts, const uint32_t *sources, uint32_t num_sources,
+                           uint32_t *out_levels, int out_is_device, gpop_run_stats *stats);
+
+/*
  * Learned SC/PC selector (replaces Eq. (mode) per partition per iteration when
  * opts.mode = GPOP_MODE_LEARNED).  An MLP 8 -> 32 -> 32 -> 1 with ReLU,
  * FP32, predicting y = log(t_PC / t_SC); PC is chosen iff y <= 0.  Features

@@ -5,7 +5,7 @@ Only the test suite, ``__graft_entry__.smoke()`` and the bench's CPU-baseline /
 reference leg may import this package; the CUDA library never calls it and
 shares no code with it.
 
-Tier 1 (plain definitions): ``pagerank``, ``ppr``, ``bfs``, ``cc``, ``sssp``.
+Tier 1 (plain definitions): ``pagerank``, ``ppr``, ``bfs``, ``msbfs``, ``cc``, ``sssp``.
 Tier 2 (the serial GPOP engine of Alg. 2 / Alg. 3 / Eq. (mode)): ``gpop``.
 Model helpers (Sec. 3.2): ``mode_decide``, ``mode_bytes``, ``partition_stats``.
 
@@ -115,6 +115,18 @@ def bfs(g, root: int):
     parent = np.zeros(n, dtype=np.uint32)
     assert _load().orc_bfs(n, _ptr(rp), _ptr(col), root, _ptr(level), _ptr(parent)) == 0
     return level, parent
+
+
+def msbfs(g, sources):
+    """BFS levels from each of several sources (the multi-source form of Alg. 5): row j is the hop
+    distance from sources[j] over out-edges, 0xFFFFFFFF for unreached.  By definition every row is the
+    single-source BFS of its source, so this is that BFS run once per source."""
+    n = g.num_vertices
+    src = [int(s) for s in sources]
+    out = np.zeros((len(src), n), dtype=np.uint32)
+    for j, s in enumerate(src):
+        out[j] = bfs(g, s)[0]
+    return out
 
 
 def cc(g):

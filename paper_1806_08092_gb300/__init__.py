@@ -18,6 +18,7 @@ import numpy as np
 from . import _lib
 from ._build import build as _build_lib
 from ._lib import ALGOS, MODES, GpopError, LOG_RECORD_FLOATS, SELECTOR_PARAMS, SELECTOR_WEIGHTS  # noqa: F401
+MSBFS_WIDTH = 32  # sources per gpop_run_msbfs engine pass (bits of a 32-bit message)
 
 __all__ = ["build", "Graph", "RunResult", "GpopError", "selector_set", "selector_get", "selector_train",
            "selector_grad"]
@@ -181,6 +182,48 @@ class Graph:
         if log is not None:
             log = log[: stats["log_records"] * LOG_RECORD_FLOATS].reshape(-1, LOG_RECORD_FLOATS)
         return RunResult(out, out_parent if algo == "bfs" else None, stats, modes, frontier, log)
+
+    def run_msbfs(self, sources, max_iters: int = 1000, mode: str = "analytic", bw_ratio=(2, 1),
+                  device_out: bool = True, trace: bool = False, stream=None, out=None,
+                  profile: bool = False) -> RunResult:
+        """BFS levels from every source (gpop_run_msbfs: up to 32 sources per engine pass); values is a
+        (len(sources), V) uint32 array, row j the levels from sources[j] (0xFFFFFFFF = unreached).  With
+        trace (at most MSBFS_WIDTH sources, one pass), the per-iteration modes and union frontier sizes."""
+        torch = _torch()
+        lib = _lib.load()
+        info = self.info()
+        n, k = info["num_vertices"], info["num_partitions"]
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64).astype(np.uint32))
+        ns = src.shape[0]
+        o = _lib.RunOpts()
+        lib.gpop_run_opts_default(ctypes.byref(o))
+        o.algo = ALGOS["bfs"]
+        o.max_iters = max_iters
+        o.mode = MODES[mode]
+        o.bw_ratio_num, o.bw_ratio_den = bw_ratio
+        o.cuda_stream = _stream_handle(stream)
+        o.profile_kernels = int(profile)
+        modes = frontier = None
+        if trace:
+            if ns > MSBFS_WIDTH:
+                raise ValueError(f"trace covers one pass: at most {MSBFS_WIDTH} sources")
+            modes = np.zeros(max(max_iters, 1) * k, dtype=np.uint8)
+            frontier = np.zeros(max(max_iters, 1) * 2, dtype=np.uint64)
+            o.trace_modes = ctypes.c_void_p(modes.ctypes.data)
+            o.trace_frontier = ctypes.c_void_p(frontier.ctypes.data)
+        if out is None:
+            out = (torch.empty((ns, n), dtype=torch.uint32, device="cuda") if device_out
+                   else np.empty((ns, n), dtype=np.uint32))
+        pv = out.data_ptr() if device_out else out.ctypes.data
+        st = _lib.RunStats()
+        _lib.check(lib.gpop_run_msbfs(self._h, ctypes.byref(o), ctypes.c_void_p(src.ctypes.data if ns else None),
+                                      ns, ctypes.c_void_p(pv if ns else None), int(device_out), ctypes.byref(st)))
+        stats = st.as_dict()
+        if trace:
+            it = stats["iterations"]
+            modes = modes[: it * k].reshape(it, k)
+            frontier = frontier[: it * 2].reshape(it, 2)
+        return RunResult(out, None, stats, modes, frontier, None)
 
 
 def selector_set(params) -> None:

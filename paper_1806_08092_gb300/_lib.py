@@ -68,6 +68,8 @@ SIGNATURES = {
     "gpop_graph_destroy": (None, [_vp]),
     "gpop_run_opts_default": (None, [ctypes.POINTER(RunOpts)]),
     "gpop_run": (ctypes.c_int, [_vp, ctypes.POINTER(RunOpts), _vp, _vp, ctypes.c_int, ctypes.POINTER(RunStats)]),
+    "gpop_run_msbfs": (ctypes.c_int, [_vp, ctypes.POINTER(RunOpts), _vp, ctypes.c_uint32, _vp, ctypes.c_int,
+                                      ctypes.POINTER(RunStats)]),
     "gpop_selector_set": (ctypes.c_int, [_vp]),
     "gpop_selector_get": (ctypes.c_int, [_vp]),
     "gpop_selector_train": (ctypes.c_int, [_vp, _vp, _u32, _u32, _f32, _u64, _vp, _vp, _vp]),

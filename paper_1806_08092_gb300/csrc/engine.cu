@@ -29,7 +29,12 @@
 
 namespace gpop {
 
-enum Algo : int { ALG_PR = GPOP_PAGERANK, ALG_BFS = GPOP_BFS, ALG_CC = GPOP_CC, ALG_SSSP = GPOP_SSSP, ALG_PPR = GPOP_PPR };
+// ALG_MSBFS: BFS from up to 32 sources at once (gpop_run_msbfs); a vertex's state is the set of sources
+// that reached it and its message the complement of the sources it reached in the last iteration
+enum Algo : int {
+    ALG_PR = GPOP_PAGERANK, ALG_BFS = GPOP_BFS, ALG_CC = GPOP_CC, ALG_SSSP = GPOP_SSSP, ALG_PPR = GPOP_PPR,
+    ALG_MSBFS = 5
+};
 
 constexpr int kGatherThreads = 256;
 constexpr int kGatherWarps = kGatherThreads / 32;
@@ -115,6 +120,9 @@ struct Params {
     uint32_t log_both;
     // per launch
     uint32_t epoch, iter, source, max_iters;
+    const uint32_t *msrc;   // multi-source BFS: the pass's sources (nsrc <= 32; bit j of a set = msrc[j])
+    uint32_t nsrc;
+    uint32_t *lvl_ms;       // multi-source BFS: levels, row j (V words) for source msrc[j]
     float c0, c1;           // PR: (1-d)/V, d.  PPR: alpha, 1-alpha
     double tol;
     int algo, policy;
@@ -136,12 +144,16 @@ __device__ __forceinline__ uint32_t from_bf16(uint32_t h) { return h << 16; }  /
 
 template <int ALGO>
 struct Op {
-    // monoid used to combine the messages a vertex receives in one gather
+    // monoid used to combine the messages a vertex receives in one gather: FP32 sum (PR / PPR), minimum
+    // (BFS parent, CC label, SSSP distance) or bitwise AND (multi-source BFS: messages are complemented
+    // source sets, so the AND is the complement of their union).  Except for the sums the identity is
+    // 0xFFFFFFFF, the NULL of an inactive source, which therefore folds as a no-op.
     static __device__ __forceinline__ uint32_t identity() {
         return (ALGO == ALG_PR || ALGO == ALG_PPR) ? 0u : kInf;
     }
     static __device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b) {
         if (ALGO == ALG_PR || ALGO == ALG_PPR) return f2u(u2f(a) + u2f(b));
+        if (ALGO == ALG_MSBFS) return a & b;
         return a < b ? a : b;
     }
     // applyWeight of Alg. 7 (SSSP adds the edge weight, saturating below kInf)
@@ -342,6 +354,10 @@ __global__ void k_init(Params p) {
                 act = (g == p.source);
                 v = act ? 0u : kInf;
                 sv = act ? 0u : kNull;
+            } else if (ALGO == ALG_MSBFS) {  // no source has reached anyone yet (k_msbfs_sources plants them)
+                act = false;
+                v = 0u;
+                sv = kNull;
             } else {  // CC: own ID as label, everyone active
                 act = true;
                 v = g;
@@ -353,6 +369,19 @@ __global__ void k_init(Params p) {
         }
         p.bits[wi] = word;
     }
+}
+
+// Multi-source BFS: source j of the pass reaches its own vertex at level 0 (one thread: at most 32
+// sources, and several may share a vertex).  Runs after k_init, before k_task_stats.
+__global__ void k_msbfs_sources(Params p) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (uint32_t j = 0; j < p.nsrc; ++j) {
+        const uint32_t g = p.msrc[j];
+        p.val[g] |= 1u << j;
+        p.lvl_ms[(uint64_t)j * p.V + g] = 0u;
+        p.bits[g >> 5] |= 1u << (g & 31);
+    }
+    for (uint32_t j = 0; j < p.nsrc; ++j) p.sval[p.msrc[j]] = ~p.val[p.msrc[j]];  // message: complemented set
 }
 
 // frontier statistics of every gather task from the bitmap (used once, for the initial frontier)
@@ -1151,10 +1180,11 @@ struct ScAcc {
         if constexpr (kSum) return f2u((float)a);
         else return a;
     }
-    // folds one SC pair's value: atomic minimum (BFS parents, CC labels, SSSP distances: the result does
-    // not depend on the order) or FP64 atomic addition
+    // folds one SC pair's value: atomic minimum (BFS parents, CC labels, SSSP distances) or AND
+    // (multi-source BFS), whose results do not depend on the order, or FP64 atomic addition
     static __device__ __forceinline__ void fold(T *slot, uint32_t v) {
         if constexpr (kSum) atomicAdd(slot, (double)u2f(v));
+        else if constexpr (ALGO == ALG_MSBFS) atomicAnd(slot, v);
         else atomicMin(slot, v);
     }
 };
@@ -1271,6 +1301,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
             const uint32_t g0 = gbase + i0;
             const bool any = i0 < wv;
             uint32_t nib = 0;
+            uint32_t fresh[4] = {0u, 0u, 0u, 0u};  // multi-source BFS: sources reaching each vertex first now
             uint32_t was_word = any ? p.bits[g0 >> 5] : 0u;
             if (any) {
                 const bool full = i0 + 4 <= wv;
@@ -1334,6 +1365,16 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                         nv[c] = f2u(xn);
                         res += fabs((double)xn - (double)xo);
                         if (act) ns[c] = f2u(deg ? xn / (float)deg : 0.f);
+                    } else if (ALGO == ALG_MSBFS) {
+                        // Alg. 5 for every source of the pass at once: the sources that reach the vertex
+                        // (complement of the AND of complemented sets) minus those that already had it
+                        const uint32_t nw = ~m & ~vals[c];
+                        if (nw) {
+                            fresh[c] = nw;
+                            nv[c] = vals[c] | nw;
+                            act = true;
+                            ns[c] = ~nw;
+                        }
                     } else if (ALGO == ALG_BFS) {
                         // Alg. 5: first discovery sets the parent (smallest candidate) and level
                         if (m != kInf && lv[c] == kInf) {
@@ -1370,6 +1411,22 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                             p.sval[g0 + c] = ns[c];
                             if (ALGO == ALG_BFS) p.lvl[g0 + c] = lv[c];
                         }
+                }
+            }
+            if (ALGO == ALG_MSBFS) {
+                // level rows: the warp walks the sources any of its lanes reached, so that the stores to
+                // one row come from consecutive lanes
+                const uint32_t mine = fresh[0] | fresh[1] | fresh[2] | fresh[3];
+                uint32_t wall = __reduce_or_sync(0xffffffffu, mine);
+                while (wall) {
+                    const int j = __ffs(wall) - 1;
+                    wall &= wall - 1;
+                    if ((mine >> j) & 1u) {
+                        uint32_t *row = p.lvl_ms + (uint64_t)j * p.V + g0;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if ((fresh[c] >> j) & 1u) row[c] = p.iter;
+                    }
                 }
             }
             // 8 consecutive threads own one frontier word
@@ -1432,13 +1489,15 @@ struct RunBuffers {
     unsigned long long *part_ea = nullptr, *t_pc = nullptr, *t_sc = nullptr, *t_gpc = nullptr, *t_gsc = nullptr;
     double rate_pc = 0.0, rate_sc = 0.0;  // LOG_BOTH: gather ns per modelled byte, last measured per mode
     float *feat = nullptr;
+    // multi-source BFS (allocated on first use): the pass's sources, staged level rows for host output
+    uint32_t *msrc = nullptr, *lvl_ms = nullptr;
 };
 
 static void release_runbufs(RunBuffers *rb) {
     void *ptrs[] = {rb->val, rb->lvl, rb->sval, rb->bits, rb->t_va, rb->t_stamp, rb->t_ea, rb->t_res,
                     rb->mode, rb->action, rb->sel_mode, rb->col_done, rb->gflag, rb->gflag_pc, rb->sc_list, rb->sc_gcur, rb->sc_udone, rb->pc_prefix, rb->counters,
                     rb->ctrl, rb->task_sc_cnt, rb->task_sc_list, rb->pc_sum, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_gpc, rb->t_gsc,
-                    rb->feat};
+                    rb->feat, rb->msrc, rb->lvl_ms};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (rb->h_ctrl) cudaFreeHost(rb->h_ctrl);
@@ -1565,9 +1624,17 @@ static gpop_status log_iteration(Graph *g, RunBuffers *rb, const gpop_run_opts *
     return GPOP_OK;
 }
 
+// One pass of a multi-source BFS: device array of n <= 32 sources and the device level rows (n x V words)
+struct MsPass {
+    const uint32_t *src;
+    uint32_t n;
+    uint32_t *lvl;
+};
+
 template <int ALGO, bool B16>
 static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cudaStream_t s, void *out_values,
-                            uint32_t *out_parent, int out_is_device, gpop_run_stats *stats) {
+                            uint32_t *out_parent, int out_is_device, gpop_run_stats *stats,
+                            const MsPass *mpass = nullptr) {
     Params p{};  // every field starts at zero / null
     memset(&p, 0, sizeof p);
     p.V = g->V; p.P = g->P; p.shift = g->shift; p.k = g->k;
@@ -1609,6 +1676,9 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     }
     p.all_list = rb->all_list; p.feat = rb->feat; p.part_va = rb->part_va; p.part_ea = rb->part_ea;
     p.source = o->source; p.max_iters = o->max_iters; p.tol = o->tol_l1;
+    if (ALGO == ALG_MSBFS) {
+        p.msrc = mpass->src; p.nsrc = mpass->n; p.lvl_ms = mpass->lvl;
+    }
     p.algo = ALGO; p.policy = o->mode == GPOP_MODE_LOG_BOTH ? GPOP_MODE_ANALYTIC : o->mode;
     p.bw_num = o->bw_ratio_num; p.bw_den = o->bw_ratio_den;
     if (ALGO == ALG_PR) {
@@ -1659,7 +1729,9 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     const bool learned = p.policy == GPOP_MODE_LEARNED && p.selector;
     p.col_done = learned ? rb->col_done : nullptr;
     if (learned) GPOP_CUDA_TRY(cudaMemsetAsync(rb->col_done, 0, 4ull * g->k, s));
+    if (ALGO == ALG_MSBFS) GPOP_CUDA_TRY(cudaMemsetAsync(p.lvl_ms, 0xFF, 4ull * p.nsrc * g->V, s));
     k_init<ALGO><<<std::max(1, std::min((int)((g->V / 32 + 255) / 256), 4096)), 256, 0, s>>>(p);
+    if (ALGO == ALG_MSBFS) k_msbfs_sources<<<1, 32, 0, s>>>(p);
     k_task_stats<<<std::max(1, std::min((int)g->ngt, 8 * g->num_sms)), kGatherThreads, 0, s>>>(p);
     GPOP_CUDA_TRY(cudaGetLastError());
 
@@ -1793,7 +1865,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     // outputs
     cudaMemcpyKind kind = out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const uint32_t *res_src = (ALGO == ALG_BFS) ? rb->lvl : rb->val;
-    if (out_values) GPOP_CUDA_TRY(cudaMemcpyAsync(out_values, res_src, 4ull * g->V, kind, s));
+    if (ALGO != ALG_MSBFS && out_values) GPOP_CUDA_TRY(cudaMemcpyAsync(out_values, res_src, 4ull * g->V, kind, s));
     if (ALGO == ALG_BFS && out_parent) GPOP_CUDA_TRY(cudaMemcpyAsync(out_parent, rb->val, 4ull * g->V, kind, s));
     GPOP_CUDA_TRY(cudaStreamSynchronize(s));
     if (stats) *stats = st;
@@ -1816,25 +1888,8 @@ extern "C" void gpop_run_opts_default(gpop_run_opts *o) {
     o->bw_ratio_den = 1;
 }
 
-extern "C" gpop_status gpop_run(gpop_graph *h, const gpop_run_opts *o, void *out_values, uint32_t *out_parent,
-                                int out_is_device, gpop_run_stats *stats) {
-    set_error("");
-    if (!h || !o) return fail(GPOP_ERR_INVALID_ARG, "NULL graph or options");
-    Graph *g = &h->g;
-    if (o->algo < GPOP_PAGERANK || o->algo > GPOP_PPR) return fail(GPOP_ERR_INVALID_ARG, "unknown algorithm");
-    if ((o->algo == GPOP_BFS || o->algo == GPOP_SSSP || o->algo == GPOP_PPR) && o->source >= g->V)
-        return fail(GPOP_ERR_INVALID_ARG, "source out of range");
-    if (o->algo == GPOP_SSSP && !g->weighted) return fail(GPOP_ERR_INVALID_ARG, "SSSP needs a weighted graph");
-    if (o->mode < GPOP_MODE_ANALYTIC || o->mode > GPOP_MODE_LOG_BOTH) return fail(GPOP_ERR_INVALID_ARG, "unknown mode policy");
-    if (o->bw_ratio_num == 0 || o->bw_ratio_den == 0) return fail(GPOP_ERR_INVALID_ARG, "bandwidth ratio must be positive");
-    if (o->msg_bf16 && o->algo != GPOP_PAGERANK && o->algo != GPOP_PPR)
-        return fail(GPOP_ERR_INVALID_ARG, "BF16 messages are for PageRank and PPR (the other algorithms stay exact)");
-    if ((o->algo == GPOP_PAGERANK || o->algo == GPOP_PPR) && !(o->damping > 0.0 && o->damping < 1.0))
-        return fail(GPOP_ERR_INVALID_ARG, "damping must be in (0, 1)");
-    if (o->mode == GPOP_MODE_LEARNED && !selector_device_params())
-        return fail(GPOP_ERR_NO_SELECTOR, "learned mode requested but no selector is installed");
-    cudaStream_t s = (cudaStream_t)o->cuda_stream;
-    const int fmt = o->msg_bf16 ? 1 : 0;
+// PC data rows in the run's message format and all-NULL where not written, and the run buffers
+static gpop_status prepare_run(Graph *g, int fmt, cudaStream_t s, RunBuffers **out) {
     if (fmt != g->pdata_fmt) {  // rows written in the other message format must not be read as this one
         g->pdata_dirty = true;
         g->pdata_fmt = fmt;
@@ -1851,6 +1906,38 @@ extern "C" gpop_status gpop_run(gpop_graph *h, const gpop_run_opts *o, void *out
         if (st != GPOP_OK) return st;
         g->run = rb;
     }
+    *out = rb;
+    return GPOP_OK;
+}
+
+static gpop_status check_common_opts(const gpop_run_opts *o) {
+    if (o->mode < GPOP_MODE_ANALYTIC || o->mode > GPOP_MODE_LOG_BOTH) return fail(GPOP_ERR_INVALID_ARG, "unknown mode policy");
+    if (o->bw_ratio_num == 0 || o->bw_ratio_den == 0) return fail(GPOP_ERR_INVALID_ARG, "bandwidth ratio must be positive");
+    if (o->mode == GPOP_MODE_LEARNED && !selector_device_params())
+        return fail(GPOP_ERR_NO_SELECTOR, "learned mode requested but no selector is installed");
+    return GPOP_OK;
+}
+
+extern "C" gpop_status gpop_run(gpop_graph *h, const gpop_run_opts *o, void *out_values, uint32_t *out_parent,
+                                int out_is_device, gpop_run_stats *stats) {
+    set_error("");
+    if (!h || !o) return fail(GPOP_ERR_INVALID_ARG, "NULL graph or options");
+    Graph *g = &h->g;
+    if (o->algo < GPOP_PAGERANK || o->algo > GPOP_PPR) return fail(GPOP_ERR_INVALID_ARG, "unknown algorithm");
+    if ((o->algo == GPOP_BFS || o->algo == GPOP_SSSP || o->algo == GPOP_PPR) && o->source >= g->V)
+        return fail(GPOP_ERR_INVALID_ARG, "source out of range");
+    if (o->algo == GPOP_SSSP && !g->weighted) return fail(GPOP_ERR_INVALID_ARG, "SSSP needs a weighted graph");
+    gpop_status cs = check_common_opts(o);
+    if (cs != GPOP_OK) return cs;
+    if (o->msg_bf16 && o->algo != GPOP_PAGERANK && o->algo != GPOP_PPR)
+        return fail(GPOP_ERR_INVALID_ARG, "BF16 messages are for PageRank and PPR (the other algorithms stay exact)");
+    if ((o->algo == GPOP_PAGERANK || o->algo == GPOP_PPR) && !(o->damping > 0.0 && o->damping < 1.0))
+        return fail(GPOP_ERR_INVALID_ARG, "damping must be in (0, 1)");
+    cudaStream_t s = (cudaStream_t)o->cuda_stream;
+    const int fmt = o->msg_bf16 ? 1 : 0;
+    RunBuffers *rb = nullptr;
+    gpop_status ps = prepare_run(g, fmt, s, &rb);
+    if (ps != GPOP_OK) return ps;
     switch (o->algo) {
     case GPOP_PAGERANK:
         return fmt ? run_algo<ALG_PR, true>(g, rb, o, s, out_values, out_parent, out_is_device, stats)
@@ -1862,4 +1949,65 @@ extern "C" gpop_status gpop_run(gpop_graph *h, const gpop_run_opts *o, void *out
         return fmt ? run_algo<ALG_PPR, true>(g, rb, o, s, out_values, out_parent, out_is_device, stats)
                    : run_algo<ALG_PPR, false>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
     }
+}
+
+extern "C" gpop_status gpop_run_msbfs(gpop_graph *h, const gpop_run_opts *o, const uint32_t *sources,
+                                      uint32_t num_sources, uint32_t *out_levels, int out_is_device,
+                                      gpop_run_stats *stats) {
+    set_error("");
+    if (!h || !o) return fail(GPOP_ERR_INVALID_ARG, "NULL graph or options");
+    if (num_sources && (!sources || !out_levels)) return fail(GPOP_ERR_INVALID_ARG, "NULL sources or level buffer");
+    Graph *g = &h->g;
+    for (uint32_t j = 0; j < num_sources; ++j)
+        if (sources[j] >= g->V) return fail(GPOP_ERR_INVALID_ARG, "source out of range");
+    if (o->msg_bf16) return fail(GPOP_ERR_INVALID_ARG, "BF16 messages are for PageRank and PPR (BFS stays exact)");
+    gpop_status cs = check_common_opts(o);
+    if (cs != GPOP_OK) return cs;
+    gpop_run_stats total;
+    memset(&total, 0, sizeof total);
+    total.converged = 1;
+    if (num_sources == 0) {
+        if (stats) *stats = total;
+        return GPOP_OK;
+    }
+    cudaStream_t s = (cudaStream_t)o->cuda_stream;
+    RunBuffers *rb = nullptr;
+    gpop_status ps = prepare_run(g, 0, s, &rb);
+    if (ps != GPOP_OK) return ps;
+    if (!rb->msrc) {
+        cudaError_t e = dalloc(g, &rb->msrc, kMsBfsWidth);
+        if (e != cudaSuccess) return fail(GPOP_ERR_OOM, std::string("source list: ") + cudaGetErrorString(e));
+    }
+    if (!out_is_device && !rb->lvl_ms) {  // host output: one pass's level rows are staged on the device
+        cudaError_t e = dalloc(g, &rb->lvl_ms, (uint64_t)kMsBfsWidth * g->V);
+        if (e != cudaSuccess) return fail(GPOP_ERR_OOM, std::string("level rows: ") + cudaGetErrorString(e));
+    }
+    for (uint32_t b = 0; b < num_sources; b += kMsBfsWidth) {
+        const uint32_t n = std::min<uint32_t>(kMsBfsWidth, num_sources - b);
+        uint32_t *rows = out_levels + (uint64_t)b * g->V;
+        GPOP_CUDA_TRY(cudaMemcpyAsync(rb->msrc, sources + b, 4ull * n, cudaMemcpyHostToDevice, s));
+        MsPass mp{rb->msrc, n, out_is_device ? rows : rb->lvl_ms};
+        gpop_run_stats st;
+        gpop_status r = run_algo<ALG_MSBFS, false>(g, rb, o, s, nullptr, nullptr, 1, &st, &mp);
+        if (r != GPOP_OK) return r;
+        if (!out_is_device) {
+            GPOP_CUDA_TRY(cudaMemcpyAsync(rows, rb->lvl_ms, 4ull * n * g->V, cudaMemcpyDeviceToHost, s));
+            GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        total.iterations += st.iterations;
+        total.converged &= st.converged;
+        total.edges_scattered += st.edges_scattered;
+        total.vertices_scattered += st.vertices_scattered;
+        total.pc_partition_steps += st.pc_partition_steps;
+        total.sc_partition_steps += st.sc_partition_steps;
+        total.model_bytes += st.model_bytes;
+        total.device_ms += st.device_ms;
+        total.log_records += st.log_records;
+        for (int i = 0; i < 6; ++i) {
+            total.kernel_ms[i] += st.kernel_ms[i];
+            total.kernel_launches[i] += st.kernel_launches[i];
+        }
+    }
+    if (stats) *stats = total;
+    return GPOP_OK;
 }

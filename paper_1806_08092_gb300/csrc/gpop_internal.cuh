@@ -17,6 +17,7 @@ namespace gpop {
 // ID, distance and label.
 constexpr uint32_t kNull = 0xFFFFFFFFu;
 constexpr uint32_t kInf = 0xFFFFFFFFu;
+constexpr uint32_t kMsBfsWidth = 32;  // sources per multi-source BFS pass (bits of a 32-bit message)
 
 constexpr int kPngAlign = 8;           // PNG rows padded to 8 entries (16-byte u16 vectors)
 constexpr uint32_t kBinAlign = 8;      // every bin padded to 8 slots: 16-byte aligned bulk copies of bin runs (BF16)

@@ -1,6 +1,6 @@
 """Measurements of the synthetic configurations on one GPU, one JSON line per result.
 
-    python -m paper_1806_08092_gb300.report [--configs c1,c2,c3,ablation]
+    python -m paper_1806_08092_gb300.report [--configs c1,c2,c3,c4,ablation]
 
 c1        PageRank, 10 iterations, d = 0.85, RMAT-16 (P = 1024): time and GTEPS = 10 E / t.  The graph
           and its bins fit in L2, so no HBM fraction is meaningful for it.
@@ -11,6 +11,8 @@ c2        RMAT-22: BFS and SSSP (weights in [1, 255]) from 16 roots, TEPS = trav
 c3        PageRank to an L1 residual below 1e-9 on RMAT-24 and on a uniform random directed graph of the
           same size and average degree, with FP32 and with BF16 bin messages: GTEPS = E x iterations / t
           and per-kernel times (the errors against the FP64 oracle come from the GPU tests).
+c4        RMAT-22 BFS from 64 sources: gpop_run_msbfs (two 32-source passes) against 64 single-source
+          gpop_run calls, TEPS = sum over sources of traversed edges / t, and the batching speedup.
 ablation  RMAT-24 BFS and SSSP and symmetrised RMAT-24 CC with every partition forced to SC, forced to
           PC, and with Eq. (mode): time, iterations and the number of PC / SC partition-steps.
 
@@ -128,6 +130,31 @@ def c3():
         del g
 
 
+def c4(nsrc=64):
+    gg = _gen()
+    g = gg.rmat(22)
+    src = [int(x) for x in gg.roots(g, nsrc)]
+    G = Graph.from_csr(g.row_ptr, g.col, None, partition_size=16384)
+    deg = torch.from_numpy(np.diff(g.row_ptr).astype(np.int64)).cuda()
+    G.run_msbfs(src)  # warm-up
+    runs = sorted((G.run_msbfs(src, profile=True) for _ in range(3)), key=lambda r: r.stats["device_ms"])
+    r = runs[1]
+    lv = r.values
+    te = sum(int(deg[lv[j] != 0xFFFFFFFF].sum().item()) for j in range(nsrc))
+    ms_b = r.stats["device_ms"]
+    single = 0.0
+    for s in src:
+        single += _median_run(G, "bfs", reps=1, source=s).stats["device_ms"]
+    _emit({"config": "c4", "graph": "rmat22", "vertices": g.num_vertices, "edges": g.num_edges,
+           "partition_size": 16384, "algo": "msbfs", "sources": nsrc, "passes": (nsrc + 31) // 32,
+           "iterations": r.stats["iterations"], "ms": ms_b, "traversed_edges": te,
+           "gteps": te / (ms_b / 1e3) / 1e9, "single_source_ms_total": single,
+           "single_source_gteps": te / (single / 1e3) / 1e9, "batching_speedup": single / ms_b,
+           "pc_partition_steps": r.stats["pc_partition_steps"], "sc_partition_steps": r.stats["sc_partition_steps"],
+           "kernels_ms": _kernels(r.stats)})
+    G.close()
+
+
 def ablation():
     gg = _gen()
     g = gg.rmat(24).with_weights()
@@ -156,9 +183,9 @@ def ablation():
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--configs", default="c1,c2,c3,ablation")
+    ap.add_argument("--configs", default="c1,c2,c3,c4,ablation")
     a = ap.parse_args()
-    fns = {"c1": c1, "c2": c2, "c3": c3, "ablation": ablation}
+    fns = {"c1": c1, "c2": c2, "c3": c3, "c4": c4, "ablation": ablation}
     for c in a.configs.split(","):
         fns[c]()
 

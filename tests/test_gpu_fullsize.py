@@ -49,6 +49,34 @@ def test_rmat22_bfs_sssp_exact(gp, rmat22):
     G.close()
 
 
+def test_rmat22_msbfs_64_sources(gp, rmat22):
+    # 64 sources in two 32-source passes at the bench partition size: rows of four sources against the
+    # full oracle BFS; every row against properties that fix BFS levels (source at 0, no edge spans more
+    # than one level downwards, every reached vertex but the source has an in-neighbour one level up)
+    g = rmat22
+    G = gp.Graph.from_csr(g.row_ptr, g.col, None, partition_size=P_BENCH)
+    src = np.asarray(gg.roots(g, 64), dtype=np.int64)
+    r = G.run_msbfs(src)
+    lv = r.values
+    for j in (0, 31, 32, 63):
+        assert np.array_equal(lv[j].cpu().numpy(), O.bfs(g, int(src[j]))[0])
+    u = torch.from_numpy(g.src().astype(np.int64)).cuda()
+    v = torch.from_numpy(g.col.astype(np.int64)).cuda()
+    inf = O.U32_INF
+    for j in range(64):
+        L = lv[j].to(torch.int64)
+        assert int(L[int(src[j])]) == 0
+        lu, lw = L[u], L[v]
+        reached = lu != inf
+        assert bool((lw[reached] <= lu[reached] + 1).all())
+        # a vertex at level l > 0 has an in-neighbour at level l - 1
+        good = torch.zeros_like(L, dtype=torch.bool)
+        good[v[reached & (lw == lu + 1)]] = True
+        good[int(src[j])] = True
+        assert bool((good | (L == inf)).all())
+    G.close()
+
+
 def test_rmat22_cc_exact(gp, rmat22):
     gs = gg.symmetrized(rmat22)
     G = gp.Graph.from_csr(gs.row_ptr, gs.col, partition_size=P_BENCH)

@@ -160,6 +160,94 @@ def test_large_partitions_multi_task_columns(case):
         assert np.array_equal(r.values.cpu().numpy(), dist), pol
 
 
+# --- multi-source BFS (gpop_run_msbfs) ------------------------------------------------------------
+
+def _sources(g, n, seed=3):
+    rng = np.random.default_rng(seed)
+    src = rng.integers(0, g.num_vertices, size=n)
+    if n > 4:
+        src[3] = src[1]  # a repeated source
+    return src
+
+
+@pytest.mark.parametrize("name,g", SMALL, ids=[s[0] for s in SMALL])
+@pytest.mark.parametrize("P", [32, 1024])
+def test_msbfs_small(name, g, P):
+    # 40 sources: one full 32-source pass and a ragged pass of 8
+    Gd = G(g, P)
+    src = _sources(g, 40)
+    ref = O.msbfs(g, src)
+    for pol in POLICIES:
+        r = Gd.run_msbfs(src, mode=pol)
+        assert np.array_equal(r.values.cpu().numpy(), ref), pol
+    r = Gd.run_msbfs(src[:7], device_out=False)
+    assert np.array_equal(r.values, ref[:7])
+
+
+@pytest.mark.parametrize("case", ["rmat18_p8192", "rmat18_p16384", "dense_column"])
+def test_msbfs_large_partitions(case):
+    if case == "dense_column":
+        g, P = _dense_column_graph()
+    else:
+        g, P = gg.rmat(18), int(case.split("_p")[1])
+    Gd = G(g, P)
+    src = _sources(g, 33, seed=5)
+    ref = O.msbfs(g, src)
+    for pol in POLICIES:
+        r = Gd.run_msbfs(src, mode=pol)
+        assert np.array_equal(r.values.cpu().numpy(), ref), pol
+
+
+@pytest.mark.parametrize("scale,P", [(12, 64), (14, 512)])
+def test_msbfs_modes_follow_union_frontier(scale, P):
+    # frontier entering iteration t = vertices some source reached at level t - 1; each partition's mode is
+    # Eq. (mode) on that frontier's V_a and E_a (exact integers on both sides)
+    g = gg.rmat(scale)
+    Gd = G(g, P)
+    src = _sources(g, 32, seed=11)
+    ref = O.msbfs(g, src)
+    r = Gd.run_msbfs(src, trace=True)
+    assert np.array_equal(r.values.cpu().numpy(), ref)
+    Ep, npng = O.partition_stats(g, P)
+    k = Ep.shape[0]
+    deg = np.diff(g.row_ptr).astype(np.int64)
+    lv = ref.astype(np.int64)
+    depth = int(lv[lv != O.U32_INF].max()) + 1
+    assert r.stats["iterations"] == depth
+    for t in range(depth):
+        front = (lv == t).any(axis=0)
+        assert r.frontier[t, 0] == int(front.sum())
+        assert r.frontier[t, 1] == int(deg[front].sum())
+        part = np.arange(g.num_vertices) // P
+        Va = np.bincount(part[front], minlength=k)
+        Ea = np.bincount(part[front], weights=deg[front], minlength=k).astype(np.int64)
+        exp = [O.mode_decide(k, int(Ep[q]), int(npng[q]), int(Va[q]), int(Ea[q])) for q in range(k)]
+        assert np.array_equal(r.modes[t], np.array(exp, dtype=np.uint8)), t
+
+
+def test_msbfs_edge_cases():
+    import paper_1806_08092_gb300 as gp
+    g = gg.rmat(10)
+    Gd = G(g, 64)
+    r = Gd.run_msbfs([])
+    assert tuple(r.values.shape) == (0, g.num_vertices) and r.stats["iterations"] == 0
+    with pytest.raises(gp.GpopError):
+        Gd.run_msbfs([0, g.num_vertices])
+    # one source repeated 32 times: every row the single BFS
+    root = int(gg.roots(g, 1)[0])
+    r = Gd.run_msbfs([root] * 32)
+    assert np.array_equal(r.values.cpu().numpy(), np.tile(O.bfs(g, root)[0], (32, 1)))
+    # max_iters caps each pass: iteration t discovers level t, deeper levels stay unreached
+    ref = O.msbfs(g, [root])
+    r = Gd.run_msbfs([root], max_iters=2)
+    exp = np.where(ref <= 2, ref, np.uint32(O.U32_INF))
+    assert np.array_equal(r.values.cpu().numpy(), exp)
+    # a single-vertex graph
+    one = gg.ring(1)
+    r = G(one, 32).run_msbfs([0, 0, 0])
+    assert np.array_equal(r.values.cpu().numpy(), np.zeros((3, 1), dtype=np.uint32))
+
+
 # BF16 messages: each message is rounded to 8 mantissa bits (relative error <= 2^-9), and the PageRank
 # fixed point amplifies a uniform relative perturbation of the messages by at most d / (1 - d) = 5.7
 BF16_TOL = 2e-2

@@ -168,6 +168,31 @@ def test_bfs_path_closed_form():
     assert np.array_equal(parent, np.concatenate([[0], np.arange(24)]))
 
 
+@pytest.mark.parametrize("g", [gg.rmat(10), gg.uniform(700, 2000), gg.disjoint_rings([4, 9, 1])],
+                         ids=lambda g: g.name)
+def test_msbfs_against_scipy_all_sources(g):
+    # 40 sources with repeats (more than one 32-source pass of the GPU path)
+    rng = np.random.default_rng(7)
+    src = rng.integers(0, g.num_vertices, size=40)
+    src[5] = src[17]
+    lv = O.msbfs(g, src)
+    dist = csgraph.shortest_path(scipy_csr(g), unweighted=True, indices=src.astype(np.int64))
+    exp = np.full(dist.shape, O.U32_INF, dtype=np.uint64)
+    exp[~np.isinf(dist)] = dist[~np.isinf(dist)].astype(np.uint64)
+    assert lv.shape == (40, g.num_vertices)
+    assert np.array_equal(lv.astype(np.uint64), exp)
+
+
+def test_msbfs_ring_closed_form():
+    # directed ring of n: level from s to v is (v - s) mod n
+    n = 29
+    src = np.array([0, 3, 28, 3])
+    lv = O.msbfs(gg.ring(n), src)
+    v = np.arange(n)
+    for j, s in enumerate(src):
+        assert np.array_equal(lv[j], (v - s) % n)
+
+
 @pytest.mark.parametrize("g", [gg.symmetrized(gg.rmat(11)), gg.symmetrized(gg.uniform(2000, 1500)),
                                gg.disjoint_rings([5, 1, 8, 2])], ids=lambda g: g.name)
 def test_cc_against_scipy(g):
