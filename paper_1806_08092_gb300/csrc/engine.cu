@@ -832,32 +832,36 @@ __device__ __forceinline__ uint32_t pc_round_end(const uint32_t *sp, int w, cons
 // them; positions that end no inner run update the scratch word sink; shared atomics measured slower).
 // Padding entries repeat their range's last destination and read the padding value slot (the identity),
 // so they fold as no-ops.
-template <int ALGO, bool B16>
+template <int ALGO, bool B16, uint32_t K>
 __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt, uint32_t j0, const uint32_t *stage,
                                         uint32_t *acc, uint32_t *sink, bool check_null, uint32_t &fd,
                                         uint32_t &head, uint32_t &run_d, uint32_t &run_v, bool &in_head) {
     using O = Op<ALGO>;
-    constexpr uint32_t K = PcShape<ALGO>::K;
+    static_assert(K == 4 || K % 8 == 0, "a lane folds whole quads of a 16-entry group, 8 entries per batch");
+    constexpr uint32_t HB = K < 8 ? K : 8;  // entries per batch
     // quads of a 16-entry group are stored swizzled by (group >> 1) & 3 (see the build); the lane's
     // entries start at round position j0, in group j0 / 16
     const uint32_t gbase = j0 & ~15u, qsw = ((j0 >> 5) & 3u), q0 = (j0 & 15u) >> 2;
     const bool nullable = ALGO == ALG_SSSP || ALGO == ALG_PPR || (ALGO == ALG_PR && check_null);
 #pragma unroll
-    for (uint32_t hb = 0; hb < K; hb += 8) {
-        const uint32_t o0 = gbase + (((q0 + hb / 4) ^ qsw) << 2), o1 = gbase + (((q0 + hb / 4 + 1) ^ qsw) << 2);
-        const uint4 e0 = *reinterpret_cast<const uint4 *>(ent + o0);
-        const uint4 e1 = *reinterpret_cast<const uint4 *>(ent + o1);
-        const uint32_t ee[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
-        int32_t ww[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (ALGO == ALG_SSSP) {
-            const int4 w0 = *reinterpret_cast<const int4 *>(wgt + o0);
-            const int4 w1 = *reinterpret_cast<const int4 *>(wgt + o1);
-            ww[0] = w0.x; ww[1] = w0.y; ww[2] = w0.z; ww[3] = w0.w;
-            ww[4] = w1.x; ww[5] = w1.y; ww[6] = w1.z; ww[7] = w1.w;
-        }
-        uint32_t d[8], x[8];
+    for (uint32_t hb = 0; hb < K; hb += HB) {
+        uint32_t ee[HB];
+        int32_t ww[HB];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (uint32_t qq = 0; qq < HB / 4; ++qq) {
+            const uint32_t o = gbase + (((q0 + hb / 4 + qq) ^ qsw) << 2);
+            const uint4 e4 = *reinterpret_cast<const uint4 *>(ent + o);
+            ee[4 * qq] = e4.x; ee[4 * qq + 1] = e4.y; ee[4 * qq + 2] = e4.z; ee[4 * qq + 3] = e4.w;
+            if (ALGO == ALG_SSSP) {
+                const int4 w4 = *reinterpret_cast<const int4 *>(wgt + o);
+                ww[4 * qq] = w4.x; ww[4 * qq + 1] = w4.y; ww[4 * qq + 2] = w4.z; ww[4 * qq + 3] = w4.w;
+            } else {
+                ww[4 * qq] = ww[4 * qq + 1] = ww[4 * qq + 2] = ww[4 * qq + 3] = 0;
+            }
+        }
+        uint32_t d[HB], x[HB];
+#pragma unroll
+        for (uint32_t i = 0; i < HB; ++i) {
             d[i] = ee[i] >> 16;
             if (B16) {  // BF16 values staged as 16-bit words
                 const uint32_t h = reinterpret_cast<const uint16_t *>(stage)[ee[i] & 0xFFFFu];
@@ -866,11 +870,11 @@ __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt
                 x[i] = stage[ee[i] & 0xFFFFu];
             }
         }
-        bool fl[8];
-        uint32_t fk[8], fv[8];
+        bool fl[HB];
+        uint32_t fk[HB], fv[HB];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            // NULL (0xFFFFFFFF) is the min identity, so BFS and CC fold it as is
+        for (uint32_t i = 0; i < HB; ++i) {
+            // NULL (0xFFFFFFFF) is the identity of min and of AND, so BFS, CC and multi-source BFS fold it as is
             const uint32_t v = (!nullable || x[i] != kNull) ? O::weigh(x[i], ww[i]) : O::identity();
             if (hb == 0 && i == 0) {
                 fd = run_d = d[0];
@@ -889,30 +893,29 @@ __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt
             run_d = d[i];
         }
         // branch-free read-modify-writes: positions that end no inner run update a scratch word
-        uint32_t *dst[8], old[8];
+        uint32_t *dst[HB], old[HB];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) dst[i] = fl[i] ? acc + fk[i] : sink;
+        for (uint32_t i = 0; i < HB; ++i) dst[i] = fl[i] ? acc + fk[i] : sink;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) old[i] = *dst[i];
+        for (uint32_t i = 0; i < HB; ++i) old[i] = *dst[i];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) *dst[i] = O::combine(old[i], fv[i]);
+        for (uint32_t i = 0; i < HB; ++i) *dst[i] = O::combine(old[i], fv[i]);
     }
 }
 
-// One warp round: n round positions (a multiple of K), sorted by destination, all inside this warp's
-// destination slice of the block.  Lane l folds positions [l K, (l+1) K) serially; one segmented warp
+// One warp round: n <= 32 K round positions (a multiple of 16), sorted by destination, all inside this
+// warp's destination slice of the block.  Lane l folds positions [l K, (l+1) K) serially; one segmented warp
 // scan, keyed by destination, joins the lanes' last runs, and a lane's first run takes the scan value of
 // the lane before it when they share the destination.  Every complete run is folded into acc directly:
 // a run cut by the round's end continues in the warp's next round, folded after this part.
-template <int ALGO, bool B16>
+template <int ALGO, bool B16, uint32_t K>
 __device__ __forceinline__ void pc_round(const uint32_t *ent, const uint32_t *wgt, uint32_t n, const uint32_t *stage,
                                          uint32_t *acc, uint32_t *sink, bool check_null, int lane) {
     using O = Op<ALGO>;
-    constexpr uint32_t K = PcShape<ALGO>::K;
     const uint32_t j0 = lane * K;
     uint32_t fd = kSent, head = O::identity(), run_d = kSent, run_v = O::identity();
     bool in_head = true;
-    if (j0 < n) pc_lane<ALGO, B16>(ent, wgt, j0, stage, acc, sink, check_null, fd, head, run_d, run_v, in_head);
+    if (j0 < n) pc_lane<ALGO, B16, K>(ent, wgt, j0, stage, acc, sink, check_null, fd, head, run_d, run_v, in_head);
     const bool uni = in_head;  // all K positions share one destination
     const uint32_t ld = run_d;
     uint32_t S = run_v;
@@ -1101,8 +1104,19 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
                 ph ^= 1u << head_slot;
                 const uint32_t e = pc_round_end<C>(s_sp, wid, cc);
                 const uint32_t *slot = ring + head_slot * kSlotWords;
-                pc_round<ALGO, B16>(slot, slot + C, e - cc.s, stage + buf * kStageWords, acc, &s_sink, p.pc_skip != 0,
-                               lane);
+                // a short round (the tail of a warp's slice) is spread over all lanes: 8 or 4 positions
+                // per lane instead of K
+                constexpr uint32_t K = PcShape<ALGO>::K;
+                const uint32_t n = e - cc.s;
+                const uint32_t *vals = stage + buf * kStageWords;
+                const bool chk = p.pc_skip != 0;
+                if (n <= 128) {
+                    pc_round<ALGO, B16, 4>(slot, slot + C, n, vals, acc, &s_sink, chk, lane);
+                } else if (K == 16 && n <= 256) {
+                    pc_round<ALGO, B16, 8>(slot, slot + C, n, vals, acc, &s_sink, chk, lane);
+                } else {
+                    pc_round<ALGO, B16, K>(slot, slot + C, n, vals, acc, &s_sink, chk, lane);
+                }
                 __syncwarp();  // the slot is refilled only after every lane has read it
                 --inflight;
                 head_slot = head_slot + 1 == ns ? 0 : head_slot + 1;
@@ -1336,6 +1350,10 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                 }
                 uint32_t nv[4], ns[4];
                 bool wrote_lv = false;
+                // L1 change of the four vertices: each |x_new - x_old| rounded once in FP32 and their sum
+                // carried in FP64 (FP64 instructions are scarce on this GPU: one conversion and one add
+                // per four vertices)
+                float res4 = 0.f;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const uint32_t g = g0 + c;
@@ -1351,7 +1369,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                         float xo = u2f(vals[c]);
                         float xn = fmaf(p.c1, u2f(m), p.c0);
                         nv[c] = f2u(xn);
-                        res += fabs((double)xn - (double)xo);
+                        res4 += fabsf(xn - xo);
                         act = true;
                         ns[c] = f2u(deg ? xn / (float)deg : 0.f);
                     } else if (ALGO == ALG_PPR) {
@@ -1363,7 +1381,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                         if (cont || recv) xn = fmaf(p.c1, u2f(m), g == p.source ? p.c0 : 0.f);
                         act = (cont || recv) && xn > 0.f;
                         nv[c] = f2u(xn);
-                        res += fabs((double)xn - (double)xo);
+                        res4 += fabsf(xn - xo);
                         if (act) ns[c] = f2u(deg ? xn / (float)deg : 0.f);
                     } else if (ALGO == ALG_MSBFS) {
                         // Alg. 5 for every source of the pass at once: the sources that reach the vertex
@@ -1398,6 +1416,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                         ea += deg;
                     }
                 }
+                if (ALGO == ALG_PR || ALGO == ALG_PPR) res += (double)res4;
                 if (full) {
                     if (nv[0] != vals[0] || nv[1] != vals[1] || nv[2] != vals[2] || nv[3] != vals[3])
                         *reinterpret_cast<uint4 *>(p.val + g0) = make_uint4(nv[0], nv[1], nv[2], nv[3]);
