@@ -542,11 +542,76 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
 
 // --- PC scatter (Alg. 3) -----------------------------------------------------------------------
 
+// --- mbarriers and bulk copies (k_scatter_pc value staging, k_gather_pc buffers) ---------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// makes the barrier initialisations visible to the asynchronous (bulk copy) proxy
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+// 1-D bulk copy global -> shared (TMA engine): 16-byte aligned addresses, size a multiple of 16; the bytes
+// are counted against the barrier's transaction count when they land
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the completion of the barrier phase with the given parity, at most kPcSpinLimit tries;
+// gives up early when another warp has raised *abort, and raises it (with the run's error flag) when
+// its own tries run out.  Returns false when the caller must stop.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort, uint32_t *err) {
+    for (uint32_t it = 0; it < kPcSpinLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+    }
+    *abort = 1;
+    atomicOr(err, 1u);
+    return false;
+}
+
+// Bounded wait used while leaving after an abort: lets copies still in flight land before the CTA exits.
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kPcSpinLimit && !mbar_try_wait(bar, parity); ++it) {
+    }
+}
+
+// --- PC scatter (Alg. 3) -----------------------------------------------------------------------
+
+// One CTA per scatter task: a chunk of one partition's PNG row (Alg. 3 for a PC partition, or a row
+// chunk refilled with NULL when the partition's data row must be cleared).  A PC task stages the
+// partition's P message values in shared memory with one bulk copy (TMA; bounded mbarrier wait) and
+// streams its chunk of the row: each thread reads four 16-byte groups of 8 PNG source IDs ahead and
+// writes the 8 values of each group as two 16-byte stores.
 template <bool B16>
 __global__ void __launch_bounds__(kScatterThreads) k_scatter_pc(Params p) {
     extern __shared__ __align__(16) uint32_t s_val[];  // the partition's P message values (PC rows)
-    __shared__ uint32_t s_task;
+    __shared__ __align__(8) uint64_t s_bar;            // completion of the value copy
+    __shared__ uint32_t s_task, s_ok;
     __shared__ unsigned long long s_t0;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar, 1);
+        fence_mbar_init();
+    }
+    uint32_t phase = 0;  // parity of s_bar's current phase
     for (;;) {
         if (threadIdx.x == 0) s_task = atomicAdd(&p.counters[p.counter_slot], 1u);
         __syncthreads();
@@ -568,41 +633,70 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_pc(Params p) {
             }
         }
         const uint32_t vbase = st.p << p.shift;
-        if (act == kActPC) {  // stage the partition's values (NULL for inactive sources), 16 B per load
-            const uint32_t wv = min(p.P, p.V - vbase);
-            for (uint32_t i = threadIdx.x * 4; i < wv; i += blockDim.x * 4) {
-                if (i + 4 <= wv) {
-                    *reinterpret_cast<uint4 *>(s_val + i) = *reinterpret_cast<const uint4 *>(p.sval + vbase + i);
-                } else {
-                    for (uint32_t c = i; c < wv; ++c) s_val[c] = p.sval[vbase + c];
+        if (act == kActPC) {
+            // stage the partition's values (NULL for inactive sources): the 16-byte multiple by one bulk
+            // copy, the last (V mod 4) values of a ragged final partition by plain loads.  The barrier at the
+            // top of the loop ordered every read of the previous task's values before this copy.
+            const uint32_t wv = min(p.P, p.V - vbase), wa = wv & ~3u;
+            if (threadIdx.x == 0) {
+                s_ok = 1;
+                if (wa) {
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    mbar_arrive_expect_tx(&s_bar, wa * 4u);
+                    bulk_g2s(s_val, p.sval + vbase, wa * 4u, &s_bar);
                 }
             }
-            __syncthreads();
-        }
-        for (uint32_t i = st.beg + threadIdx.x * 8; i < st.end; i += blockDim.x * 8) {
-            uint4 o0, o1;
-            if (act == kActPC) {  // padding slots hold source 0: staged, never gathered
-                uint4 s = *reinterpret_cast<const uint4 *>(p.png + i);
-                o0.x = s_val[s.x & 0xFFFFu];
-                o0.y = s_val[s.x >> 16];
-                o0.z = s_val[s.y & 0xFFFFu];
-                o0.w = s_val[s.y >> 16];
-                o1.x = s_val[s.z & 0xFFFFu];
-                o1.y = s_val[s.z >> 16];
-                o1.z = s_val[s.w & 0xFFFFu];
-                o1.w = s_val[s.w >> 16];
-            } else {
-                o0 = make_uint4(kNull, kNull, kNull, kNull);
-                o1 = o0;
+            for (uint32_t c = wa + threadIdx.x; c < wv; c += blockDim.x) s_val[c] = p.sval[vbase + c];
+            if (wa && threadIdx.x == 0) {
+                uint32_t it = 0;
+                while (it < kPcSpinLimit && !mbar_try_wait(&s_bar, phase)) ++it;
+                if (it == kPcSpinLimit) {
+                    atomicOr(&p.ctrl->error, 1u);
+                    mbar_drain(&s_bar, phase);
+                    s_ok = 0;
+                }
             }
-            if (B16) {  // 8 BF16 slots in one 16-byte store (slot 2k in the low half of word k)
-                const uint4 h = make_uint4(to_bf16(o0.x) | (to_bf16(o0.y) << 16), to_bf16(o0.z) | (to_bf16(o0.w) << 16),
-                                           to_bf16(o1.x) | (to_bf16(o1.y) << 16), to_bf16(o1.z) | (to_bf16(o1.w) << 16));
-                *reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(p.pdata) + i) = h;
-            } else {
-                uint4 *dst = reinterpret_cast<uint4 *>(p.pdata + i);
-                dst[0] = o0;
-                dst[1] = o1;
+            if (wa) phase ^= 1u;
+            __syncthreads();
+            if (!s_ok) return;  // the run reports the error; the copy has landed or been waited out
+        }
+        const uint32_t stride = blockDim.x * 8;
+        for (uint32_t i0 = st.beg + threadIdx.x * 8; i0 < st.end; i0 += 4 * stride) {
+            uint4 sx[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {  // up to four independent 16-byte loads in flight
+                const uint32_t i = i0 + u * stride;
+                sx[u] = (act == kActPC && i < st.end) ? *reinterpret_cast<const uint4 *>(p.png + i)
+                                                       : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t i = i0 + u * stride;
+                if (i >= st.end) break;
+                uint4 o0, o1;
+                if (act == kActPC) {  // padding slots hold source 0: staged, never gathered
+                    const uint4 sv = sx[u];
+                    o0.x = s_val[sv.x & 0xFFFFu];
+                    o0.y = s_val[sv.x >> 16];
+                    o0.z = s_val[sv.y & 0xFFFFu];
+                    o0.w = s_val[sv.y >> 16];
+                    o1.x = s_val[sv.z & 0xFFFFu];
+                    o1.y = s_val[sv.z >> 16];
+                    o1.z = s_val[sv.w & 0xFFFFu];
+                    o1.w = s_val[sv.w >> 16];
+                } else {
+                    o0 = make_uint4(kNull, kNull, kNull, kNull);
+                    o1 = o0;
+                }
+                if (B16) {  // 8 BF16 slots in one 16-byte store (slot 2k in the low half of word k)
+                    const uint4 h = make_uint4(to_bf16(o0.x) | (to_bf16(o0.y) << 16), to_bf16(o0.z) | (to_bf16(o0.w) << 16),
+                                               to_bf16(o1.x) | (to_bf16(o1.y) << 16), to_bf16(o1.z) | (to_bf16(o1.w) << 16));
+                    *reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(p.pdata) + i) = h;
+                } else {
+                    uint4 *dst = reinterpret_cast<uint4 *>(p.pdata + i);
+                    dst[0] = o0;
+                    dst[1] = o1;
+                }
             }
         }
         if (p.t_task) {
@@ -754,57 +848,6 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
 
 // --- gather + filter ---------------------------------------------------------------------------
 
-// --- mbarriers (block value buffers of k_gather_pc) ---------------------------------------------
-
-__device__ __forceinline__ uint32_t smem_addr(const void *ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-// makes the barrier initialisations visible to the asynchronous (bulk copy) proxy
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
-// 1-D bulk copy global -> shared (TMA engine): 16-byte aligned addresses, size a multiple of 16; the bytes
-// are counted against the barrier's transaction count when they land
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Waits for the completion of the barrier phase with the given parity, at most kPcSpinLimit tries;
-// gives up early when another warp has raised *abort, and raises it (with the run's error flag) when
-// its own tries run out.  Returns false when the caller must stop.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort, uint32_t *err) {
-    for (uint32_t it = 0; it < kPcSpinLimit; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*abort) return false;
-    }
-    *abort = 1;
-    atomicOr(err, 1u);
-    return false;
-}
-
-// Bounded wait used while leaving after an abort: lets copies still in flight land before the CTA exits.
-__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kPcSpinLimit && !mbar_try_wait(bar, parity); ++it) {
-    }
-}
 
 // Position in one warp's entry stream through a PC gather task: block i (relative to the
 // task's first block), next entry s.  sp[i * (kPcWarps + 1) + w] .. [.. + w + 1] bound warp w's entries in
