@@ -155,7 +155,8 @@ typedef struct {
     uint64_t log_records;         /* LOG_BOTH records written */
     /* with opts.profile_kernels: per kernel kind (0 plan (+ learned selection), 1 PC scatter,
        2 SC scatter, 3 task gather + filter, 4 PC gather, 5 merge of split columns' PC partials) the
-       summed CUDA-event duration and the number of launches */
+       summed CUDA-event duration and the number of launches (a kind the plan gives nothing to do in
+       an iteration is not launched) */
     double kernel_ms[6];
     uint64_t kernel_launches[6];
 } gpop_run_stats;

@@ -38,7 +38,8 @@ enum Algo : int {
 
 constexpr int kGatherThreads = 256;
 constexpr int kGatherWarps = kGatherThreads / 32;
-constexpr int kScatterThreads = 256;
+constexpr int kScatterThreads = 256;    // k_scatter_sc
+constexpr int kScatterPcThreads = 512;  // k_scatter_pc
 constexpr int kPlanThreads = 1024;
 constexpr uint32_t kSent = 0xFFFFFFFFu;
 constexpr uint32_t kScUnitEdges = 1u << 16;  // active edges per SC scatter unit of a split partition
@@ -101,6 +102,7 @@ struct Params {
     uint4 *sc_list;                   // SC scatter units: (partition, unit, units, active edges)
     uint32_t *sc_gcur, *sc_udone;     // split SC partitions: bin cursors and finished units (zero at rest)
     Control *ctrl;
+    Control *ctrl_snap;     // the plan's snapshot for the host: mapped pinned memory, slot (iter - 1) & 1
     const float *selector;  // learned selector parameters (W1, W2 transposed) or null
     uint8_t *sel_mode;      // learned policy: per-partition choice for the next plan (k_select / k_gather tail)
     uint32_t *col_done;     // learned policy: finished gather tasks per column (zero at rest)
@@ -529,6 +531,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         p.pc_prefix[p.k] = pc_base;
         c.pad = 0;
         *p.ctrl = c;
+        p.ctrl_snap[(p.iter - 1) & 1] = c;  // read by the host once the plan has finished
+        __threadfence_system();
         for (int i = 0; i < 8; ++i) p.counters[i] = 0;
         p.counters[7] = all_base;  // LOG_BOTH: size of all_list
         s_done = done;
@@ -602,7 +606,7 @@ __device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
 // streams its chunk of the row: each thread reads four 16-byte groups of 8 PNG source IDs ahead and
 // writes the 8 values of each group as two 16-byte stores.
 template <bool B16>
-__global__ void __launch_bounds__(kScatterThreads) k_scatter_pc(Params p) {
+__global__ void __launch_bounds__(kScatterPcThreads) k_scatter_pc(Params p) {
     extern __shared__ __align__(16) uint32_t s_val[];  // the partition's P message values (PC rows)
     __shared__ __align__(8) uint64_t s_bar;            // completion of the value copy
     __shared__ uint32_t s_task, s_ok;
@@ -1017,6 +1021,7 @@ __device__ __forceinline__ uint4 pc_first_run(const Params &p, uint32_t r0, uint
 // is raised and all warps leave.
 template <int ALGO, bool B16>
 __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
+    const bool pc_skip = p.pc_skip != 0;  // some partition is not PC: skip blocks whose sources all are not
     using O = Op<ALGO>;
     constexpr uint32_t C = PcShape<ALGO>::kRound, kSlotWords = PcShape<ALGO>::kSlotWords;
     constexpr uint32_t kSp = kPcWarps + 1, kStageWords = kPcBlock + 4;
@@ -1084,8 +1089,8 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
         const uint32_t wq = min(p.P, p.V - gq);
         // a block only holds NULLs unless one of its source partitions sent PC messages this iteration
         if (threadIdx.x < nb) {
-            const uint2 pr = p.pc_skip ? p.pc_blk_prange[tk.y + threadIdx.x] : make_uint2(0, 0);
-            s_blist[threadIdx.x] = !p.pc_skip || p.pc_prefix[pr.y + 1] != p.pc_prefix[pr.x];
+            const uint2 pr = pc_skip ? p.pc_blk_prange[tk.y + threadIdx.x] : make_uint2(0, 0);
+            s_blist[threadIdx.x] = !pc_skip || p.pc_prefix[pr.y + 1] != p.pc_prefix[pr.x];
         }
         for (uint32_t i = threadIdx.x; i < wq; i += kPcThreads) acc[i] = O::identity();
         __syncthreads();
@@ -1152,7 +1157,7 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
                 constexpr uint32_t K = PcShape<ALGO>::K;
                 const uint32_t n = e - cc.s;
                 const uint32_t *vals = stage + buf * kStageWords;
-                const bool chk = p.pc_skip != 0;
+                const bool chk = pc_skip;
                 if (n <= 128) {
                     pc_round<ALGO, B16, 4>(slot, slot + C, n, vals, acc, &s_sink, chk, lane);
                 } else if (K == 16 && n <= 256) {
@@ -1544,7 +1549,7 @@ struct RunBuffers {
     uint4 *sc_list = nullptr;
     uint32_t *sc_gcur = nullptr, *sc_udone = nullptr, *pc_prefix = nullptr;
     uint32_t *task_sc_cnt = nullptr, *task_sc_list = nullptr, *pc_sum = nullptr;
-    Control *ctrl = nullptr, *h_ctrl = nullptr;
+    Control *ctrl = nullptr, *h_ctrl = nullptr, *d_ctrl_snap = nullptr;
     // LOG_BOTH only (allocated on first use)
     uint32_t *shadow = nullptr, *part_va = nullptr;
     uint4 *all_list = nullptr;
@@ -1599,7 +1604,10 @@ static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
     A(&rb->pc_sum, g->V);
     A(&rb->task_sc_list, g->nsub);
     A(&rb->ctrl, 1);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&rb->h_ctrl, sizeof(Control));
+    // the plans' snapshots: two slots of mapped pinned memory that k_plan writes directly (no copy in the
+    // stream between a plan and its iteration's kernels)
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&rb->h_ctrl, 2 * sizeof(Control), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&rb->d_ctrl_snap, rb->h_ctrl, 0);
     if (e == cudaSuccess) e = cudaMemset(rb->t_stamp, 0, 4ull * std::max<uint32_t>(g->ngt, 1));
     if (e == cudaSuccess) e = cudaMemset(rb->gflag, 0, 4ull * g->k);
     if (e == cudaSuccess) e = cudaMemset(rb->gflag_pc, 0, 4ull * g->k);
@@ -1715,7 +1723,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     p.val = rb->val; p.lvl = rb->lvl; p.sval = rb->sval; p.bits = rb->bits;
     p.t_va = rb->t_va; p.t_ea = rb->t_ea; p.t_res = rb->t_res; p.t_stamp = rb->t_stamp;
     p.mode = rb->mode; p.action = rb->action; p.sel_mode = rb->sel_mode; p.gflag = rb->gflag; p.gflag_pc = rb->gflag_pc;
-    p.sc_list = rb->sc_list; p.sc_gcur = rb->sc_gcur; p.sc_udone = rb->sc_udone; p.pc_prefix = rb->pc_prefix; p.counters = rb->counters; p.ctrl = rb->ctrl;
+    p.sc_list = rb->sc_list; p.sc_gcur = rb->sc_gcur; p.sc_udone = rb->sc_udone; p.pc_prefix = rb->pc_prefix; p.counters = rb->counters; p.ctrl = rb->ctrl; p.ctrl_snap = rb->d_ctrl_snap;
     p.selector = (o->mode == GPOP_MODE_LEARNED) ? selector_device_params_transposed() : nullptr;
     p.list = rb->sc_list; p.list_count = &rb->ctrl->n_sc_units; p.counter_slot = 0; p.dry = 0; p.t_task = nullptr;
     p.t_gpc = nullptr;
@@ -1758,7 +1766,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     // k_scatter_pc stages one partition's values (P words) in dynamic shared memory
     const size_t spc_smem = sizeof(uint32_t) * (size_t)g->P;
     GPOP_CUDA_TRY(cudaFuncSetAttribute(k_scatter_pc<B16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spc_smem));
-    grid_pc = persistent_grid(k_scatter_pc<B16>, kScatterThreads, spc_smem, g->num_sms);
+    grid_pc = persistent_grid(k_scatter_pc<B16>, kScatterPcThreads, spc_smem, g->num_sms);
     grid_sc = persistent_grid(k_scatter_sc<ALGO, B16>, kScatterThreads, sc_smem, g->num_sms);
     grid_ga = persistent_grid(k_gather<ALGO, B16>, kGatherThreads, 0, g->num_sms);
     // k_gather_pc: column accumulator, two block value buffers and as many entry-chunk slots as the
@@ -1805,57 +1813,89 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     GPOP_CUDA_TRY(cudaEventRecord(ev0, s));
     // optional per-kernel CUDA-event timing: a start/stop pair per kernel kind, resolved at the
     // next host synchronisation (which the plan's control read provides every iteration)
+    // Launches between two host synchronisations form a chain of events: one record before the first
+    // launch and one after each, so that launch j takes from event j to event j + 1.
     const bool prof = o->profile_kernels != 0;
-    cudaEvent_t kev[12] = {};
-    bool pend[6] = {false, false, false, false, false, false};
+    cudaEvent_t kev[8] = {};
+    int kind_of[7] = {};
+    int nchain = 0;  // launches in the chain
     if (prof)
         for (auto &ev : kev) GPOP_CUDA_TRY(cudaEventCreate(&ev));
     auto resolve = [&]() {
-        for (int i = 0; i < 6; ++i)
-            if (pend[i]) {
-                float kms = 0.f;
-                cudaEventElapsedTime(&kms, kev[2 * i], kev[2 * i + 1]);
-                st.kernel_ms[i] += kms;
-                st.kernel_launches[i] += 1;
-                pend[i] = false;
-            }
+        for (int j = 0; j < nchain; ++j) {
+            float kms = 0.f;
+            cudaEventElapsedTime(&kms, kev[j], kev[j + 1]);
+            st.kernel_ms[kind_of[j]] += kms;
+            st.kernel_launches[kind_of[j]] += 1;
+        }
+        nchain = 0;
     };
     auto timed = [&](int kind, auto launch) {
-        if (prof) cudaEventRecord(kev[2 * kind], s);
+        if (prof && nchain == 0) cudaEventRecord(kev[0], s);
         launch();
         if (prof) {
-            cudaEventRecord(kev[2 * kind + 1], s);
-            pend[kind] = true;
+            kind_of[nchain] = kind;
+            cudaEventRecord(kev[++nchain], s);
         }
     };
     uint32_t iter = 0;
     gpop_status status = GPOP_OK;
-    for (;;) {
-        p.iter = iter + 1;
-        p.epoch = ++g->epoch;
-        // learned policy: the first plan's choices come from k_select, later ones from the previous
-        // gather's tail (the last task of each column)
-        const bool first_select = learned && iter == 0;
+    // plan of iteration it (0-based): learned policy's first choices from k_select, later ones from the
+    // previous gather's tail (the last task of each column)
+    auto launch_plan = [&](uint32_t it, const Params &pp) {
+        const bool first_select = learned && it == 0;
         timed(0, [&] {
             if (first_select)
                 k_select<<<std::min<uint32_t>((g->k + kSelectWarps - 1) / kSelectWarps, 8u * g->num_sms),
-                           32 * kSelectWarps, 0, s>>>(p);
-            k_plan<<<1, kPlanThreads, 0, s>>>(p);
+                           32 * kSelectWarps, 0, s>>>(pp);
+            k_plan<<<1, kPlanThreads, 0, s>>>(pp);
         });
         if (prof && first_select) st.kernel_launches[0] += 1;  // k_select
-        cudaError_t ce = cudaMemcpyAsync(rb->h_ctrl, rb->ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-        if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("plan: ") + cudaGetErrorString(ce)); break; }
-        if (prof) resolve();
-        const Control c = *rb->h_ctrl;
+    };
+    // scatter and gather of one iteration, as the plan c decided
+    auto launch_work = [&](const Params &pp, const Control &c) -> cudaError_t {
+        if (p.log_both) {
+            // time both modes for every partition picked this iteration (shadow launches first:
+            // the real SC scatter below rewrites the same bins with the same pairs)
+            cudaMemsetAsync(rb->t_gpc, 0, 8, s);
+            cudaMemsetAsync(rb->t_gsc, 0, 8, s);
+            Params q1 = pp;
+            q1.pdata = rb->shadow; q1.dry = 1; q1.counter_slot = 3; q1.t_task = rb->t_pc;
+            k_scatter_pc<B16><<<grid_pc, kScatterPcThreads, spc_smem, s>>>(q1);
+            Params q2 = pp;
+            q2.dry = 1; q2.counter_slot = 4; q2.list = rb->all_list; q2.list_count = &rb->counters[7];
+            q2.t_task = rb->t_sc;
+            cudaMemsetAsync(rb->t_sc, 0, 8ull * g->k, s);  // split partitions add their units' CTA times
+            k_scatter_sc<ALGO, B16><<<grid_sc, kScatterThreads, sc_smem, s>>>(q2);
+        }
+        Params ps = pp;
+        ps.counter_slot = 1;
+        Params pg = pp;
+        pg.t_gsc = p.log_both ? rb->t_gsc : nullptr;
+        Params pgc = pp;
+        pgc.t_gpc = p.log_both ? rb->t_gpc : nullptr;
+        pgc.pc_skip = c.n_pc < g->k;  // some partition is not PC: skip blocks whose sources all are not
+        if (c.n_pc + c.n_null > 0)
+            timed(1, [&] { k_scatter_pc<B16><<<grid_pc, kScatterPcThreads, spc_smem, s>>>(pp); });
+        if (c.n_sc > 0) timed(2, [&] { k_scatter_sc<ALGO, B16><<<grid_sc, kScatterThreads, sc_smem, s>>>(ps); });
+        if (c.n_pc > 0) {
+            timed(4, [&] { k_gather_pc<ALGO, B16><<<grid_gh, kPcThreads, gpc_smem, s>>>(pgc); });
+            if (g->nmerge)
+                timed(5, [&] { k_merge_pc<ALGO><<<std::min<uint32_t>(g->nmerge, 16u * g->num_sms), 256, 0, s>>>(pp); });
+        }
+        timed(3, [&] { k_gather<ALGO, B16><<<grid_ga, kGatherThreads, 0, s>>>(pg); });
+        return cudaGetLastError();
+    };
+    // the plan's verdict on iteration iter: false when the loop stops (termination or error)
+    auto take = [&](const Control &c) -> bool {
         if (c.error) {
-            status = fail(GPOP_ERR_TIMEOUT, "PC gather: a bounded mbarrier wait ran out");
-            break;
+            status = fail(GPOP_ERR_TIMEOUT, "a bounded mbarrier wait ran out");
+            return false;
         }
         st.residual = c.residual;
         if (c.done) {
             st.converged = (c.frontier_v == 0) || ((ALGO == ALG_PR || ALGO == ALG_PPR) && iter > 0 && c.residual < o->tol_l1);
-            break;
+            return false;
         }
         ++iter;
         st.edges_scattered += c.frontier_e;
@@ -1863,6 +1903,19 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         st.pc_partition_steps += c.n_pc;
         st.sc_partition_steps += c.n_sc;
         st.model_bytes += c.model_bytes;
+        return true;
+    };
+    // Each iteration: the plan, the host's read of its snapshot (mapped memory written by k_plan, no copy
+    // in the stream), then the launches the plan asks for
+    for (;;) {
+        p.iter = iter + 1;
+        p.epoch = ++g->epoch;
+        launch_plan(iter, p);
+        cudaError_t ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("plan: ") + cudaGetErrorString(ce)); break; }
+        if (prof) resolve();
+        const Control c = rb->h_ctrl[iter & 1];  // this plan's slot: p.iter - 1 = iter
+        if (!take(c)) break;
         if (o->trace_frontier) {
             o->trace_frontier[2 * (iter - 1)] = c.frontier_v;
             o->trace_frontier[2 * (iter - 1) + 1] = c.frontier_e;
@@ -1871,36 +1924,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
             ce = cudaMemcpyAsync(o->trace_modes + (uint64_t)(iter - 1) * g->k, rb->mode, g->k, cudaMemcpyDeviceToHost, s);
             if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, cudaGetErrorString(ce)); break; }
         }
-        if (p.log_both) {
-            // time both modes for every partition picked this iteration (shadow launches first:
-            // the real SC scatter below rewrites the same bins with the same pairs)
-            cudaMemsetAsync(rb->t_gpc, 0, 8, s);
-            cudaMemsetAsync(rb->t_gsc, 0, 8, s);
-            Params q1 = p;
-            q1.pdata = rb->shadow; q1.dry = 1; q1.counter_slot = 3; q1.t_task = rb->t_pc;
-            k_scatter_pc<B16><<<grid_pc, kScatterThreads, spc_smem, s>>>(q1);
-            Params q2 = p;
-            q2.dry = 1; q2.counter_slot = 4; q2.list = rb->all_list; q2.list_count = &rb->counters[7];
-            q2.t_task = rb->t_sc;
-            cudaMemsetAsync(rb->t_sc, 0, 8ull * g->k, s);  // split partitions add their units' CTA times
-            k_scatter_sc<ALGO, B16><<<grid_sc, kScatterThreads, sc_smem, s>>>(q2);
-        }
-        Params ps = p;
-        ps.counter_slot = 1;
-        Params pg = p;
-        pg.t_gsc = p.log_both ? rb->t_gsc : nullptr;
-        Params pgc = p;
-        pgc.t_gpc = p.log_both ? rb->t_gpc : nullptr;
-        pgc.pc_skip = c.n_pc < g->k;  // some partition is not PC: skip blocks whose sources all are not
-        if (c.n_pc + c.n_null > 0) timed(1, [&] { k_scatter_pc<B16><<<grid_pc, kScatterThreads, spc_smem, s>>>(p); });
-        if (c.n_sc > 0) timed(2, [&] { k_scatter_sc<ALGO, B16><<<grid_sc, kScatterThreads, sc_smem, s>>>(ps); });
-        if (c.n_pc > 0) {
-            timed(4, [&] { k_gather_pc<ALGO, B16><<<grid_gh, kPcThreads, gpc_smem, s>>>(pgc); });
-            if (g->nmerge)
-                timed(5, [&] { k_merge_pc<ALGO><<<std::min<uint32_t>(g->nmerge, 16u * g->num_sms), 256, 0, s>>>(p); });
-        }
-        timed(3, [&] { k_gather<ALGO, B16><<<grid_ga, kGatherThreads, 0, s>>>(pg); });
-        ce = cudaGetLastError();
+        ce = launch_work(p, c);
         if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(ce)); break; }
         if (p.log_both) {
             status = log_iteration(g, rb, o, s, iter, &st);

@@ -160,6 +160,25 @@ def test_large_partitions_multi_task_columns(case):
         assert np.array_equal(r.values.cpu().numpy(), dist), pol
 
 
+def test_traced_and_untraced_runs_agree():
+    # tracing reads every plan's modes and frontier; the results, iterations and launches stay the same
+    g = gg.rmat(14).with_weights()
+    Gd = G(g, 512)
+    root = int(gg.roots(g, 1)[0])
+    for algo, kw in (("pagerank", dict(max_iters=30, tol=1e-9)), ("bfs", dict(source=root)),
+                     ("sssp", dict(source=root)), ("ppr", dict(source=root, max_iters=50, tol=1e-10))):
+        for pol in ("analytic", "force_sc"):
+            # a warm-up with the same policy: the data rows a run must clear depend on the run before it
+            Gd.run(algo, mode=pol, **kw)
+            a = Gd.run(algo, mode=pol, profile=True, **kw)
+            b = Gd.run(algo, mode=pol, profile=True, trace=True, **kw)
+            assert np.array_equal(a.values.cpu().numpy().view(np.uint32), b.values.cpu().numpy().view(np.uint32))
+            for key in ("iterations", "converged", "edges_scattered", "pc_partition_steps", "sc_partition_steps",
+                        "kernel_launches"):
+                assert a.stats[key] == b.stats[key], (algo, pol, key)
+            assert a.stats["kernel_launches"][0] == a.stats["iterations"] + 1
+
+
 # --- multi-source BFS (gpop_run_msbfs) ------------------------------------------------------------
 
 def _sources(g, n, seed=3):
