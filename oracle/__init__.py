@@ -6,6 +6,7 @@ reference leg may import this package; the CUDA library never calls it and
 shares no code with it.
 
 Tier 1 (plain definitions): ``pagerank``, ``ppr``, ``bfs``, ``msbfs``, ``cc``, ``sssp``.
+Approximation following its algorithm's steps: ``nibble`` (Alg. 4).
 Tier 2 (the serial GPOP engine of Alg. 2 / Alg. 3 / Eq. (mode)): ``gpop``.
 Model helpers (Sec. 3.2): ``mode_decide``, ``mode_bytes``, ``partition_stats``.
 
@@ -54,6 +55,7 @@ def _load():
             u32, u64, dbl = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
             lib.orc_pagerank.argtypes = [u32, vp, vp, dbl, u32, dbl, vp, vp, vp, vp]
             lib.orc_ppr.argtypes = [u32, vp, vp, u32, dbl, u32, dbl, vp, vp, vp]
+            lib.orc_nibble.argtypes = [u32, vp, vp, u32, dbl, u32, vp, vp, vp]
             lib.orc_bfs.argtypes = [u32, vp, vp, u32, vp, vp]
             lib.orc_cc.argtypes = [u32, vp, vp, vp]
             lib.orc_sssp.argtypes = [u32, vp, vp, vp, u32, vp]
@@ -63,7 +65,7 @@ def _load():
             lib.orc_partition_stats.argtypes = [u32, vp, vp, u32, vp, vp]
             lib.orc_gpop.argtypes = [u32, vp, vp, vp, u32, u32, u32, dbl, u32, dbl, u32, u32, u32,
                                      vp, vp, vp, vp, vp, vp, vp, vp, vp]
-            for f in ("orc_pagerank", "orc_ppr", "orc_bfs", "orc_cc", "orc_sssp", "orc_mode_decide",
+            for f in ("orc_pagerank", "orc_ppr", "orc_nibble", "orc_bfs", "orc_cc", "orc_sssp", "orc_mode_decide",
                       "orc_partition_stats", "orc_gpop"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
@@ -106,6 +108,18 @@ def ppr(g, seed: int, alpha: float = 0.15, max_iters: int = 100, tol: float = 0.
                          ctypes.byref(res))
     assert rc == 0
     return x[:n], it.value, res.value
+
+
+def nibble(g, seed: int, eps: float = 1e-9, max_iters: int = 1000):
+    """Parallel Nibble (Alg. 4) in FP64: returns (PR, iterations, frontier sizes entering each iteration).
+    Sinks are never kept on the frontier (the reading of PR >= eps * deg at deg 0)."""
+    n, rp, col = _csr(g)
+    pr = np.zeros(max(n, 1), dtype=np.float64)
+    fr = np.zeros(max(max_iters, 1), dtype=np.uint64)
+    it = ctypes.c_uint32()
+    rc = _load().orc_nibble(n, _ptr(rp), _ptr(col), seed, eps, max_iters, _ptr(pr), ctypes.byref(it), _ptr(fr))
+    assert rc == 0
+    return pr[:n], it.value, fr[: it.value].copy()
 
 
 def bfs(g, root: int):

@@ -15,6 +15,9 @@
  *                             power iteration it performs, sinks not redistributed
  *              orc_ppr        seeded personalised PageRank (restart alpha) in
  *                             the same form, seed re-injected every iteration
+ *              orc_nibble     parallel Nibble (Alg. 4): its user functions run
+ *                             in Alg. 2's order; an approximation (eps
+ *                             truncation), so this follows the algorithm's steps
  *              orc_bfs        queue BFS (Alg. 5 computes a BFS tree); parent =
  *                             minimum-ID in-neighbour one level up
  *              orc_cc         union-find; label = minimum vertex ID of the
@@ -121,6 +124,71 @@ int orc_ppr(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t s, dou
     free(y);
     if (iters_out) *iters_out = t;
     if (res_out) *res_out = res;
+    return 0;
+}
+
+/* Parallel Nibble (Alg. 4) run through the bulk-synchronous flow of Alg. 2,
+ * in FP64.  PR starts as the indicator of the seed s and the frontier is {s}.
+ * Each iteration, in the paper's order:
+ *   scatter  every frontier vertex v sends PR[v] / (2 deg v) along each out-edge
+ *            (scatterFunc; the values are read before initFunc changes them);
+ *   initFunc every frontier vertex keeps half its PR (update1) and stays on
+ *            (cond1) iff PR[v] >= eps * deg v;
+ *   gather   every message adds its value to PR of its destination (gatherFunc),
+ *            which is thereby activated;
+ *   filter   the next frontier is every vertex that stayed on or was activated
+ *            and has PR[v] >= eps * deg v (cond2).
+ * Reading for sinks: the paper's test is PR >= eps * 0, always true, which would
+ * keep a reached sink on forever while it sends nothing; here a sink is never
+ * kept (cond1 and cond2 also require deg v > 0).
+ * Stops when the frontier is empty or after max_iters iterations.  frontier_out
+ * (optional, max_iters entries) receives the frontier size entering each
+ * iteration. */
+int orc_nibble(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t s, double eps,
+               uint32_t max_iters, double *pr, uint32_t *iters_out, uint64_t *frontier_out) {
+    if (s >= n) return -1;
+    double *msg = (double *)calloc(n, sizeof(double));
+    uint8_t *front = (uint8_t *)calloc(n, 1), *nfront = (uint8_t *)calloc(n, 1), *recv = (uint8_t *)calloc(n, 1);
+    if (!msg || !front || !nfront || !recv) { free(msg); free(front); free(nfront); free(recv); return -1; }
+    for (uint32_t v = 0; v < n; ++v) pr[v] = 0.0;
+    pr[s] = 1.0;
+    front[s] = 1;
+    uint64_t nf = 1;
+    uint32_t t = 0;
+    while (nf > 0 && t < max_iters) {
+        if (frontier_out) frontier_out[t] = nf;
+        for (uint32_t v = 0; v < n; ++v) { msg[v] = 0.0; recv[v] = 0; nfront[v] = 0; }
+        /* scatter */
+        for (uint32_t v = 0; v < n; ++v) {
+            if (!front[v]) continue;
+            uint64_t deg = rp[v + 1] - rp[v];
+            for (uint64_t e = rp[v]; e < rp[v + 1]; ++e) {
+                msg[col[e]] += pr[v] / (2.0 * (double)deg);
+                recv[col[e]] = 1;
+            }
+        }
+        /* initFunc on the frontier */
+        for (uint32_t v = 0; v < n; ++v) {
+            if (!front[v]) continue;
+            uint64_t deg = rp[v + 1] - rp[v];
+            pr[v] = pr[v] / 2.0;
+            nfront[v] = deg > 0 && pr[v] >= eps * (double)deg;
+        }
+        /* gather, then filter over the kept and the activated vertices */
+        nf = 0;
+        for (uint32_t v = 0; v < n; ++v) {
+            if (recv[v]) pr[v] += msg[v];
+            if (nfront[v] || recv[v]) {
+                uint64_t deg = rp[v + 1] - rp[v];
+                nfront[v] = deg > 0 && pr[v] >= eps * (double)deg;
+            }
+            nf += nfront[v];
+        }
+        uint8_t *tmp = front; front = nfront; nfront = tmp;
+        ++t;
+    }
+    free(msg); free(front); free(nfront); free(recv);
+    if (iters_out) *iters_out = t;
     return 0;
 }
 

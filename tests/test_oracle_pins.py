@@ -127,6 +127,71 @@ def test_ppr_linear_solve(g):
     assert np.max(np.abs(x - expect)) < 1e-13
 
 
+# --- parallel Nibble (Alg. 4) ------------------------------------------------------------------
+
+def sink_free(n, m, seed):
+    # uniform edges plus the cycle 0 -> 1 -> ... -> 0: every vertex has an out-edge
+    rng = np.random.default_rng(seed)
+    u = np.concatenate([rng.integers(0, n, m), np.arange(n)])
+    v = np.concatenate([rng.integers(0, n, m), (np.arange(n) + 1) % n])
+    keep = u != v
+    return gg.multigraph(n, u[keep].tolist(), v[keep].tolist())
+
+
+@pytest.mark.parametrize("g", [gg.ring(9), gg.complete(6), sink_free(60, 200, 1)], ids=lambda g: g.name)
+def test_nibble_without_threshold_is_the_lazy_walk(g):
+    # eps = 0 and no sinks: every reached vertex stays on, so t iterations apply the lazy walk
+    # W = (I + A^T D^-1) / 2 to the seed's indicator (half the mass stays, half spreads over out-edges)
+    n = g.num_vertices
+    A = np.zeros((n, n))
+    np.add.at(A, (g.src().astype(np.int64), g.col.astype(np.int64)), 1.0)
+    W = 0.5 * (np.eye(n) + (A / A.sum(axis=1, keepdims=True)).T)
+    for t in (1, 2, 7, 25):
+        pr, it, _ = O.nibble(g, 0, 0.0, max_iters=t)
+        assert it == t
+        exp = np.linalg.matrix_power(W, t) @ np.eye(n)[0]
+        assert np.max(np.abs(pr - exp)) < 1e-14
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-6, 1e-4, 1e-3])
+def test_nibble_conserves_mass(eps):
+    # a kept vertex with out-edges keeps half its PR and sends the other half; a vertex off the frontier
+    # keeps all of it: the total stays 1 whatever the threshold truncates
+    g = gg.rmat(10)
+    for s in gg.roots(g, 3):
+        pr, it, fr = O.nibble(g, int(s), eps, max_iters=60)
+        assert abs(pr.sum() - 1.0) < 1e-12
+        assert (pr >= 0).all() and fr[0] == 1
+
+
+def test_nibble_one_step_closed_form():
+    # a threshold no vertex meets: one iteration, the seed keeps 1/2 and each out-neighbour gets
+    # 1 / (2 deg) per edge
+    g = gg.rmat(9)
+    s = int(gg.roots(g, 1)[0])
+    pr, it, fr = O.nibble(g, s, 10.0, max_iters=100)
+    deg = int(g.row_ptr[s + 1] - g.row_ptr[s])
+    exp = np.zeros(g.num_vertices)
+    np.add.at(exp, g.col[g.row_ptr[s]:g.row_ptr[s + 1]].astype(np.int64), 1.0 / (2 * deg))
+    exp[s] += 0.5
+    assert it == 1 and list(fr) == [1]
+    assert np.max(np.abs(pr - exp)) < 1e-15
+
+
+def test_nibble_path_worked_example():
+    # directed path 0 -> 1 -> 2 -> 3 (vertex 3 is a sink), seed 0, eps = 0.2, worked by hand from Alg. 4:
+    #  it 1: {0} sends 0.5 to 1; PR0 = 0.5 kept                           -> PR .5 .5 0 0,        on {0,1}
+    #  it 2: 0 sends .25 to 1, 1 sends .25 to 2; both halve to .25, kept -> PR .25 .5 .25 0,     on {0,1,2}
+    #  it 3: sends .125, .25, .125; 0 and 2 halve below .2 (cond1 fails), 1 kept at .25;
+    #        gather: PR1 = .375, PR2 = .375, PR3 = .125 (a sink: never on) -> on {1,2}
+    #  it 4: 1 and 2 send .1875 each and fall below .2; 2 receives (.375, on), 3 receives
+    #                                                                     -> PR .125 .1875 .375 .3125, on {2}
+    #  it 5: 2 sends .1875 to the sink and falls below .2                -> PR .125 .1875 .1875 .5,   empty
+    pr, it, fr = O.nibble(gg.path(4), 0, 0.2, max_iters=100)
+    assert it == 5 and list(fr) == [1, 2, 3, 2, 1]
+    assert np.array_equal(pr, [0.125, 0.1875, 0.1875, 0.5])
+
+
 # --- BFS (Alg. 5), CC, SSSP (Alg. 7) against scipy ---------------------------------------------
 
 def scipy_csr(g, weighted=False):
