@@ -106,7 +106,10 @@ typedef enum {
     GPOP_BFS = 1,        /* Alg. 5: BFS levels and parents from a root */
     GPOP_CC = 2,         /* Sec. 5: min-label propagation (use a symmetrised graph) */
     GPOP_SSSP = 3,       /* Alg. 7: Bellman-Ford over non-negative integer weights */
-    GPOP_PPR = 4         /* seeded personalised PageRank, restart = 1 - damping */
+    GPOP_PPR = 4,        /* seeded personalised PageRank, restart = 1 - damping */
+    GPOP_NIBBLE = 5      /* Alg. 4: parallel Nibble from the seed `source` with threshold `epsilon`
+                            (a vertex stays on the frontier while PR >= epsilon * outdeg; a sink never
+                            stays on) */
 } gpop_algo;
 
 typedef enum {
@@ -119,7 +122,7 @@ typedef enum {
 
 typedef struct {
     int32_t algo;              /* gpop_algo */
-    uint32_t source;           /* BFS/SSSP root, PPR seed (ignored by PageRank/CC) */
+    uint32_t source;           /* BFS/SSSP root, PPR / Nibble seed (ignored by PageRank/CC) */
     double damping;            /* PageRank d (default 0.85); PPR continuation 1 - restart */
     uint32_t max_iters;        /* iteration cap (default 1000) */
     double tol_l1;             /* PageRank/PPR: stop once sum_v |x_{t+1}-x_t| < tol_l1; 0 = run max_iters */
@@ -136,6 +139,7 @@ typedef struct {
     float *log_buffer;         /* optional HOST buffer for GPOP_MODE_LOG_BOTH timing records,
                                   log_capacity records of GPOP_LOG_RECORD_FLOATS floats */
     uint64_t log_capacity;
+    double epsilon;            /* Nibble threshold (default 1e-9, Sec. 5's setting); >= 0, finite */
 } gpop_run_opts;
 
 /* Floats per LOG_BOTH record: 8 selector features, t_PC (us), t_SC (us),
@@ -169,7 +173,7 @@ void gpop_run_opts_default(gpop_run_opts *opts);
  * Runs one application on the graph (Alg. 2 iterations until the frontier is
  * empty, max_iters is reached, or for PageRank/PPR the L1 change drops below
  * tol_l1).
- *   out_values  V elements: float PageRank / PPR values; uint32 BFS level,
+ *   out_values  V elements: float PageRank / PPR / Nibble values; uint32 BFS level,
  *               SSSP distance or CC label (0xFFFFFFFF = unreached)
  *   out_parent  BFS only: V uint32 parents (root's parent is the root,
  *               0xFFFFFFFF = unreached), or NULL

@@ -128,9 +128,10 @@ class Graph:
     def run(self, algo: str, source: int = 0, damping: float = 0.85, max_iters: int = 1000, tol: float = 0.0,
             mode: str = "analytic", bw_ratio=(2, 1), device_out: bool = True, trace: bool = False,
             log_capacity: int = 0, stream=None, out=None, out_parent=None, profile: bool = False,
-            msg_bf16: bool = False) -> RunResult:
+            msg_bf16: bool = False, epsilon: float = 1e-9) -> RunResult:
         """Runs one application; outputs are torch tensors on cuda (device_out) or host numpy arrays.
-        msg_bf16: PageRank / PPR messages travel through the bins as BF16 (gathered in FP32)."""
+        msg_bf16: PageRank / PPR messages travel through the bins as BF16 (gathered in FP32).
+        epsilon: Nibble's threshold (a vertex stays on while PR >= epsilon * out-degree)."""
         torch = _torch()
         lib = _lib.load()
         info = self.info()
@@ -147,6 +148,7 @@ class Graph:
         o.cuda_stream = _stream_handle(stream)
         o.profile_kernels = int(profile)
         o.msg_bf16 = int(msg_bf16)
+        o.epsilon = epsilon
         modes = frontier = log = None
         if trace:
             modes = np.zeros(max(max_iters, 1) * k, dtype=np.uint8)
@@ -157,7 +159,7 @@ class Graph:
             log = np.zeros(log_capacity * LOG_RECORD_FLOATS, dtype=np.float32)
             o.log_buffer = ctypes.c_void_p(log.ctypes.data)
             o.log_capacity = log_capacity
-        fdt = algo in ("pagerank", "ppr")
+        fdt = algo in ("pagerank", "ppr", "nibble")
         if device_out:
             if out is None:
                 out = torch.empty(n, dtype=torch.float32 if fdt else torch.uint32, device="cuda")

@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "GPOP_OK", 1: "GPOP_ERR_INVALID_ARG", 2: "GPOP_ERR_OOM", 3: "
                 4: "GPOP_ERR_DEVICE_CHECK", 5: "GPOP_ERR_TIMEOUT", 6: "GPOP_ERR_NOT_CONVERGED",
                 7: "GPOP_ERR_NO_SELECTOR"}
 
-ALGOS = {"pagerank": 0, "bfs": 1, "cc": 2, "sssp": 3, "ppr": 4}
+ALGOS = {"pagerank": 0, "bfs": 1, "cc": 2, "sssp": 3, "ppr": 4, "nibble": 5}
 MODES = {"analytic": 0, "learned": 1, "force_sc": 2, "force_pc": 3, "log_both": 4}
 
 SELECTOR_FEATURES = 8
@@ -42,7 +42,7 @@ class RunOpts(ctypes.Structure):
                 ("bw_ratio_num", ctypes.c_uint32), ("bw_ratio_den", ctypes.c_uint32), ("msg_bf16", ctypes.c_int32),
                 ("profile_kernels", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p), ("trace_modes", ctypes.c_void_p),
                 ("trace_frontier", ctypes.c_void_p), ("log_buffer", ctypes.c_void_p),
-                ("log_capacity", ctypes.c_uint64)]
+                ("log_capacity", ctypes.c_uint64), ("epsilon", ctypes.c_double)]
 
 
 class RunStats(ctypes.Structure):

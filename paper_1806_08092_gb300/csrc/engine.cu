@@ -33,8 +33,10 @@ namespace gpop {
 // that reached it and its message the complement of the sources it reached in the last iteration
 enum Algo : int {
     ALG_PR = GPOP_PAGERANK, ALG_BFS = GPOP_BFS, ALG_CC = GPOP_CC, ALG_SSSP = GPOP_SSSP, ALG_PPR = GPOP_PPR,
-    ALG_MSBFS = 5
+    ALG_NIBBLE = GPOP_NIBBLE, ALG_MSBFS = 6
 };
+// applications whose messages are FP32 values combined by addition
+__host__ __device__ constexpr bool sums(int a) { return a == ALG_PR || a == ALG_PPR || a == ALG_NIBBLE; }
 
 constexpr int kGatherThreads = 256;
 constexpr int kGatherWarps = kGatherThreads / 32;
@@ -126,6 +128,7 @@ struct Params {
     uint32_t nsrc;
     uint32_t *lvl_ms;       // multi-source BFS: levels, row j (V words) for source msrc[j]
     float c0, c1;           // PR: (1-d)/V, d.  PPR: alpha, 1-alpha
+    float eps;              // Nibble: the threshold per unit of out-degree
     double tol;
     int algo, policy;
     uint32_t bw_num, bw_den;
@@ -151,10 +154,10 @@ struct Op {
     // source sets, so the AND is the complement of their union).  Except for the sums the identity is
     // 0xFFFFFFFF, the NULL of an inactive source, which therefore folds as a no-op.
     static __device__ __forceinline__ uint32_t identity() {
-        return (ALGO == ALG_PR || ALGO == ALG_PPR) ? 0u : kInf;
+        return sums(ALGO) ? 0u : kInf;
     }
     static __device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b) {
-        if (ALGO == ALG_PR || ALGO == ALG_PPR) return f2u(u2f(a) + u2f(b));
+        if (sums(ALGO)) return f2u(u2f(a) + u2f(b));
         if (ALGO == ALG_MSBFS) return a & b;
         return a < b ? a : b;
     }
@@ -347,6 +350,10 @@ __global__ void k_init(Params p) {
                 act = (g == p.source);
                 v = f2u(act ? 1.f : 0.f);
                 sv = act ? f2u(deg ? 1.f / (float)deg : 0.f) : kNull;
+            } else if (ALGO == ALG_NIBBLE) {  // Alg. 4: PR = indicator of the seed, frontier = {seed}
+                act = (g == p.source);
+                v = f2u(act ? 1.f : 0.f);
+                sv = act ? f2u(deg ? 1.f / (2.f * (float)deg) : 0.f) : kNull;
             } else if (ALGO == ALG_BFS) {
                 act = (g == p.source);
                 v = act ? g : kInf;
@@ -889,7 +896,7 @@ __device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt
     // quads of a 16-entry group are stored swizzled by (group >> 1) & 3 (see the build); the lane's
     // entries start at round position j0, in group j0 / 16
     const uint32_t gbase = j0 & ~15u, qsw = ((j0 >> 5) & 3u), q0 = (j0 & 15u) >> 2;
-    const bool nullable = ALGO == ALG_SSSP || ALGO == ALG_PPR || (ALGO == ALG_PR && check_null);
+    const bool nullable = ALGO == ALG_SSSP || ALGO == ALG_PPR || ALGO == ALG_NIBBLE || (ALGO == ALG_PR && check_null);
 #pragma unroll
     for (uint32_t hb = 0; hb < K; hb += HB) {
         uint32_t ee[HB];
@@ -1232,7 +1239,7 @@ __global__ void __launch_bounds__(256) k_merge_pc(Params p) {
 // FP64 keeps their sum within rounding of the exact one, and the filter rounds it to FP32 once).
 template <int ALGO>
 struct ScAcc {
-    static constexpr bool kSum = ALGO == ALG_PR || ALGO == ALG_PPR;
+    static constexpr bool kSum = sums(ALGO);
     using T = typename std::conditional<kSum, double, uint32_t>::type;
     static __device__ __forceinline__ T from_msg(uint32_t m) {
         if constexpr (kSum) return (double)u2f(m);
@@ -1431,6 +1438,24 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                         nv[c] = f2u(xn);
                         res4 += fabsf(xn - xo);
                         if (act) ns[c] = f2u(deg ? xn / (float)deg : 0.f);
+                    } else if (ALGO == ALG_NIBBLE) {
+                        // Alg. 4: initFunc halves PR of a frontier vertex (update1) and keeps it on iff
+                        // PR >= eps deg (cond1); gatherFunc adds the messages and activates the vertex;
+                        // filterFunc keeps it iff PR >= eps deg (cond2).  A sink never stays on.
+                        const float xo = u2f(vals[c]);
+                        const float thr = p.eps * (float)deg;
+                        float x = xo;
+                        bool keep = false;
+                        if (was) {
+                            x = 0.5f * x;
+                            keep = deg > 0 && x >= thr;
+                        }
+                        const bool recv = m != 0u;
+                        if (recv) x = x + u2f(m);
+                        act = (keep || recv) && deg > 0 && x >= thr;
+                        nv[c] = f2u(x);
+                        res4 += fabsf(x - xo);
+                        if (act) ns[c] = f2u(x / (2.f * (float)deg));
                     } else if (ALGO == ALG_MSBFS) {
                         // Alg. 5 for every source of the pass at once: the sources that reach the vertex
                         // (complement of the AND of complemented sets) minus those that already had it
@@ -1464,7 +1489,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                         ea += deg;
                     }
                 }
-                if (ALGO == ALG_PR || ALGO == ALG_PPR) res += (double)res4;
+                if (sums(ALGO)) res += (double)res4;
                 if (full) {
                     if (nv[0] != vals[0] || nv[1] != vals[1] || nv[2] != vals[2] || nv[3] != vals[3])
                         *reinterpret_cast<uint4 *>(p.val + g0) = make_uint4(nv[0], nv[1], nv[2], nv[3]);
@@ -1757,6 +1782,8 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     } else if (ALGO == ALG_PPR) {
         p.c0 = (float)(1.0 - o->damping);
         p.c1 = (float)o->damping;
+    } else if (ALGO == ALG_NIBBLE) {
+        p.eps = (float)o->epsilon;
     }
 
     int grid_pc = 0, grid_sc = 0, grid_ga = 0;
@@ -1972,6 +1999,7 @@ extern "C" void gpop_run_opts_default(gpop_run_opts *o) {
     o->mode = GPOP_MODE_ANALYTIC;
     o->bw_ratio_num = 2;
     o->bw_ratio_den = 1;
+    o->epsilon = 1e-9;
 }
 
 // PC data rows in the run's message format and all-NULL where not written, and the run buffers
@@ -2009,16 +2037,19 @@ extern "C" gpop_status gpop_run(gpop_graph *h, const gpop_run_opts *o, void *out
     set_error("");
     if (!h || !o) return fail(GPOP_ERR_INVALID_ARG, "NULL graph or options");
     Graph *g = &h->g;
-    if (o->algo < GPOP_PAGERANK || o->algo > GPOP_PPR) return fail(GPOP_ERR_INVALID_ARG, "unknown algorithm");
-    if ((o->algo == GPOP_BFS || o->algo == GPOP_SSSP || o->algo == GPOP_PPR) && o->source >= g->V)
+    if (o->algo < GPOP_PAGERANK || o->algo > GPOP_NIBBLE) return fail(GPOP_ERR_INVALID_ARG, "unknown algorithm");
+    if ((o->algo == GPOP_BFS || o->algo == GPOP_SSSP || o->algo == GPOP_PPR || o->algo == GPOP_NIBBLE) &&
+        o->source >= g->V)
         return fail(GPOP_ERR_INVALID_ARG, "source out of range");
     if (o->algo == GPOP_SSSP && !g->weighted) return fail(GPOP_ERR_INVALID_ARG, "SSSP needs a weighted graph");
     gpop_status cs = check_common_opts(o);
     if (cs != GPOP_OK) return cs;
     if (o->msg_bf16 && o->algo != GPOP_PAGERANK && o->algo != GPOP_PPR)
-        return fail(GPOP_ERR_INVALID_ARG, "BF16 messages are for PageRank and PPR (the other algorithms stay exact)");
+        return fail(GPOP_ERR_INVALID_ARG, "BF16 messages are for PageRank and PPR (the other algorithms keep FP32 / exact messages)");
     if ((o->algo == GPOP_PAGERANK || o->algo == GPOP_PPR) && !(o->damping > 0.0 && o->damping < 1.0))
         return fail(GPOP_ERR_INVALID_ARG, "damping must be in (0, 1)");
+    if (o->algo == GPOP_NIBBLE && !(o->epsilon >= 0.0 && std::isfinite(o->epsilon)))
+        return fail(GPOP_ERR_INVALID_ARG, "Nibble threshold must be finite and >= 0");
     cudaStream_t s = (cudaStream_t)o->cuda_stream;
     const int fmt = o->msg_bf16 ? 1 : 0;
     RunBuffers *rb = nullptr;
@@ -2031,6 +2062,7 @@ extern "C" gpop_status gpop_run(gpop_graph *h, const gpop_run_opts *o, void *out
     case GPOP_BFS: return run_algo<ALG_BFS, false>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
     case GPOP_CC: return run_algo<ALG_CC, false>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
     case GPOP_SSSP: return run_algo<ALG_SSSP, false>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
+    case GPOP_NIBBLE: return run_algo<ALG_NIBBLE, false>(g, rb, o, s, out_values, out_parent, out_is_device, stats);
     default:
         return fmt ? run_algo<ALG_PPR, true>(g, rb, o, s, out_values, out_parent, out_is_device, stats)
                    : run_algo<ALG_PPR, false>(g, rb, o, s, out_values, out_parent, out_is_device, stats);

@@ -48,8 +48,9 @@ def test_struct_layouts_match_the_header(tmp_path):
 #include <stddef.h>
 #include "gpop.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(gpop_graph_info), sizeof(gpop_run_opts), sizeof(gpop_run_stats),
-         offsetof(gpop_run_opts, cuda_stream), offsetof(gpop_run_opts, log_capacity));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(gpop_graph_info), sizeof(gpop_run_opts), sizeof(gpop_run_stats),
+         offsetof(gpop_run_opts, cuda_stream), offsetof(gpop_run_opts, log_capacity),
+         offsetof(gpop_run_opts, epsilon));
   printf("%d %d %d\n", GPOP_SELECTOR_WEIGHTS, GPOP_SELECTOR_PARAMS, GPOP_LOG_RECORD_FLOATS);
   return 0; }
 ''')
@@ -58,7 +59,7 @@ int main(void) {
     lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     a = [int(x) for x in lines[0].split()]
     assert a == [ctypes.sizeof(_lib.GraphInfo), ctypes.sizeof(_lib.RunOpts), ctypes.sizeof(_lib.RunStats),
-                 _lib.RunOpts.cuda_stream.offset, _lib.RunOpts.log_capacity.offset]
+                 _lib.RunOpts.cuda_stream.offset, _lib.RunOpts.log_capacity.offset, _lib.RunOpts.epsilon.offset]
     b = [int(x) for x in lines[1].split()]
     assert b == [_lib.SELECTOR_WEIGHTS, _lib.SELECTOR_PARAMS, _lib.LOG_RECORD_FLOATS]
 
@@ -67,6 +68,7 @@ def test_opts_default_is_host_only(lib):
     o = _lib.RunOpts()
     lib.gpop_run_opts_default(ctypes.byref(o))
     assert (o.algo, o.damping, o.max_iters, o.mode, o.bw_ratio_num, o.bw_ratio_den) == (0, 0.85, 1000, 0, 2, 1)
+    assert o.epsilon == 1e-9
     assert lib.gpop_last_error() is not None
 
 

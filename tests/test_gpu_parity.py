@@ -179,6 +179,66 @@ def test_traced_and_untraced_runs_agree():
             assert a.stats["kernel_launches"][0] == a.stats["iterations"] + 1
 
 
+# --- parallel Nibble (Alg. 4) ---------------------------------------------------------------------
+# FP32 on the GPU against the FP64 oracle: PR values are probabilities (they sum to 1), compared in
+# absolute terms.  The threshold PR >= eps deg is decided on FP32 values on the GPU and on FP64 values
+# in the oracle, so a vertex whose PR lies within rounding of eps deg may fall on either side: frontier
+# sizes agree to max(2, 2 %) per iteration and the run lengths to 2 iterations (exactly in the worked
+# example).  Thresholds near 1 / volume keep the frontier at the threshold for many iterations, where
+# such flips accumulate; the cases here end on their own.
+NIBBLE_ABS_TOL = 1e-6
+
+
+def nibble_close(r, ref, it, fr):
+    n = min(r.stats["iterations"], it)
+    assert abs(r.stats["iterations"] - it) <= 2
+    d = np.abs(r.frontier[:n, 0].astype(np.int64) - fr[:n].astype(np.int64))
+    assert (d <= np.maximum(2, fr[:n] // 50)).all(), d
+    assert np.max(np.abs(r.values.cpu().numpy().astype(np.float64) - ref)) <= NIBBLE_ABS_TOL
+
+
+@pytest.mark.parametrize("name,g", SMALL, ids=[s[0] for s in SMALL])
+@pytest.mark.parametrize("P", [32, 1024])
+def test_nibble_small(name, g, P):
+    Gd = G(g, P)
+    for seed in gg.roots(g, 2):
+        seed = int(seed)
+        for eps in (1e-3, max(1e-4, 10.0 / max(g.num_edges, 1))):
+            ref, it, fr = O.nibble(g, seed, eps, max_iters=200)
+            for pol in POLICIES:
+                r = Gd.run("nibble", source=seed, epsilon=eps, max_iters=200, mode=pol, trace=True)
+                nibble_close(r, ref, it, fr)
+
+
+def test_nibble_worked_example_and_edge_cases():
+    import paper_1806_08092_gb300 as gp
+    # the path example of the oracle pins: dyadic values, exact in FP32
+    r = G(gg.path(4), 32).run("nibble", source=0, epsilon=0.2, trace=True)
+    assert r.stats["iterations"] == 5 and list(r.frontier[:, 0]) == [1, 2, 3, 2, 1]
+    assert np.array_equal(r.values.cpu().numpy(), np.array([0.125, 0.1875, 0.1875, 0.5], dtype=np.float32))
+    # a sink seed (the path's last vertex) scatters nothing and keeps half its mass
+    r = G(gg.path(4), 32).run("nibble", source=3, epsilon=1e-9)
+    x = r.values.cpu().numpy()
+    assert r.stats["iterations"] == 1 and x[3] == 0.5 and x.sum() == 0.5
+    st = gg.star(20)
+    with pytest.raises(gp.GpopError):
+        G(st, 32).run("nibble", source=0, epsilon=-1.0)
+    with pytest.raises(gp.GpopError):
+        G(st, 32).run("nibble", source=0, epsilon=float("nan"))
+    with pytest.raises(gp.GpopError):
+        G(st, 32).run("nibble", source=0, msg_bf16=True)
+
+
+def test_nibble_large_partitions():
+    g, P = gg.rmat(18), 16384
+    Gd = G(g, P)
+    seed = int(gg.roots(g, 1)[0])
+    ref, it, fr = O.nibble(g, seed, 1e-7, max_iters=40)
+    for pol in POLICIES:
+        r = Gd.run("nibble", source=seed, epsilon=1e-7, max_iters=40, mode=pol, trace=True)
+        nibble_close(r, ref, it, fr)
+
+
 # --- multi-source BFS (gpop_run_msbfs) ------------------------------------------------------------
 
 def _sources(g, n, seed=3):
