@@ -38,7 +38,9 @@ void free_graph(Graph *g) {
 
 namespace {
 
-// RAII list of temporary device buffers released at scope exit.
+// RAII list of temporary device buffers released at scope exit, or earlier by release() once a step no
+// longer needs one (cudaFree waits for the work queued on the device, so no launch still reads it); the
+// build's peak footprint is then a few steps' buffers instead of all of them.
 struct Temps {
     std::vector<void *> ptrs;
     template <typename T>
@@ -47,6 +49,14 @@ struct Temps {
         cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
         if (e == cudaSuccess) ptrs.push_back(*p);
         return e;
+    }
+    void release(void *p) {
+        for (size_t i = 0; i < ptrs.size(); ++i)
+            if (ptrs[i] == p) {
+                cudaFree(p);
+                ptrs.erase(ptrs.begin() + (long)i);
+                return;
+            }
     }
     ~Temps() {
         for (void *p : ptrs) cudaFree(p);
@@ -242,6 +252,12 @@ __global__ void k_sub_split(uint64_t nsub, const uint64_t *ukey, uint32_t *sub_t
     }
 }
 
+// in-degree of every 32-vertex block of destinations (where the gather tasks are cut)
+__global__ void k_block_indeg(uint64_t E, const uint32_t *col, uint32_t *cnt) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E; e += stride) atomicAdd(&cnt[col[e] >> 5], 1u);
+}
+
 // index of every edge's SC bin within its bin row (binary search of its task in the row)
 __global__ void k_edge_sub(uint64_t E, uint32_t shift, const uint32_t *src, const uint32_t *col,
                            const uint32_t *task_of, const uint32_t *row_sub, const uint32_t *sub_task, uint16_t *esub) {
@@ -340,7 +356,9 @@ cudaError_t cub_run(Temps &t, F f) {
     void *tmp = nullptr;
     e = t.alloc((char **)&tmp, bytes);
     if (e != cudaSuccess) return e;
-    return f(tmp, bytes);
+    e = f(tmp, bytes);
+    t.release(tmp);
+    return e;
 }
 
 int bits_for(uint64_t x) {  // number of bits to represent values < x
@@ -421,12 +439,14 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
             }));
         }
         k_unpack_dst<<<blocks_for(E), kThreads, 0, s>>>(E, k1, g->col);
+        t.release(k0);
+        t.release(k1);
     }
 
     // 3. messages: one per (source, destination partition), sorted by (p, q, source)
     uint8_t *head;
-    uint64_t *mkey, *skey;
-    uint32_t *head_idx, *shead, *d_nmsg;
+    uint64_t *mkey, *skey = nullptr;
+    uint32_t *head_idx, *shead = nullptr, *d_nmsg;
     GPOP_CUDA_TRY(t.alloc(&head, E));
     GPOP_CUDA_TRY(t.alloc(&mkey, E));
     GPOP_CUDA_TRY(t.alloc(&head_idx, E));
@@ -445,6 +465,7 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
             return cub::DeviceSelect::Flagged(tmp, bytes, head_idx, head, hidx, d_nmsg, (int64_t)E, s);
         }));
+        t.release(mkey);
         uint32_t h_nmsg = 0;
         GPOP_CUDA_TRY(cudaMemcpyAsync(&h_nmsg, d_nmsg, 4, cudaMemcpyDeviceToHost, s));
         GPOP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -455,7 +476,10 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
             return cub::DeviceRadixSort::SortPairs(tmp, bytes, hkey, skey, hidx, shead, nmsg, 0, end_bit, s);
         }));
+        t.release(hkey);
+        t.release(hidx);
     }
+    t.release(head);
     g->npng = nmsg;
 
     // 4. bins, rows, padded PNG slots
@@ -477,6 +501,7 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
             return cub::DeviceScan::InclusiveSum(tmp, bytes, newbin, binscan, nmsg, s);
         }));
     }
+    t.release(newbin);
     // messages are sorted by (row p, column q, source): row p = (key >> shift) / k
     k_seg_starts<<<blocks_for(nmsg + 1), kThreads, 0, s>>>(nmsg, skey, shift, k, k, row_start);
     k_row_counts<<<blocks_for(k), kThreads, 0, s>>>(k, row_start, binscan, msgs_row, g->nbins_p);
@@ -531,6 +556,9 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         k_place_msgs<<<blocks_for(nmsg), kThreads, 0, s>>>(nmsg, shift, skey, shead, binscan, bin_j0, bin_p, binoff,
                                                            g->row_bin, g->row_png, g->png, slot_of_head, bin_of_head,
                                                            bin_slot0);
+    t.release(skey);
+    t.release(shead);
+    t.release(binscan);
 
     // 5. message head of every edge (its first edge to the same destination partition)
     uint32_t *head_of;
@@ -540,6 +568,7 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
             return cub::DeviceScan::InclusiveScan(tmp, bytes, head_idx, head_of, MaxOp(), E, s);
         }));
     }
+    t.release(head_idx);
 
     // 7. bins per column in ascending source partition
     GPOP_CUDA_TRY(dalloc(g, &g->col_bins, g->nb));
@@ -648,6 +677,9 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
             GPOP_CUDA_TRY(t.alloc(&pk2, E));
             k_pc_keys<<<blocks_for(E), kThreads, 0, s>>>(E, shift, P, head_of, slot_of_head, bin_of_head, g->col,
                                                          bin_slot0, d_cseq0, d_colblk0, pk);
+            t.release(head_of);
+            t.release(slot_of_head);
+            t.release(bin_of_head);
             int end_bit = 32 + bits_for((uint64_t)nblocks + 1);
             if (g->weighted) {
                 GPOP_CUDA_TRY(cub_run(t, [&](void *tmp, size_t &bytes) {
@@ -660,6 +692,8 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
             }
             k_pc_unpack<<<blocks_for(E), kThreads, 0, s>>>(E, pk2, g->pe);
             k_seg_starts<<<blocks_for(E + 1), kThreads, 0, s>>>(E, pk2, 32, 1, nblocks, g->pc_blk_ent);
+            t.release(pk);
+            t.release(pk2);
         } else {
             GPOP_CUDA_TRY(cudaMemsetAsync(g->pc_blk_ent, 0, 4ull * (nblocks + 1), s));
         }
@@ -834,8 +868,18 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
     GPOP_CUDA_TRY(cudaMemcpyAsync(hnb.data(), g->nbins_p, 4ull * k, cudaMemcpyDeviceToHost, s));
     GPOP_CUDA_TRY(cudaMemcpyAsync(hrow_png.data(), g->row_png, 4ull * (k + 1), cudaMemcpyDeviceToHost, s));
 
-    // 9. static gather tasks: destination ranges of at most kGatherWidth vertices of one column
+    // 9. static gather tasks: ranges of whole 32-vertex blocks of one column, at most kGatherWidth
+    //    destinations and (unless one block alone has more) at most `tgt` in-edges, so that the SC pairs
+    //    of a hub column, which one task folds alone, are spread over several
     uint32_t nblk = (V + 31) / 32;
+    std::vector<uint32_t> hin(nblk);
+    {
+        uint32_t *d_in;
+        GPOP_CUDA_TRY(t.alloc(&d_in, nblk));
+        GPOP_CUDA_TRY(cudaMemsetAsync(d_in, 0, 4ull * nblk, s));
+        if (E) k_block_indeg<<<blocks_for(E), kThreads, 0, s>>>(E, g->col, d_in);
+        GPOP_CUDA_TRY(cudaMemcpyAsync(hin.data(), d_in, 4ull * nblk, cudaMemcpyDeviceToHost, s));
+    }
     GPOP_CUDA_TRY(cudaStreamSynchronize(s));
     g->h_Ep = new uint64_t[k];
     g->h_npng = new uint64_t[k];
@@ -851,14 +895,17 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
     std::vector<GatherTask> gt;
     std::vector<uint32_t> col_task(k + 1);
     const uint32_t width_blocks = std::min(P, kGatherWidth) / 32;
+    const uint64_t tgt = std::max<uint64_t>(kGatherTaskMinEdges, E / (4ull * (uint64_t)std::max(1, g->num_sms)));
     for (uint32_t q = 0; q < k; ++q) {
         col_task[q] = (uint32_t)gt.size();
         uint32_t b0 = (uint32_t)(((uint64_t)q << shift) / 32);
         uint32_t b1 = (uint32_t)std::min<uint64_t>((((uint64_t)q + 1) << shift) / 32, nblk);
         uint32_t base = b0;
         while (b0 < b1) {
-            uint32_t b = std::min(b0 + width_blocks, b1);
-            gt.push_back(GatherTask{q, (b0 - base) * 32, (b - base) * 32, 0});
+            uint32_t b = b0;
+            uint64_t in = 0;
+            while (b < b1 && b - b0 < width_blocks && (b == b0 || in + hin[b] <= tgt)) in += hin[b++];
+            gt.push_back(GatherTask{q, (b0 - base) * 32, (b - base) * 32, (uint32_t)std::min<uint64_t>(in, 0xFFFFFFFFu)});
             b0 = b;
         }
     }

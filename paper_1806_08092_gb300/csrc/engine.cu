@@ -1234,27 +1234,32 @@ __global__ void __launch_bounds__(256) k_merge_pc(Params p) {
     }
 }
 
-// Task accumulator of the SC pass: a 32-bit word per destination for the min monoids, an FP64 sum per
-// destination for PR / PPR (a hub destination can receive very many pairs, folded in arbitrary order:
-// FP64 keeps their sum within rounding of the exact one, and the filter rounds it to FP32 once).
+// Task accumulator of the SC pass: a 32-bit word per destination for the min / AND monoids, and for the
+// sums (PR, PPR, Nibble, whose values are probability masses: every sum lies in [0, 1]) an unsigned
+// 64-bit fixed-point number with 62 fraction bits.  A message converts exactly when it is at least 2^-39
+// (within 2^-63 below that), the integer additions are exact and independent of the order in which the
+// pairs arrive (a hub destination can receive very many), and the filter rounds the total to FP32 once.
+// 64-bit integer atomics are native on shared memory; FP64 ones are not, and FP64 is scarce on this GPU.
+constexpr float kFixOne = 0x1p62f;    // 2^62
+constexpr float kFixUnit = 0x1p-62f;  // 2^-62
 template <int ALGO>
 struct ScAcc {
     static constexpr bool kSum = sums(ALGO);
-    using T = typename std::conditional<kSum, double, uint32_t>::type;
+    using T = typename std::conditional<kSum, unsigned long long, uint32_t>::type;
     static __device__ __forceinline__ T from_msg(uint32_t m) {
-        if constexpr (kSum) return (double)u2f(m);
+        if constexpr (kSum) return __float2ull_rn(u2f(m) * kFixOne);
         else return m;
     }
     static __device__ __forceinline__ uint32_t to_msg(T a) {
-        if constexpr (kSum) return f2u((float)a);
+        if constexpr (kSum) return f2u(__ull2float_rn(a) * kFixUnit);
         else return a;
     }
-    // folds one SC pair's value: atomic minimum (BFS parents, CC labels, SSSP distances) or AND
-    // (multi-source BFS), whose results do not depend on the order, or FP64 atomic addition
-    static __device__ __forceinline__ void fold(T *slot, uint32_t v) {
-        if constexpr (kSum) atomicAdd(slot, (double)u2f(v));
-        else if constexpr (ALGO == ALG_MSBFS) atomicAnd(slot, v);
-        else atomicMin(slot, v);
+    // folds one SC pair's value v into acc[d]: atomic minimum (BFS parents, CC labels, SSSP distances), AND
+    // (multi-source BFS) or fixed-point addition, none of whose results depends on the order of the pairs
+    static __device__ __forceinline__ void fold(T *acc, uint32_t d, uint32_t v) {
+        if constexpr (kSum) atomicAdd(&acc[d], from_msg(v));
+        else if constexpr (ALGO == ALG_MSBFS) atomicAnd(&acc[d], v);
+        else atomicMin(&acc[d], v);
     }
 };
 
@@ -1340,7 +1345,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                 }
                 for (uint32_t j = lane; j < cnt; j += 32) {
                     const uint2 pr = sc_pair<B16>(p, sb + j);
-                    A::fold(&s_acc[pr.x - gt.d0], pr.y);
+                    A::fold(s_acc, pr.x - gt.d0, pr.y);
                 }
             }
             __syncthreads();
@@ -1350,7 +1355,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                 const uint32_t cnt = p.sccnt[bn], sb = p.sub_cap[bn];
                 for (uint32_t j = tid; j < cnt; j += nthr) {
                     const uint2 pr = sc_pair<B16>(p, sb + j);
-                    A::fold(&s_acc[pr.x - gt.d0], pr.y);
+                    A::fold(s_acc, pr.x - gt.d0, pr.y);
                 }
             }
             __syncthreads();

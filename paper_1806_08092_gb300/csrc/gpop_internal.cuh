@@ -22,6 +22,7 @@ constexpr uint32_t kMsBfsWidth = 32;  // sources per multi-source BFS pass (bits
 constexpr int kPngAlign = 8;           // PNG rows padded to 8 entries (16-byte u16 vectors)
 constexpr uint32_t kBinAlign = 8;      // every bin padded to 8 slots: 16-byte aligned bulk copies of bin runs (BF16)
 constexpr uint32_t kGatherWidth = 4096;  // max destinations per gather task (smem accumulator)
+constexpr uint64_t kGatherTaskMinEdges = 65536;  // in-edges a gather task may take before it is cut
 constexpr uint32_t kGatherEntries = 32768;  // target in-entries per gather task
 constexpr uint32_t kScatterChunk = 131072;  // PNG slots per PC scatter task (one staging of the partition's values)
 constexpr uint32_t kMaxRowBins = 40960;     // SC scatter keeps one cursor per row bin in smem
@@ -50,7 +51,7 @@ struct Control {
     uint32_t pad;
 };
 
-// Static gather task: destinations [d0, d1) (local IDs) of column q.
+// Static gather task: destinations [d0, d1) (local IDs) of column q, which have `entries` in-edges.
 struct GatherTask {
     uint32_t q, d0, d1, entries;
 };

@@ -1,6 +1,6 @@
 """Measurements of the synthetic configurations on one GPU, one JSON line per result.
 
-    python -m paper_1806_08092_gb300.report [--configs c1,c2,c3,c4,ablation]
+    python -m paper_1806_08092_gb300.report [--configs c1,c2,c3,c4,nibble,ablation,degree]
 
 c1        PageRank, 10 iterations, d = 0.85, RMAT-16 (P = 1024): time and GTEPS = 10 E / t.  The graph
           and its bins fit in L2, so no HBM fraction is meaningful for it.
@@ -13,6 +13,12 @@ c3        PageRank to an L1 residual below 1e-9 on RMAT-24 and on a uniform rand
           and per-kernel times (the errors against the FP64 oracle come from the GPU tests).
 c4        RMAT-22 BFS from 64 sources: gpop_run_msbfs (two 32-source passes) against 64 single-source
           gpop_run calls, TEPS = sum over sources of traversed edges / t, and the batching speedup.
+nibble    parallel Nibble (Alg. 4) on RMAT-24 from 16 seeds with Sec. 5's threshold eps = 1e-9, at most
+          100 iterations: time, iterations, vertices with PR > 0 and edges scattered per seed.
+degree    time against average degree (Sec. 5, execution time vs degree): RMAT-26 (64 M vertices) from
+          edge factor 1 to 32 (the paper goes to 128; 32 keeps the largest layout near 70 GB), PageRank
+          10 iterations, BFS, SSSP and Nibble (eps = 1e-9, at most 100 iterations) from one root, and CC
+          on the symmetrised graph up to edge factor 16; with the PC / SC partition-steps of each run.
 ablation  RMAT-24 BFS and SSSP and symmetrised RMAT-24 CC with every partition forced to SC, forced to
           PC, and with Eq. (mode): time, iterations and the number of PC / SC partition-steps.
 
@@ -155,6 +161,62 @@ def c4(nsrc=64):
     G.close()
 
 
+def nibble(nseeds=16, eps=1e-9, max_iters=100):
+    gg = _gen()
+    g = gg.rmat(24)
+    G = Graph.from_csr(g.row_ptr, g.col, None, partition_size=16384)
+    for s in gg.roots(g, nseeds):
+        s = int(s)
+        r = _median_run(G, "nibble", reps=3, source=s, epsilon=eps, max_iters=max_iters)
+        _emit({"config": "nibble", "graph": "rmat24", "vertices": g.num_vertices, "edges": g.num_edges,
+               "partition_size": 16384, "seed": s, "epsilon": eps, "max_iters": max_iters,
+               "iterations": r.stats["iterations"], "converged": r.stats["converged"],
+               "ms": r.stats["device_ms"], "support": int((r.values > 0).sum().item()),
+               "edges_scattered": r.stats["edges_scattered"], "pc_partition_steps": r.stats["pc_partition_steps"],
+               "sc_partition_steps": r.stats["sc_partition_steps"], "kernels_ms": _kernels(r.stats)})
+    G.close()
+
+
+def degree(scale=26, efs=(1, 2, 4, 8, 16, 32), cc_max_ef=16):
+    from . import GpopError
+    gg = _gen()
+    for ef in efs:
+        g = gg.rmat(scale, ef).with_weights()
+        root = int(gg.roots(g, 1)[0])
+        out = {"config": "degree", "graph": f"rmat{scale}", "edge_factor": ef, "vertices": g.num_vertices,
+               "edges": g.num_edges, "partition_size": 16384}
+        try:
+            G = Graph.from_csr(g.row_ptr, g.col, g.weights, partition_size=16384)
+        except GpopError as e:  # the layout does not fit: recorded, and the sweep goes on
+            out["skipped"] = str(e)
+            _emit(out)
+            del g
+            continue
+        info = G.info()
+        out["r"] = info["num_png"] / max(g.num_edges, 1)
+        for algo, kw in (("pagerank", dict(max_iters=10)), ("bfs", dict(source=root)), ("sssp", dict(source=root)),
+                         ("nibble", dict(source=root, epsilon=1e-9, max_iters=100))):
+            r = _median_run(G, algo, **kw)
+            out[algo] = {"ms": r.stats["device_ms"], "iterations": r.stats["iterations"],
+                         "pc_partition_steps": r.stats["pc_partition_steps"],
+                         "sc_partition_steps": r.stats["sc_partition_steps"]}
+        G.close()
+        if ef <= cc_max_ef:
+            gs = gg.symmetrized(g)
+            try:
+                Gs = Graph.from_csr(gs.row_ptr, gs.col, None, partition_size=16384)
+                r = _median_run(Gs, "cc")
+                out["cc"] = {"ms": r.stats["device_ms"], "iterations": r.stats["iterations"],
+                             "edges_sym": gs.num_edges, "pc_partition_steps": r.stats["pc_partition_steps"],
+                             "sc_partition_steps": r.stats["sc_partition_steps"]}
+                Gs.close()
+            except GpopError as e:
+                out["cc"] = {"edges_sym": gs.num_edges, "skipped": str(e)}
+            del gs
+        _emit(out)
+        del g
+
+
 def ablation():
     gg = _gen()
     g = gg.rmat(24).with_weights()
@@ -183,9 +245,9 @@ def ablation():
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--configs", default="c1,c2,c3,c4,ablation")
+    ap.add_argument("--configs", default="c1,c2,c3,c4,nibble,ablation,degree")
     a = ap.parse_args()
-    fns = {"c1": c1, "c2": c2, "c3": c3, "c4": c4, "ablation": ablation}
+    fns = {"c1": c1, "c2": c2, "c3": c3, "c4": c4, "nibble": nibble, "ablation": ablation, "degree": degree}
     for c in a.configs.split(","):
         fns[c]()
 
