@@ -137,10 +137,20 @@ def cpu_baseline(g, roots, pr_iters):
             "host_cores_available": os.cpu_count()}
 
 
+def engine_code_sha(path=ENGINE_SRC):
+    """sha256 prefix (16 hex) of the engine's code: the source with its comments, blank lines and the
+    whitespace around each line removed, so that an edit of comments alone keeps it."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    code = "\n".join(line.strip() for line in text.split("\n") if line.strip())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
+
+
 def traffic_from_profile(kernel):
     """Per-launch DRAM bytes of `kernel` from a committed ncu summary under profiles/ that names this kernel
-    and was taken from the current engine source (sha256 prefix); None otherwise."""
-    sha = hashlib.sha256(open(ENGINE_SRC, "rb").read()).hexdigest()[:16]
+    and was taken from the current engine code (engine_code_sha); None otherwise."""
+    sha = engine_code_sha()
     try:
         names = sorted(os.listdir(PROFILES))
     except OSError:

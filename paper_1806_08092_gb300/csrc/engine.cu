@@ -1,20 +1,25 @@
 // Per-iteration scatter/gather engine (Alg. 2 with Alg. 3 and Eq. (mode)).
 //
-// One iteration = four launches on the caller's stream:
+// One iteration = up to six launches on the caller's stream, after the host has read the plan:
 //   k_plan        1 CTA: per-partition V_a/E_a from the previous gather, mode
 //                 choice (Eq. (mode), forced, or learned), PC/NULL actions,
-//                 SC work list, termination test (Sec. 3.1.x active lists).
+//                 SC work list, termination test (Sec. 3.1.x active lists); its
+//                 control snapshot goes straight to mapped host memory.
 //   k_scatter_pc  PC mode (Alg. 3): every PNG slot of a PC partition receives
 //                 the current value of its source (NULL if inactive) as a
 //                 sequential vectorised stream over the padded row.
 //   k_scatter_sc  SC mode (Alg. 2 scatter): active vertices of the partition
 //                 append (destination, value) pairs to their bins through
 //                 warp-aggregated cursors.
-//   k_gather      per (column q, destination range) task: PC messages through
-//                 the destination-sorted lists (segmented reductions, no
-//                 atomics on vertex data), SC pairs with per-warp destination
-//                 ownership, then reInit/gather/filter user functions and the
-//                 next frontier (Alg. 2 gather + filter; Sec. 4).
+//   k_gather_pc   PC part of the gather: each column's bins staged block by
+//                 block in shared memory by bulk copies, folded through the
+//                 destination-sorted entry lists into a shared accumulator
+//                 (lane-serial runs and segmented warp scans, no atomics).
+//   k_merge_pc    columns split over several PC gather tasks: partial vectors
+//                 combined in task order.
+//   k_gather      per (column q, destination range) task: the column's PC
+//                 result and the task's SC pairs, then reInit/gather/filter user
+//                 functions and the next frontier (Alg. 2 gather + filter; Sec. 4).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

@@ -37,3 +37,16 @@ def test_two_rank_reduction():
 def test_single_rank_passthrough():
     import bench
     assert bench.reduce_over_ranks(2.0, 5.0, None, "cpu") == (2.0, 5.0)
+
+
+def test_engine_code_sha_ignores_comments_only(tmp_path):
+    import bench
+    a = tmp_path / "a.cu"
+    a.write_text("// header\n__global__ void k(int *x) {\n    x[0] = 1;  // set\n}\n")
+    b = tmp_path / "b.cu"
+    b.write_text("/* another\n   header */\n\n__global__ void k(int *x) {\n      x[0] = 1;\n}\n")
+    c = tmp_path / "c.cu"
+    c.write_text("__global__ void k(int *x) {\n    x[0] = 2;\n}\n")
+    assert bench.engine_code_sha(str(a)) == bench.engine_code_sha(str(b))
+    assert bench.engine_code_sha(str(a)) != bench.engine_code_sha(str(c))
+
