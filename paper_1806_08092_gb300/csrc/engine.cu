@@ -49,7 +49,7 @@ constexpr int kScatterThreads = 256;    // k_scatter_sc
 constexpr int kScatterPcThreads = 512;  // k_scatter_pc
 constexpr int kPlanThreads = 1024;
 constexpr uint32_t kSent = 0xFFFFFFFFu;
-constexpr uint32_t kScUnitEdges = 1u << 16;  // active edges per SC scatter unit of a split partition
+constexpr uint32_t kScUnitEdges = 1u << 12;  // active edges per SC scatter unit of a split partition
 constexpr uint32_t kBigScBin = 2048;     // SC bins at least this large are folded by the whole gather CTA
 constexpr uint32_t kMaxBigScBins = 64;
 constexpr int kPcWarps = kPcGatherWarps;          // k_gather_pc warps (one destination slice of a block each)
@@ -736,9 +736,10 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
     __shared__ uint32_t s_list[1024];       // active local IDs of the current 1024-vertex segment
     __shared__ uint32_t s_pref[1025];       // exclusive prefix of their out-degrees
     __shared__ uint32_t s_warp[33];
+    __shared__ uint32_t s_sege[16];         // active out-edges of each 1024-vertex segment of the partition
     __shared__ uint32_t s_task, s_nact, s_last;
     __shared__ unsigned long long s_t0;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t nunits = *p.list_count;
     for (;;) {
         if (threadIdx.x == 0) s_task = atomicAdd(&p.counters[p.counter_slot], 1u);
@@ -759,8 +760,35 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
         uint32_t *cur = split ? p.sc_gcur + rb0 : s_cursor;
         const uint32_t g0 = part << p.shift;
         const uint32_t gend = min(g0 + p.P, p.V);
+        // active out-edges of every segment (one warp per segment, from the frontier bits and the row
+        // offsets), so that empty segments, and those before a split unit's range, are passed over
+        // without building their active lists
+        const uint32_t nseg = (gend - g0 + 1023) / 1024;  // at most 16 (P <= 16384)
+        for (uint32_t si = wid; si < nseg; si += kScatterThreads / 32) {
+            const uint32_t gw = g0 + si * 1024 + (uint32_t)lane * 32;
+            uint32_t word = gw < gend ? p.bits[gw >> 5] : 0u;
+            uint32_t e = 0;
+            if (word == 0xFFFFFFFFu && gw + 32 <= gend) {
+                e = p.rowptr[gw + 32] - p.rowptr[gw];
+            } else {
+                while (word) {
+                    const uint32_t u = gw + (uint32_t)(__ffs(word) - 1);
+                    word &= word - 1;
+                    e += p.rowptr[u + 1] - p.rowptr[u];
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+            if (lane == 0) s_sege[si] = e;
+        }
+        __syncthreads();
         uint64_t run0 = 0;  // active edges of the partition before this segment
-        for (uint32_t seg = g0; seg < gend && run0 < ub; seg += 1024) {
+        for (uint32_t seg = g0, si = 0; seg < gend && run0 < ub; seg += 1024, ++si) {
+            const uint32_t seg_e = s_sege[si];
+            if (seg_e == 0 || run0 + seg_e <= ua) {  // nothing to scatter here (uniform over the CTA)
+                run0 += seg_e;
+                continue;
+            }
             // active vertices of this segment, ascending
             if (threadIdx.x < 32) {
                 uint32_t gw = seg + threadIdx.x * 32;

@@ -12,7 +12,9 @@ c3        PageRank to an L1 residual below 1e-9 on RMAT-24 and on a uniform rand
           same size and average degree, with FP32 and with BF16 bin messages: GTEPS = E x iterations / t
           and per-kernel times (the errors against the FP64 oracle come from the GPU tests).
 c4        RMAT-22 BFS from 64 sources: gpop_run_msbfs (two 32-source passes) against 64 single-source
-          gpop_run calls, TEPS = sum over sources of traversed edges / t, and the batching speedup.
+          gpop_run calls, TEPS = sum over sources of traversed edges / t, and the batching speedup; and
+          PPR from 256 seeds (alpha = 0.15, L1 change < 1e-9 or 100 iterations), one gpop_run per seed
+          (a 32-bit message holds one FP32 value, so seeds are not packed into one pass).
 nibble    parallel Nibble (Alg. 4) on RMAT-24 from 16 seeds with Sec. 5's threshold eps = 1e-9, at most
           100 iterations: time, iterations, vertices with PR > 0 and edges scattered per seed.
 degree    time against average degree (Sec. 5, execution time vs degree): RMAT-26 (64 M vertices) from
@@ -158,6 +160,18 @@ def c4(nsrc=64):
            "single_source_gteps": te / (single / 1e3) / 1e9, "batching_speedup": single / ms_b,
            "pc_partition_steps": r.stats["pc_partition_steps"], "sc_partition_steps": r.stats["sc_partition_steps"],
            "kernels_ms": _kernels(r.stats)})
+    seeds = [int(x) for x in gg.roots(g, 256)]
+    G.run("ppr", source=seeds[0], max_iters=100, tol=1e-9)  # warm-up
+    ms = its = edges = conv = 0
+    for s in seeds:
+        r = G.run("ppr", source=s, max_iters=100, tol=1e-9)
+        ms += r.stats["device_ms"]
+        its += r.stats["iterations"]
+        edges += r.stats["edges_scattered"]
+        conv += int(r.stats["converged"])
+    _emit({"config": "c4", "graph": "rmat22", "algo": "ppr", "seeds": len(seeds), "alpha": 0.15, "tol_l1": 1e-9,
+           "ms_total": ms, "ms_per_seed": ms / len(seeds), "iterations_mean": its / len(seeds), "converged": conv,
+           "gteps_scattered": edges / (ms / 1e3) / 1e9})
     G.close()
 
 
