@@ -204,6 +204,28 @@ __device__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_warp, uint32_t *tota
     return r;
 }
 
+// Work units of one chunk of partitions, written by every thread of the block: thread t has cnt units,
+// the first at position beg (an exclusive scan over the chunk, tot units in all), for partition q with ea
+// active edges.  A hub partition can have thousands of units, so each unit finds its partition by a
+// binary search over the chunk's unit ends instead of its partition's thread writing them all.
+__device__ void write_units(uint4 *list, uint32_t base, uint32_t q, uint32_t cnt, uint32_t beg, uint32_t tot, uint32_t ea,
+                            uint32_t *s_beg, uint32_t *s_end, uint32_t *s_q, uint32_t *s_ea) {
+    s_beg[threadIdx.x] = beg;
+    s_end[threadIdx.x] = beg + cnt;
+    s_q[threadIdx.x] = q;
+    s_ea[threadIdx.x] = ea;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < tot; i += blockDim.x) {
+        uint32_t lo = 0, hi = blockDim.x - 1;  // first thread whose units end after i
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_end[mid] > i) hi = mid; else lo = mid + 1;
+        }
+        list[base + i] = make_uint4(s_q[lo], i - s_beg[lo], s_end[lo] - s_beg[lo], s_ea[lo]);
+    }
+    __syncthreads();
+}
+
 // --- Eq. (mode) ----------------------------------------------------------------------------------
 
 // PC iff den * E^p * (3 n_png + k + E^p) <= num * (V_a E^p + 3 E_a E^p + 2 n_png E_a):
@@ -437,6 +459,7 @@ __global__ void k_task_stats(Params p) {
 
 __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
     __shared__ uint32_t s_warp[33];
+    __shared__ uint32_t s_ub[kPlanThreads], s_ue[kPlanThreads], s_uq[kPlanThreads], s_uea[kPlanThreads];
     __shared__ unsigned long long s_v[kPlanThreads / 32], s_e[kPlanThreads / 32];
     __shared__ double s_r[kPlanThreads / 32], s_b[kPlanThreads / 32];
     __shared__ uint32_t s_pc[kPlanThreads / 32], s_sc[kPlanThreads / 32], s_nl[kPlanThreads / 32], s_fb[kPlanThreads / 32];
@@ -498,14 +521,14 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         // kScUnitEdges active edges, scattered by several CTAs
         const uint32_t nu = Ea > 2ull * kScUnitEdges ? (uint32_t)min((unsigned long long)((Ea + kScUnitEdges - 1) / kScUnitEdges), 65535ull) : 1u;
         uint32_t total;
-        uint32_t off = block_excl_scan((valid && m == kModeSC) ? nu : 0u, s_warp, &total);
-        if (valid && m == kModeSC)
-            for (uint32_t j = 0; j < nu; ++j) p.sc_list[sc_base + off + j] = make_uint4(q, j, nu, (uint32_t)Ea);
+        const uint32_t nsc_u = (valid && m == kModeSC) ? nu : 0u;
+        uint32_t off = block_excl_scan(nsc_u, s_warp, &total);
+        write_units(p.sc_list, sc_base, q, nsc_u, off, total, (uint32_t)Ea, s_ub, s_ue, s_uq, s_uea);
         sc_base += total;
         if (p.log_both) {
-            uint32_t off2 = block_excl_scan((valid && m != kModeNone) ? nu : 0u, s_warp, &total);
-            if (valid && m != kModeNone)
-                for (uint32_t j = 0; j < nu; ++j) p.all_list[all_base + off2 + j] = make_uint4(q, j, nu, (uint32_t)Ea);
+            const uint32_t nall_u = (valid && m != kModeNone) ? nu : 0u;
+            uint32_t off2 = block_excl_scan(nall_u, s_warp, &total);
+            write_units(p.all_list, all_base, q, nall_u, off2, total, (uint32_t)Ea, s_ub, s_ue, s_uq, s_uea);
             all_base += total;
         }
     }
