@@ -214,6 +214,17 @@ gpop_status gpop_run_msbfs(gpop_graph *g, const gpop_run_opts *opts, const uint3
                            uint32_t *out_levels, int out_is_device, gpop_run_stats *stats);
 
 /*
+ * Diagnostics of the bounded device waits (every mbarrier wait of the PC gather and the PC scatter gives
+ * up after a fixed number of polls, raises the run's error word and lets the run return
+ * GPOP_ERR_TIMEOUT, leaving the CUDA context usable).  This call runs the same wait, on the current
+ * device, against a barrier phase that nothing completes, with at most `tries` polls, and sets
+ * *gave_up = 1 when the wait ran out and raised the error word as it must.  Errors:
+ * GPOP_ERR_INVALID_ARG (gave_up NULL), GPOP_ERR_CUDA, GPOP_ERR_DEVICE_CHECK (the phase reported
+ * completion, which would be a defect).
+ */
+gpop_status gpop_probe_bounded_wait(uint32_t tries, uint32_t *gave_up);
+
+/*
  * Learned SC/PC selector (replaces Eq. (mode) per partition per iteration when
  * opts.mode = GPOP_MODE_LEARNED).  An MLP 8 -> 32 -> 32 -> 1 with ReLU,
  * FP32, predicting y = log(t_PC / t_SC); PC is chosen iff y <= 0.  Features

@@ -228,6 +228,14 @@ class Graph:
         return RunResult(out, None, stats, modes, frontier, None)
 
 
+def probe_bounded_wait(tries: int) -> bool:
+    """Runs the engine's bounded mbarrier wait against a phase nothing completes (gpop_probe_bounded_wait);
+    True when the wait gave up after `tries` polls and raised the error word."""
+    gave = ctypes.c_uint32(0)
+    _lib.check(_lib.load().gpop_probe_bounded_wait(tries, ctypes.byref(gave)))
+    return bool(gave.value)
+
+
 def selector_set(params) -> None:
     """Installs learned-selector parameters (GPOP_SELECTOR_PARAMS floats) or removes them (None)."""
     lib = _lib.load()

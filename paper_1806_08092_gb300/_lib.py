@@ -70,6 +70,7 @@ SIGNATURES = {
     "gpop_run": (ctypes.c_int, [_vp, ctypes.POINTER(RunOpts), _vp, _vp, ctypes.c_int, ctypes.POINTER(RunStats)]),
     "gpop_run_msbfs": (ctypes.c_int, [_vp, ctypes.POINTER(RunOpts), _vp, ctypes.c_uint32, _vp, ctypes.c_int,
                                       ctypes.POINTER(RunStats)]),
+    "gpop_probe_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "gpop_selector_set": (ctypes.c_int, [_vp]),
     "gpop_selector_get": (ctypes.c_int, [_vp]),
     "gpop_selector_train": (ctypes.c_int, [_vp, _vp, _u32, _u32, _f32, _u64, _vp, _vp, _vp]),

@@ -617,14 +617,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // Waits for the completion of the barrier phase with the given parity, at most kPcSpinLimit tries;
 // gives up early when another warp has raised *abort, and raises it (with the run's error flag) when
 // its own tries run out.  Returns false when the caller must stop.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort, uint32_t *err) {
-    for (uint32_t it = 0; it < kPcSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort, uint32_t *err,
+                                          uint32_t limit = kPcSpinLimit) {
+    for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
     }
     *abort = 1;
     atomicOr(err, 1u);
     return false;
+}
+
+// Diagnostic of the bounded waits: one thread waits, through mbar_wait with `tries` polls, on a freshly
+// initialised mbarrier whose first phase nothing completes (no arrival, no copy); the wait must give up
+// and raise bit 0 of *err.  Bit 1 would mean the phase completed, which cannot happen.
+__global__ void k_wait_probe(uint32_t tries, uint32_t *err) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t abort;
+    if (threadIdx.x != 0) return;
+    abort = 0;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (mbar_wait(&bar, 0, &abort, err, tries)) atomicOr(err, 2u);
 }
 
 // Bounded wait used while leaving after an abort: lets copies still in flight land before the CTA exits.
@@ -2188,5 +2202,24 @@ extern "C" gpop_status gpop_run_msbfs(gpop_graph *h, const gpop_run_opts *o, con
         }
     }
     if (stats) *stats = total;
+    return GPOP_OK;
+}
+
+extern "C" gpop_status gpop_probe_bounded_wait(uint32_t tries, uint32_t *gave_up) {
+    set_error("");
+    if (!gave_up) return fail(GPOP_ERR_INVALID_ARG, "gave_up is NULL");
+    uint32_t *d_err = nullptr;
+    GPOP_CUDA_TRY(cudaMalloc((void **)&d_err, 4));
+    uint32_t h = 0;
+    cudaError_t e = cudaMemset(d_err, 0, 4);
+    if (e == cudaSuccess) {
+        k_wait_probe<<<1, 32>>>(tries, d_err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d_err, 4, cudaMemcpyDeviceToHost);
+    cudaFree(d_err);
+    if (e != cudaSuccess) return fail(GPOP_ERR_CUDA, std::string("wait probe: ") + cudaGetErrorString(e));
+    if (h & 2u) return fail(GPOP_ERR_DEVICE_CHECK, "a barrier phase that nothing completes reported completion");
+    *gave_up = h & 1u;
     return GPOP_OK;
 }

@@ -179,6 +179,17 @@ def test_traced_and_untraced_runs_agree():
             assert a.stats["kernel_launches"][0] == a.stats["iterations"] + 1
 
 
+def test_bounded_wait_gives_up_and_context_stays_usable():
+    # the engine's bounded mbarrier wait, against a phase that nothing completes: it must give up after
+    # its polls and raise the error word (no trap, no hang), and the device must stay usable afterwards
+    import paper_1806_08092_gb300 as gp
+    assert gp.probe_bounded_wait(1 << 16) is True
+    assert gp.probe_bounded_wait(0) is True
+    g = gg.rmat(10)
+    root = int(gg.roots(g, 1)[0])
+    assert np.array_equal(G(g, 64).run("bfs", source=root).values.cpu().numpy(), O.bfs(g, root)[0])
+
+
 # --- parallel Nibble (Alg. 4) ---------------------------------------------------------------------
 # FP32 on the GPU against the FP64 oracle: PR values are probabilities (they sum to 1), compared in
 # absolute terms.  The threshold PR >= eps deg is decided on FP32 values on the GPU and on FP64 values
