@@ -140,6 +140,14 @@ typedef struct {
                                   log_capacity records of GPOP_LOG_RECORD_FLOATS floats */
     uint64_t log_capacity;
     double epsilon;            /* Nibble threshold (default 1e-9, Sec. 5's setting); >= 0, finite */
+    int32_t resume;            /* non-zero: continue the state the graph holds (the last successful run of
+                                  this algorithm on it, or gpop_state_import) instead of starting afresh:
+                                  no initial frontier, iterations numbered on from the saved ones (BFS
+                                  levels), max_iters counts this call's iterations, and the first plan
+                                  tests the saved L1 change, so a run split at any iteration gives the
+                                  same results as one uninterrupted run.  source is not used.  Not for
+                                  gpop_run_msbfs.  GPOP_ERR_INVALID_ARG when no state of the algorithm
+                                  is held. */
 } gpop_run_opts;
 
 /* Floats per LOG_BOTH record: 8 selector features, t_PC (us), t_SC (us),
@@ -202,7 +210,7 @@ gpop_status gpop_run(gpop_graph *g, const gpop_run_opts *opts, void *out_values,
  *                device buffer owned by the graph)
  *   opts         mode, bw ratio, max_iters (per pass), profile_kernels and
  *                cuda_stream are used; algo, source and damping are ignored;
- *                msg_bf16 must be 0; trace buffers hold the last pass
+ *                msg_bf16 and resume must be 0; trace buffers hold the last pass
  *   stats        optional: sums over the passes (iterations, device_ms,
  *                kernel times, ...), converged = every pass converged
  * No parents are produced.  Errors: GPOP_ERR_INVALID_ARG (NULL pointers with
@@ -212,6 +220,22 @@ gpop_status gpop_run(gpop_graph *g, const gpop_run_opts *opts, void *out_values,
  */
 gpop_status gpop_run_msbfs(gpop_graph *g, const gpop_run_opts *opts, const uint32_t *sources, uint32_t num_sources,
                            uint32_t *out_levels, int out_is_device, gpop_run_stats *stats);
+
+/*
+ * Checkpoint of a run (all applications but multi-source BFS): the vertex values, BFS levels, next
+ * messages and frontier bitmap the last successful gpop_run on this graph left, with its algorithm, the
+ * number of iterations behind it and the L1 change of its last gather.
+ *   gpop_state_export  writes the checkpoint into the caller's HOST buffer of `capacity` bytes and its
+ *                      size into *size; with buffer NULL only the size is returned.
+ *   gpop_state_import  loads a checkpoint (of a graph with the same vertex count) into this graph, for a
+ *                      following gpop_run with opts.resume set.
+ * The layout is a 48-byte header (magic "GPST", version 1, algorithm, V, iterations, frontier words,
+ * L1 change) then V words each of values, levels and messages and the frontier words, little endian.
+ * Errors: GPOP_ERR_INVALID_ARG (no state held, buffer too small, header or size that does not match),
+ * GPOP_ERR_OOM, GPOP_ERR_CUDA.
+ */
+gpop_status gpop_state_export(const gpop_graph *g, void *buffer, uint64_t capacity, uint64_t *size);
+gpop_status gpop_state_import(gpop_graph *g, const void *buffer, uint64_t size);
 
 /*
  * Diagnostics of the bounded device waits (every mbarrier wait of the PC gather and the PC scatter gives

@@ -128,10 +128,12 @@ class Graph:
     def run(self, algo: str, source: int = 0, damping: float = 0.85, max_iters: int = 1000, tol: float = 0.0,
             mode: str = "analytic", bw_ratio=(2, 1), device_out: bool = True, trace: bool = False,
             log_capacity: int = 0, stream=None, out=None, out_parent=None, profile: bool = False,
-            msg_bf16: bool = False, epsilon: float = 1e-9) -> RunResult:
+            msg_bf16: bool = False, epsilon: float = 1e-9, resume: bool = False) -> RunResult:
         """Runs one application; outputs are torch tensors on cuda (device_out) or host numpy arrays.
         msg_bf16: PageRank / PPR messages travel through the bins as BF16 (gathered in FP32).
-        epsilon: Nibble's threshold (a vertex stays on while PR >= epsilon * out-degree)."""
+        epsilon: Nibble's threshold (a vertex stays on while PR >= epsilon * out-degree).
+        resume: continue the state this graph holds (its last run of `algo`, or state_import) for up to
+        max_iters more iterations, with the results of one uninterrupted run."""
         torch = _torch()
         lib = _lib.load()
         info = self.info()
@@ -149,6 +151,7 @@ class Graph:
         o.profile_kernels = int(profile)
         o.msg_bf16 = int(msg_bf16)
         o.epsilon = epsilon
+        o.resume = int(resume)
         modes = frontier = log = None
         if trace:
             modes = np.zeros(max(max_iters, 1) * k, dtype=np.uint8)
@@ -184,6 +187,20 @@ class Graph:
         if log is not None:
             log = log[: stats["log_records"] * LOG_RECORD_FLOATS].reshape(-1, LOG_RECORD_FLOATS)
         return RunResult(out, out_parent if algo == "bfs" else None, stats, modes, frontier, log)
+
+    def state_export(self) -> np.ndarray:
+        """Checkpoint of the last successful run on this graph (gpop_state_export), as host bytes."""
+        lib = _lib.load()
+        size = ctypes.c_uint64(0)
+        _lib.check(lib.gpop_state_export(self._h, None, 0, ctypes.byref(size)))
+        buf = np.zeros(size.value, dtype=np.uint8)
+        _lib.check(lib.gpop_state_export(self._h, ctypes.c_void_p(buf.ctypes.data), size.value, ctypes.byref(size)))
+        return buf
+
+    def state_import(self, buf) -> None:
+        """Loads a checkpoint written by state_export (of a graph with the same vertex count)."""
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        _lib.check(_lib.load().gpop_state_import(self._h, ctypes.c_void_p(b.ctypes.data), b.size))
 
     def run_msbfs(self, sources, max_iters: int = 1000, mode: str = "analytic", bw_ratio=(2, 1),
                   device_out: bool = True, trace: bool = False, stream=None, out=None,

@@ -42,7 +42,7 @@ class RunOpts(ctypes.Structure):
                 ("bw_ratio_num", ctypes.c_uint32), ("bw_ratio_den", ctypes.c_uint32), ("msg_bf16", ctypes.c_int32),
                 ("profile_kernels", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p), ("trace_modes", ctypes.c_void_p),
                 ("trace_frontier", ctypes.c_void_p), ("log_buffer", ctypes.c_void_p),
-                ("log_capacity", ctypes.c_uint64), ("epsilon", ctypes.c_double)]
+                ("log_capacity", ctypes.c_uint64), ("epsilon", ctypes.c_double), ("resume", ctypes.c_int32)]
 
 
 class RunStats(ctypes.Structure):
@@ -71,6 +71,8 @@ SIGNATURES = {
     "gpop_run_msbfs": (ctypes.c_int, [_vp, ctypes.POINTER(RunOpts), _vp, ctypes.c_uint32, _vp, ctypes.c_int,
                                       ctypes.POINTER(RunStats)]),
     "gpop_probe_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
+    "gpop_state_export": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+    "gpop_state_import": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64]),
     "gpop_selector_set": (ctypes.c_int, [_vp]),
     "gpop_selector_get": (ctypes.c_int, [_vp]),
     "gpop_selector_train": (ctypes.c_int, [_vp, _vp, _u32, _u32, _f32, _u64, _vp, _vp, _vp]),

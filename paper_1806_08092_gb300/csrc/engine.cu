@@ -134,6 +134,7 @@ struct Params {
     uint32_t *lvl_ms;       // multi-source BFS: levels, row j (V words) for source msrc[j]
     float c0, c1;           // PR: (1-d)/V, d.  PPR: alpha, 1-alpha
     float eps;              // Nibble: the threshold per unit of out-degree
+    double t_res0;          // resumed run: the L1 change of the last gather before the state was saved
     double tol;
     int algo, policy;
     uint32_t bw_num, bw_den;
@@ -448,7 +449,7 @@ __global__ void k_task_stats(Params p) {
             for (int i = 0; i < kGatherWarps; ++i) { a += s_va[i]; b += s_ea[i]; }
             p.t_va[t] = a;
             p.t_ea[t] = b;
-            p.t_res[t] = 0.0;
+            p.t_res[t] = t == 0 ? p.t_res0 : 0.0;  // a resumed run's first plan sees the saved L1 change
             p.t_stamp[t] = p.epoch;
         }
         __syncthreads();
@@ -1658,6 +1659,11 @@ struct RunBuffers {
     float *feat = nullptr;
     // multi-source BFS (allocated on first use): the pass's sources, staged level rows for host output
     uint32_t *msrc = nullptr, *lvl_ms = nullptr;
+    // the state the last successful run left (val, lvl, sval, bits), for gpop_state_export and resume:
+    // its algorithm (-1: none), the iterations behind it and the L1 change of its last gather
+    int state_algo = -1;
+    uint32_t state_iter = 0;
+    double state_res = 0.0;
 };
 
 static void release_runbufs(RunBuffers *rb) {
@@ -1845,7 +1851,15 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         if (ae != cudaSuccess) return fail(GPOP_ERR_OOM, std::string("LOG_BOTH buffers: ") + cudaGetErrorString(ae));
     }
     p.all_list = rb->all_list; p.feat = rb->feat; p.part_va = rb->part_va; p.part_ea = rb->part_ea;
-    p.source = o->source; p.max_iters = o->max_iters; p.tol = o->tol_l1;
+    // a resumed run continues the saved state: iterations are numbered on from it (BFS levels), the cap
+    // counts this call's iterations, and its first plan tests the saved L1 change
+    const bool resume = o->resume != 0;
+    if (resume && rb->state_algo != ALGO) return fail(GPOP_ERR_INVALID_ARG, "resume: no saved state of this algorithm");
+    const uint32_t base = resume ? rb->state_iter : 0u;
+    p.source = o->source; p.tol = o->tol_l1;
+    p.max_iters = o->max_iters > 0xFFFFFFFEu - base ? 0xFFFFFFFEu : base + o->max_iters;
+    p.t_res0 = resume ? rb->state_res : 0.0;
+    rb->state_algo = -1;  // until this run succeeds
     if (ALGO == ALG_MSBFS) {
         p.msrc = mpass->src; p.nsrc = mpass->n; p.lvl_ms = mpass->lvl;
     }
@@ -1901,9 +1915,13 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     const bool learned = p.policy == GPOP_MODE_LEARNED && p.selector;
     p.col_done = learned ? rb->col_done : nullptr;
     if (learned) GPOP_CUDA_TRY(cudaMemsetAsync(rb->col_done, 0, 4ull * g->k, s));
-    if (ALGO == ALG_MSBFS) GPOP_CUDA_TRY(cudaMemsetAsync(p.lvl_ms, 0xFF, 4ull * p.nsrc * g->V, s));
-    k_init<ALGO><<<std::max(1, std::min((int)((g->V / 32 + 255) / 256), 4096)), 256, 0, s>>>(p);
-    if (ALGO == ALG_MSBFS) k_msbfs_sources<<<1, 32, 0, s>>>(p);
+    if (!resume) {
+        if (ALGO == ALG_MSBFS) GPOP_CUDA_TRY(cudaMemsetAsync(p.lvl_ms, 0xFF, 4ull * p.nsrc * g->V, s));
+        k_init<ALGO><<<std::max(1, std::min((int)((g->V / 32 + 255) / 256), 4096)), 256, 0, s>>>(p);
+        if (ALGO == ALG_MSBFS) k_msbfs_sources<<<1, 32, 0, s>>>(p);
+    } else {
+        GPOP_CUDA_TRY(cudaMemsetAsync(&rb->ctrl->error, 0, 4, s));  // k_init's reset of the error word
+    }
     k_task_stats<<<std::max(1, std::min((int)g->ngt, 8 * g->num_sms)), kGatherThreads, 0, s>>>(p);
     GPOP_CUDA_TRY(cudaGetLastError());
 
@@ -1996,7 +2014,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         }
         st.residual = c.residual;
         if (c.done) {
-            st.converged = (c.frontier_v == 0) || ((ALGO == ALG_PR || ALGO == ALG_PPR) && iter > 0 && c.residual < o->tol_l1);
+            st.converged = (c.frontier_v == 0) || ((ALGO == ALG_PR || ALGO == ALG_PPR) && base + iter > 0 && c.residual < o->tol_l1);
             return false;
         }
         ++iter;
@@ -2010,13 +2028,13 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     // Each iteration: the plan, the host's read of its snapshot (mapped memory written by k_plan, no copy
     // in the stream), then the launches the plan asks for
     for (;;) {
-        p.iter = iter + 1;
+        p.iter = base + iter + 1;
         p.epoch = ++g->epoch;
         launch_plan(iter, p);
         cudaError_t ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("plan: ") + cudaGetErrorString(ce)); break; }
         if (prof) resolve();
-        const Control c = rb->h_ctrl[iter & 1];  // this plan's slot: p.iter - 1 = iter
+        const Control c = rb->h_ctrl[(base + iter) & 1];  // this plan's slot: (p.iter - 1) & 1
         if (!take(c)) break;
         if (o->trace_frontier) {
             o->trace_frontier[2 * (iter - 1)] = c.frontier_v;
@@ -2049,6 +2067,11 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     }
     st.iterations = iter;
     st.device_ms = ms;
+    if (ALGO != ALG_MSBFS) {
+        rb->state_algo = ALGO;
+        rb->state_iter = base + iter;
+        rb->state_res = st.residual;
+    }
 
     // outputs
     cudaMemcpyKind kind = out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -2154,6 +2177,7 @@ extern "C" gpop_status gpop_run_msbfs(gpop_graph *h, const gpop_run_opts *o, con
     for (uint32_t j = 0; j < num_sources; ++j)
         if (sources[j] >= g->V) return fail(GPOP_ERR_INVALID_ARG, "source out of range");
     if (o->msg_bf16) return fail(GPOP_ERR_INVALID_ARG, "BF16 messages are for PageRank and PPR (BFS stays exact)");
+    if (o->resume) return fail(GPOP_ERR_INVALID_ARG, "multi-source BFS does not resume");
     gpop_status cs = check_common_opts(o);
     if (cs != GPOP_OK) return cs;
     gpop_run_stats total;
@@ -2221,5 +2245,78 @@ extern "C" gpop_status gpop_probe_bounded_wait(uint32_t tries, uint32_t *gave_up
     if (e != cudaSuccess) return fail(GPOP_ERR_CUDA, std::string("wait probe: ") + cudaGetErrorString(e));
     if (h & 2u) return fail(GPOP_ERR_DEVICE_CHECK, "a barrier phase that nothing completes reported completion");
     *gave_up = h & 1u;
+    return GPOP_OK;
+}
+
+// --- checkpoint ---------------------------------------------------------------------------------
+
+namespace {
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t algo;
+    uint32_t V, iterations, nwords;
+    double residual;
+    uint64_t pad[2];
+};
+static_assert(sizeof(StateHeader) == 48, "checkpoint header is 48 bytes");
+constexpr uint32_t kStateMagic = 0x54535047u;  // "GPST"
+uint64_t state_bytes(uint32_t V) { return sizeof(StateHeader) + 12ull * V + 4ull * ((V + 31) / 32); }
+}  // namespace
+
+extern "C" gpop_status gpop_state_export(const gpop_graph *h, void *buffer, uint64_t capacity, uint64_t *size) {
+    set_error("");
+    if (!h || !size) return fail(GPOP_ERR_INVALID_ARG, "NULL graph or size");
+    const Graph *g = &h->g;
+    const RunBuffers *rb = static_cast<const RunBuffers *>(g->run);
+    if (!rb || rb->state_algo < 0) return fail(GPOP_ERR_INVALID_ARG, "no run state to export");
+    const uint64_t need = state_bytes(g->V);
+    *size = need;
+    if (!buffer) return GPOP_OK;
+    if (capacity < need) return fail(GPOP_ERR_INVALID_ARG, "checkpoint buffer too small");
+    StateHeader hd{};
+    hd.magic = kStateMagic;
+    hd.version = 1;
+    hd.algo = rb->state_algo;
+    hd.V = g->V;
+    hd.iterations = rb->state_iter;
+    hd.nwords = (g->V + 31) / 32;
+    hd.residual = rb->state_res;
+    char *out = static_cast<char *>(buffer);
+    memcpy(out, &hd, sizeof hd);
+    out += sizeof hd;
+    GPOP_CUDA_TRY(cudaDeviceSynchronize());
+    GPOP_CUDA_TRY(cudaMemcpy(out, rb->val, 4ull * g->V, cudaMemcpyDeviceToHost));
+    GPOP_CUDA_TRY(cudaMemcpy(out + 4ull * g->V, rb->lvl, 4ull * g->V, cudaMemcpyDeviceToHost));
+    GPOP_CUDA_TRY(cudaMemcpy(out + 8ull * g->V, rb->sval, 4ull * g->V, cudaMemcpyDeviceToHost));
+    GPOP_CUDA_TRY(cudaMemcpy(out + 12ull * g->V, rb->bits, 4ull * hd.nwords, cudaMemcpyDeviceToHost));
+    return GPOP_OK;
+}
+
+extern "C" gpop_status gpop_state_import(gpop_graph *h, const void *buffer, uint64_t size) {
+    set_error("");
+    if (!h || !buffer) return fail(GPOP_ERR_INVALID_ARG, "NULL graph or buffer");
+    Graph *g = &h->g;
+    if (size < sizeof(StateHeader)) return fail(GPOP_ERR_INVALID_ARG, "checkpoint shorter than its header");
+    StateHeader hd;
+    memcpy(&hd, buffer, sizeof hd);
+    if (hd.magic != kStateMagic || hd.version != 1) return fail(GPOP_ERR_INVALID_ARG, "not a checkpoint of this format");
+    if (hd.V != g->V || size != state_bytes(g->V) || hd.nwords != (g->V + 31) / 32)
+        return fail(GPOP_ERR_INVALID_ARG, "checkpoint of a graph with another vertex count");
+    if (hd.algo < GPOP_PAGERANK || hd.algo > GPOP_NIBBLE) return fail(GPOP_ERR_INVALID_ARG, "checkpoint of an unknown algorithm");
+    RunBuffers *rb = static_cast<RunBuffers *>(g->run);
+    if (!rb) {
+        gpop_status st = alloc_runbufs(g, &rb);
+        if (st != GPOP_OK) return st;
+        g->run = rb;
+    }
+    const char *in = static_cast<const char *>(buffer) + sizeof hd;
+    GPOP_CUDA_TRY(cudaDeviceSynchronize());
+    GPOP_CUDA_TRY(cudaMemcpy(rb->val, in, 4ull * g->V, cudaMemcpyHostToDevice));
+    GPOP_CUDA_TRY(cudaMemcpy(rb->lvl, in + 4ull * g->V, 4ull * g->V, cudaMemcpyHostToDevice));
+    GPOP_CUDA_TRY(cudaMemcpy(rb->sval, in + 8ull * g->V, 4ull * g->V, cudaMemcpyHostToDevice));
+    GPOP_CUDA_TRY(cudaMemcpy(rb->bits, in + 12ull * g->V, 4ull * hd.nwords, cudaMemcpyHostToDevice));
+    rb->state_algo = hd.algo;
+    rb->state_iter = hd.iterations;
+    rb->state_res = hd.residual;
     return GPOP_OK;
 }

@@ -48,9 +48,9 @@ def test_struct_layouts_match_the_header(tmp_path):
 #include <stddef.h>
 #include "gpop.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(gpop_graph_info), sizeof(gpop_run_opts), sizeof(gpop_run_stats),
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(gpop_graph_info), sizeof(gpop_run_opts), sizeof(gpop_run_stats),
          offsetof(gpop_run_opts, cuda_stream), offsetof(gpop_run_opts, log_capacity),
-         offsetof(gpop_run_opts, epsilon));
+         offsetof(gpop_run_opts, epsilon), offsetof(gpop_run_opts, resume));
   printf("%d %d %d\n", GPOP_SELECTOR_WEIGHTS, GPOP_SELECTOR_PARAMS, GPOP_LOG_RECORD_FLOATS);
   return 0; }
 ''')
@@ -59,7 +59,8 @@ int main(void) {
     lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     a = [int(x) for x in lines[0].split()]
     assert a == [ctypes.sizeof(_lib.GraphInfo), ctypes.sizeof(_lib.RunOpts), ctypes.sizeof(_lib.RunStats),
-                 _lib.RunOpts.cuda_stream.offset, _lib.RunOpts.log_capacity.offset, _lib.RunOpts.epsilon.offset]
+                 _lib.RunOpts.cuda_stream.offset, _lib.RunOpts.log_capacity.offset, _lib.RunOpts.epsilon.offset,
+                 _lib.RunOpts.resume.offset]
     b = [int(x) for x in lines[1].split()]
     assert b == [_lib.SELECTOR_WEIGHTS, _lib.SELECTOR_PARAMS, _lib.LOG_RECORD_FLOATS]
 

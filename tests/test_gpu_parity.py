@@ -190,6 +190,66 @@ def test_bounded_wait_gives_up_and_context_stays_usable():
     assert np.array_equal(G(g, 64).run("bfs", source=root).values.cpu().numpy(), O.bfs(g, root)[0])
 
 
+def _bits(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def test_resume_from_checkpoint_matches_uninterrupted_run():
+    # a run split at iteration `split` (continued on the same handle, and from an exported checkpoint on a
+    # fresh handle of the same graph) gives the uninterrupted run's results bit for bit
+    g = gg.rmat(14).with_weights()
+    root = int(gg.roots(g, 1)[0])
+    cases = (("pagerank", dict(max_iters=20), 8), ("pagerank", dict(max_iters=300, tol=1e-9), 10),
+             ("bfs", dict(source=root), 3), ("sssp", dict(source=root), 4),
+             ("ppr", dict(source=root, max_iters=80, tol=1e-10), 7),
+             ("nibble", dict(source=root, epsilon=1e-4, max_iters=200), 3))
+    for algo, kw, split in cases:
+        Gd = G(g, 512)
+        full = Gd.run(algo, **kw)
+        total = kw.get("max_iters", 1000)
+        first = Gd.run(algo, **{**kw, "max_iters": split})
+        assert first.stats["iterations"] == split, algo
+        blob = Gd.state_export()
+        same = Gd.run(algo, resume=True, **{**kw, "max_iters": total - split})
+        fresh = G(g, 512)
+        fresh.state_import(blob)
+        other = fresh.run(algo, resume=True, **{**kw, "max_iters": total - split})
+        for r in (same, other):
+            assert split + r.stats["iterations"] == full.stats["iterations"], algo
+            assert r.stats["converged"] == full.stats["converged"], algo
+            assert np.array_equal(_bits(r.values), _bits(full.values)), algo
+            if algo == "bfs":
+                assert np.array_equal(_bits(r.parent), _bits(full.parent))
+    gs = gg.symmetrized(gg.rmat(13))
+    Gs = G(gs, 256)
+    full = Gs.run("cc")
+    Gs.run("cc", max_iters=2)
+    rest = Gs.run("cc", resume=True)
+    assert 2 + rest.stats["iterations"] == full.stats["iterations"]
+    assert np.array_equal(_bits(rest.values), _bits(full.values))
+
+
+def test_checkpoint_errors():
+    import paper_1806_08092_gb300 as gp
+    g = gg.rmat(10)
+    Gd = G(g, 64)
+    with pytest.raises(gp.GpopError):
+        Gd.state_export()  # nothing has run
+    with pytest.raises(gp.GpopError):
+        Gd.run("pagerank", resume=True, max_iters=3)  # no state to continue
+    root = int(gg.roots(g, 1)[0])
+    Gd.run("bfs", source=root, max_iters=2)
+    blob = Gd.state_export()
+    with pytest.raises(gp.GpopError):
+        Gd.run("pagerank", resume=True, max_iters=3)  # the state is a BFS's
+    with pytest.raises(gp.GpopError):
+        G(gg.rmat(11), 64).state_import(blob)  # another vertex count
+    bad = blob.copy()
+    bad[0] ^= 0xFF
+    with pytest.raises(gp.GpopError):
+        G(g, 64).state_import(bad)  # not a checkpoint
+
+
 # --- parallel Nibble (Alg. 4) ---------------------------------------------------------------------
 # FP32 on the GPU against the FP64 oracle: PR values are probabilities (they sum to 1), compared in
 # absolute terms.  The threshold PR >= eps deg is decided on FP32 values on the GPU and on FP64 values
