@@ -9,6 +9,7 @@
 
     python -m paper_1806_08092_gb300.selector_train --out paper_1806_08092_gb300/selector_rmat.f32   # train + eval
     python -m paper_1806_08092_gb300.selector_train --params paper_1806_08092_gb300/selector_rmat.f32 --eval-scale 25
+    python -m paper_1806_08092_gb300.selector_train --nibble --out selector.f32   # + Nibble records and evaluation
 
 `selector_rmat.f32` in this package was written by the first command; bench.py reads it.
 """
@@ -42,14 +43,19 @@ def training_graphs(scales=(20, 21, 22, 23), uniform_scales=(21, 22)):
         yield f"uniform{s}", gg.uniform(n, 16 * n).with_weights()
 
 
-def collect(graphs, partition_size=16384, roots_per_graph=4, algos=("bfs", "sssp"), capacity=2_000_000):
+def collect(graphs, partition_size=16384, roots_per_graph=4, algos=("bfs", "sssp"), capacity=2_000_000,
+            nibble_iters=40):
+    """LOG_BOTH records of every run.  Nibble runs use eps = 1 / E of the graph, the threshold at which
+    its frontier stays large and made of low-degree vertices (the walk thins out to about 1 / volume),
+    and stop after nibble_iters iterations."""
     gg = _gen()
     recs = []
     for name, g in graphs:
         G = Graph.from_csr(g.row_ptr, g.col, g.weights, partition_size=partition_size)
         for root in gg.roots(g, roots_per_graph):
             for algo in algos:
-                r = G.run(algo, source=int(root), mode="log_both", log_capacity=capacity)
+                kw = dict(epsilon=1.0 / max(g.num_edges, 1), max_iters=nibble_iters) if algo == "nibble" else {}
+                r = G.run(algo, source=int(root), mode="log_both", log_capacity=capacity, **kw)
                 if r.log is not None and len(r.log):
                     recs.append(r.log.copy())
         G.close()
@@ -83,7 +89,7 @@ def regret_report(params, records):
             "agree_with_best_learned": float(np.mean(learned_pc == (t_pc <= t_sc)))}
 
 
-def evaluate(g, params, partition_size=16384, roots=4, reps=5, algos=("bfs", "sssp")):
+def evaluate(g, params, partition_size=16384, roots=4, reps=5, algos=("bfs", "sssp"), run_kw=None):
     """Median device time per (root, algorithm) with Eq. (mode) and with the trained selector."""
     gg = _gen()
     G = Graph.from_csr(g.row_ptr, g.col, g.weights, partition_size=partition_size)
@@ -95,7 +101,7 @@ def evaluate(g, params, partition_size=16384, roots=4, reps=5, algos=("bfs", "ss
                 t = {"analytic": [], "learned": []}
                 for _ in range(reps):
                     for mode in ("analytic", "learned"):
-                        r = G.run(algo, source=int(root), mode=mode)
+                        r = G.run(algo, source=int(root), mode=mode, **(run_kw or {}))
                         t[mode].append(r.stats["device_ms"])
                 out["analytic_ms"] += float(np.median(t["analytic"]))
                 out["learned_ms"] += float(np.median(t["learned"]))
@@ -113,13 +119,18 @@ def main():
     ap.add_argument("--eval-scale", type=int, default=25)
     ap.add_argument("--partition", type=int, default=16384)
     ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--nibble", action="store_true",
+                    help="also train on Nibble runs (eps = 1 / E) and evaluate Nibble on RMAT-26, edge factor 16")
+    ap.add_argument("--nibble-eval-scale", type=int, default=26)
+    ap.add_argument("--nibble-eval-ef", type=int, default=16)
     a = ap.parse_args()
     report = {}
     if a.params:
         params = np.fromfile(a.params, dtype=np.float32)
     else:
         t0 = time.time()
-        recs = collect(training_graphs(), partition_size=a.partition)
+        algos = ("bfs", "sssp", "nibble") if a.nibble else ("bfs", "sssp")
+        recs = collect(training_graphs(), partition_size=a.partition, algos=algos)
         rng = np.random.default_rng(0)
         idx = rng.permutation(len(recs))
         cut = int(0.8 * len(recs))
@@ -132,6 +143,12 @@ def main():
     g = gg.rmat(a.eval_scale).with_weights()
     report["eval"] = evaluate(g, params, partition_size=a.partition)
     report["eval"]["graph"] = f"rmat{a.eval_scale}"
+    del g
+    if a.nibble:
+        g = gg.rmat(a.nibble_eval_scale, a.nibble_eval_ef)
+        report["eval_nibble"] = evaluate(g, params, partition_size=a.partition, roots=2, reps=3, algos=("nibble",),
+                                         run_kw=dict(epsilon=1e-9, max_iters=100))
+        report["eval_nibble"]["graph"] = f"rmat{a.nibble_eval_scale}_ef{a.nibble_eval_ef}"
     print(json.dumps(report))
 
 
