@@ -519,8 +519,11 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
             pc_base += totp;
         }
         // SC scatter units: a partition with many active edges is split into ranges of about
-        // kScUnitEdges active edges, scattered by several CTAs
-        const uint32_t nu = Ea > 2ull * kScUnitEdges ? (uint32_t)min((unsigned long long)((Ea + kScUnitEdges - 1) / kScUnitEdges), 65535ull) : 1u;
+        // max(kScUnitEdges, V_a) active edges, scattered by several CTAs (every unit first sums its
+        // partition's active out-edges per segment, about V_a loads, so a unit is never made smaller
+        // than that)
+        const unsigned long long unit = max((unsigned long long)kScUnitEdges, (unsigned long long)Va);
+        const uint32_t nu = Ea > 2ull * unit ? (uint32_t)min((unsigned long long)((Ea + unit - 1) / unit), 65535ull) : 1u;
         uint32_t total;
         const uint32_t nsc_u = (valid && m == kModeSC) ? nu : 0u;
         uint32_t off = block_excl_scan(nsc_u, s_warp, &total);
