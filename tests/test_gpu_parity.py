@@ -250,6 +250,24 @@ def test_checkpoint_errors():
         G(g, 64).state_import(bad)  # not a checkpoint
 
 
+def test_partition_size_autotuner():
+    # every candidate is built and timed through the library; the fastest is returned, and a candidate
+    # the library rejects (not a power of two) is listed with the library's message and skipped
+    from paper_1806_08092_gb300.autotune import pick_partition_size
+    g = gg.rmat(13).with_weights()
+    root = int(gg.roots(g, 1)[0])
+    best, table = pick_partition_size(g.row_ptr, g.col, g.weights, runs=[("bfs", {"source": root}),
+                                      ("sssp", {"source": root})], candidates=(256, 1000, 2048, 8192), reps=3)
+    timed = [r for r in table if r[1] is not None]
+    assert [r[0] for r in timed] == [256, 2048, 8192]
+    assert best == min(timed, key=lambda r: r[1])[0]
+    rejected = [r for r in table if r[1] is None]
+    assert [r[0] for r in rejected] == [1000] and "power of two" in rejected[0][3]
+    # the layout it picks gives the same exact results
+    Gd = G(g, best)
+    assert np.array_equal(Gd.run("bfs", source=root).values.cpu().numpy(), O.bfs(g, root)[0])
+
+
 # --- parallel Nibble (Alg. 4) ---------------------------------------------------------------------
 # FP32 on the GPU against the FP64 oracle: PR values are probabilities (they sum to 1), compared in
 # absolute terms.  The threshold PR >= eps deg is decided on FP32 values on the GPU and on FP64 values
