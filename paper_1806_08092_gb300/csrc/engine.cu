@@ -765,9 +765,11 @@ __global__ void __launch_bounds__(kScatterPcThreads) k_scatter_pc(Params p) {
 
 // --- SC scatter (Alg. 2 scatter in source-centric mode) ---------------------------------------
 
-// One CTA per work unit: a whole SC partition, or one range of about kScUnitEdges active edges of a
-// partition with many (split partitions).  The partition's active vertices are taken in ascending order,
-// 1024 at a time, and their out-edges expanded one per thread; each pair goes to the sub-bin of its
+// One CTA per work unit: a whole SC partition, or one range of about max(kScUnitEdges, V_a) active edges
+// of a partition with many (split partitions).  A unit first sums the active out-edges of each of its
+// partition's 1024-vertex segments and passes over the empty ones and those before its range.  The
+// partition's active vertices are taken in ascending order, 1024 at a time, and their out-edges
+// expanded one per thread; each pair goes to the sub-bin of its
 // (partition, gather task) at a cursor bumped once per distinct sub-bin per warp.  Whole partitions keep
 // their cursors in shared memory and publish the counts at the end; split partitions bump global cursors
 // (zero at rest), and their last unit to finish publishes the counts and resets the cursors.

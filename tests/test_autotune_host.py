@@ -1,0 +1,49 @@
+"""Host logic of the partition-size autotuner on CPU: a stand-in Graph with fixed device times."""
+import pytest
+
+from paper_1806_08092_gb300 import GpopError
+from paper_1806_08092_gb300 import autotune
+
+
+class _FakeRun:
+    def __init__(self, ms):
+        self.stats = {"device_ms": ms}
+
+
+class _FakeGraph:
+    times = {}
+    closed = []
+
+    def __init__(self, P):
+        self.P = P
+
+    @classmethod
+    def from_csr(cls, row_ptr, col, weights, partition_size):
+        if partition_size not in cls.times:
+            raise GpopError(1, "partition_size must be a power of two in [32, 16384]")
+        return cls(partition_size)
+
+    def run(self, algo, **kw):
+        return _FakeRun(self.times[self.P][algo])
+
+    def close(self):
+        self.closed.append(self.P)
+
+
+def test_picks_the_fastest_and_lists_rejected(monkeypatch):
+    _FakeGraph.times = {1024: {"bfs": 3.0, "sssp": 9.0}, 4096: {"bfs": 2.0, "sssp": 7.5}, 16384: {"bfs": 2.5, "sssp": 7.4}}
+    _FakeGraph.closed = []
+    monkeypatch.setattr(autotune, "Graph", _FakeGraph)
+    best, table = autotune.pick_partition_size(None, None, None, runs=[("bfs", {}), ("sssp", {})],
+                                               candidates=(1024, 3000, 4096, 16384), reps=3)
+    assert best == 4096  # 9.5 ms against 12.0 and 9.9
+    assert [(r[0], r[1]) for r in table] == [(1024, 12.0), (3000, None), (4096, 9.5), (16384, 9.9)]
+    assert "power of two" in table[1][3]
+    assert _FakeGraph.closed == [1024, 4096, 16384]  # every built layout is released
+
+
+def test_no_candidate_raises(monkeypatch):
+    _FakeGraph.times = {}
+    monkeypatch.setattr(autotune, "Graph", _FakeGraph)
+    with pytest.raises(ValueError):
+        autotune.pick_partition_size(None, None, None, candidates=(3000,))
