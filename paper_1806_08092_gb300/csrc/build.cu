@@ -273,35 +273,61 @@ __global__ void k_edge_sub(uint64_t E, uint32_t shift, const uint32_t *src, cons
     }
 }
 
+// first entry of [l, h) (sorted by destination) whose destination is at least D
+__device__ __forceinline__ uint32_t first_dest_at_least(const uint32_t *pe, uint32_t l, uint32_t h, uint32_t D) {
+    while (l < h) {
+        const uint32_t m = l + (h - l) / 2;
+        if ((pe[m] >> 16) < D) l = m + 1; else h = m;
+    }
+    return l;
+}
+
+// Destination cuts of the PC gather's warps, one set per task: the w-th cut (w = 1 .. kPcGatherWarps - 1)
+// of task t is the smallest destination D such that at least w / kPcGatherWarps of the task's entries (over
+// all its blocks, rows [row0[t], row0[t + 1]) with entries [lo, hi) each, sorted by destination) go to
+// destinations below D.  Warp w then owns destinations [D_w, D_w+1) in every block of the task, so that
+// gather warps working on different blocks never touch one destination.
+__global__ void k_task_cuts(uint32_t ntask, uint32_t P, const uint32_t *row0, const uint32_t *lo, const uint32_t *hi,
+                            const uint32_t *pe, uint32_t *cut) {
+    constexpr uint32_t kW = kPcGatherWarps;
+    const uint64_t n = (uint64_t)ntask * (kW - 1), stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t t = (uint32_t)(i / (kW - 1)), w = (uint32_t)(i % (kW - 1)) + 1;
+        uint64_t total = 0;
+        for (uint32_t r = row0[t]; r < row0[t + 1]; ++r) total += hi[r] - lo[r];
+        const uint64_t target = (total * w + kW - 1) / kW;
+        uint32_t a = 0, b = P;  // smallest D in [0, P] with count(dest < D) >= target
+        while (a < b) {
+            const uint32_t D = a + (b - a) / 2;
+            uint64_t c = 0;
+            for (uint32_t r = row0[t]; r < row0[t + 1]; ++r) c += first_dest_at_least(pe, lo[r], hi[r], D) - lo[r];
+            if (c >= target) b = D; else a = D + 1;
+        }
+        cut[i] = a;
+    }
+}
+
 // Warp splits of the PC gather: for every task block (entries [lo, hi), sorted by destination) and w in
-// 0..kPcGatherWarps, the w-th of kPcGatherWarps ranges of about equal size: the nominal cut
-// lo + (hi - lo) w / kPcGatherWarps moved forward to the next change of destination, so that every
-// destination's entries of the block fall into one range.
-__global__ void k_warp_splits(uint32_t nrow, const uint32_t *lo, const uint32_t *hi, const uint32_t *pe,
-                              uint32_t *out) {
+// 0..kPcGatherWarps, the first entry of warp w's destinations [D_w, D_w+1) under its task's cuts.
+__global__ void k_warp_splits(uint32_t nrow, const uint32_t *lo, const uint32_t *hi, const uint32_t *row_task,
+                              const uint32_t *cut, const uint32_t *pe, uint32_t *out) {
     constexpr uint32_t kSp = kPcGatherWarps + 1;
     uint64_t n = (uint64_t)nrow * kSp, stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint32_t r = (uint32_t)(i / kSp), w = (uint32_t)(i % kSp);
         const uint32_t l = lo[r], h = hi[r];
-        uint32_t a = (uint32_t)(l + (uint64_t)(h - l) * w / kPcGatherWarps), b = h;
-        if (a > l && a < h) {
-            const uint32_t d = pe[a - 1] >> 16;
-            while (a < b) {  // first entry in [a, h) with destination > d
-                const uint32_t m = a + (b - a) / 2;
-                if ((pe[m] >> 16) <= d) a = m + 1; else b = m;
-            }
-        }
+        uint32_t a = w == 0 ? l : h;
+        if (w > 0 && w < kPcGatherWarps)
+            a = first_dest_at_least(pe, l, h, cut[(uint64_t)row_task[r] * (kPcGatherWarps - 1) + w - 1]);
         out[i] = a;
     }
 }
 
 // Copies each warp range [old0, old0 + len) of the destination entries to new0, padded to a multiple of
 // kPcPad with entries that repeat the range's last destination and point to the padding value slot
-// (which holds the monoid identity in the gather).  Within
-// every 16-entry group g of a range, the four 16-byte quads are stored in the order quad ^ ((g >> 1) & 3):
-// a gather lane reads one group with 16-byte loads, and the swizzle spreads the eight lanes of each load
-// phase over distinct banks.
+// (which holds the monoid identity in the gather).  The range is stored round by round in the gather's
+// lane-interleaved order (pc_round_pos), and every entry's destination field becomes its swizzled
+// accumulator position (pc_swz; destinations stay equal exactly when their positions are).
 __global__ void k_pad_entries(uint32_t nrange, const uint32_t *old0, const uint32_t *len, const uint32_t *new0,
                               const uint32_t *pe, const int32_t *pw, uint32_t *pe2, int32_t *pw2) {
     for (uint32_t r = blockIdx.x; r < nrange; r += gridDim.x) {
@@ -316,8 +342,9 @@ __global__ void k_pad_entries(uint32_t nrange, const uint32_t *old0, const uint3
             } else {
                 v = (pe[a + L - 1] & 0xFFFF0000u) | kPcPadIdx;
             }
-            const uint32_t grp = i / 16, quad = (i / 4) % 4;
-            const uint32_t o = grp * 16 + ((quad ^ ((grp >> 1) & 3u)) * 4) + (i % 4);
+            v = (pc_swz(v >> 16) << 16) | (v & 0xFFFFu);
+            const uint32_t r0 = i / kPcRound * kPcRound;
+            const uint32_t o = r0 + pc_round_pos(i - r0, min(kPcRound, PL - r0));
             pe2[b + o] = v;
             if (pw2) pw2[b + o] = w;
         }
@@ -763,27 +790,36 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         // destination boundaries
         constexpr uint32_t kSp = kPcGatherWarps + 1;
         {
-            std::vector<uint32_t> tsp(stasks.size()), rlo, rhi;
+            std::vector<uint32_t> tsp(stasks.size() + 1), rlo, rhi, rtask;
             for (size_t ti = 0; ti < stasks.size(); ++ti) {
                 tsp[ti] = (uint32_t)rlo.size();
                 const uint4 tk = stasks[ti];
                 for (uint32_t b = tk.y; b < tk.z; ++b) {
                     rlo.push_back(b == tk.y ? srng[ti].x : hbe[b]);
                     rhi.push_back(b + 1 == tk.z ? srng[ti].y : hbe[b + 1]);
+                    rtask.push_back((uint32_t)ti);
                 }
             }
-            const uint32_t nrow = (uint32_t)rlo.size();
-            uint32_t *d_lo, *d_hi;
+            tsp[stasks.size()] = (uint32_t)rlo.size();
+            const uint32_t nrow = (uint32_t)rlo.size(), ntask = (uint32_t)stasks.size();
+            uint32_t *d_lo, *d_hi, *d_rtask, *d_row0, *d_cut;
             GPOP_CUDA_TRY(t.alloc(&d_lo, (uint64_t)nrow + 1));
             GPOP_CUDA_TRY(t.alloc(&d_hi, (uint64_t)nrow + 1));
+            GPOP_CUDA_TRY(t.alloc(&d_rtask, (uint64_t)nrow + 1));
+            GPOP_CUDA_TRY(t.alloc(&d_row0, (uint64_t)ntask + 1));
+            GPOP_CUDA_TRY(t.alloc(&d_cut, (uint64_t)ntask * (kPcGatherWarps - 1) + 1));
             GPOP_CUDA_TRY(dalloc(g, &g->pc_wsp, (uint64_t)nrow * kSp + 1));
-            GPOP_CUDA_TRY(dalloc(g, &g->pc_tsp, (uint64_t)tsp.size() + 1));
+            GPOP_CUDA_TRY(dalloc(g, &g->pc_tsp, (uint64_t)ntask + 1));
             if (nrow) {
                 GPOP_CUDA_TRY(cudaMemcpyAsync(d_lo, rlo.data(), 4ull * nrow, cudaMemcpyHostToDevice, s));
                 GPOP_CUDA_TRY(cudaMemcpyAsync(d_hi, rhi.data(), 4ull * nrow, cudaMemcpyHostToDevice, s));
-                GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_tsp, tsp.data(), 4ull * tsp.size(), cudaMemcpyHostToDevice, s));
-                k_warp_splits<<<blocks_for((uint64_t)nrow * kSp), kThreads, 0, s>>>(nrow, d_lo, d_hi, g->pe,
-                                                                                    g->pc_wsp);
+                GPOP_CUDA_TRY(cudaMemcpyAsync(d_rtask, rtask.data(), 4ull * nrow, cudaMemcpyHostToDevice, s));
+                GPOP_CUDA_TRY(cudaMemcpyAsync(d_row0, tsp.data(), 4ull * (ntask + 1), cudaMemcpyHostToDevice, s));
+                GPOP_CUDA_TRY(cudaMemcpyAsync(g->pc_tsp, tsp.data(), 4ull * ntask, cudaMemcpyHostToDevice, s));
+                k_task_cuts<<<blocks_for((uint64_t)ntask * (kPcGatherWarps - 1)), kThreads, 0, s>>>(
+                    ntask, g->P, d_row0, d_lo, d_hi, g->pe, d_cut);
+                k_warp_splits<<<blocks_for((uint64_t)nrow * kSp), kThreads, 0, s>>>(nrow, d_lo, d_hi, d_rtask, d_cut,
+                                                                                    g->pe, g->pc_wsp);
             }
             // re-lay the entries so that every warp range starts 16-aligned and is padded to kPcPad
             std::vector<uint32_t> sp((size_t)nrow * kSp);

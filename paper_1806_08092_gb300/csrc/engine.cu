@@ -52,17 +52,13 @@ constexpr uint32_t kSent = 0xFFFFFFFFu;
 constexpr uint32_t kScUnitEdges = 1u << 12;  // active edges per SC scatter unit of a split partition
 constexpr uint32_t kBigScBin = 2048;     // SC bins at least this large are folded by the whole gather CTA
 constexpr uint32_t kMaxBigScBins = 64;
-constexpr int kPcWarps = kPcGatherWarps;          // k_gather_pc warps (one destination slice of a block each)
-constexpr int kPcThreads = 32 * kPcWarps;
-constexpr uint32_t kPcMaxSlots = 3;               // entry ring depth limit per warp
-constexpr uint32_t kPcSpinLimit = 1u << 24;       // bounded mbarrier waits
-// destination entries a lane folds serially per round (SSSP also stages weights: half as many)
-template <int ALGO>
-struct PcShape {
-    static constexpr uint32_t K = ALGO == ALG_SSSP ? 8 : 16;
-    static constexpr uint32_t kRound = 32 * K;  // entries per warp round
-    static constexpr uint32_t kSlotWords = kRound * (ALGO == ALG_SSSP ? 2 : 1);
-};
+constexpr int kPcWarps = kPcGatherWarps;          // k_gather_pc consumer warps (one destination slice of a block each)
+constexpr int kPcThreads = 32 * (kPcWarps + 1);   // + the producer warp
+constexpr uint32_t kPcMaxBufs = 4;                // value buffers of k_gather_pc (blocks staged ahead)
+constexpr uint32_t kPcSpinLimit = 1u << 24;       // tries of a bounded mbarrier wait
+constexpr unsigned long long kPcWaitNs = 2000000000ull;  // ... and its time limit (2 s)
+constexpr uint32_t kPcSleepNs = 20000;            // k_gather_pc: a waiting warp sleeps up to 20 us per try
+static_assert(kPcRound == 32 * 16, "a full round gives each lane 16 entries");
 
 struct Params {
     // graph
@@ -89,7 +85,7 @@ struct Params {
     uint32_t npct;
     const uint2 *pc_merge;  // merge items of split columns
     uint32_t nmerge;
-    uint32_t pc_slots;  // entry ring slots per consumer warp of k_gather_pc (2..kPcMaxSlots)
+    uint32_t pc_nbuf;   // value buffers of k_gather_pc (2..kPcMaxBufs)
     uint32_t *pc_sum;  // per vertex: combined PC message of the iteration (single-task columns)
     const uint32_t *Ep, *npng_p;
     const GatherTask *gtask;
@@ -618,14 +614,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Waits for the completion of the barrier phase with the given parity, at most kPcSpinLimit tries;
-// gives up early when another warp has raised *abort, and raises it (with the run's error flag) when
-// its own tries run out.  Returns false when the caller must stop.
+// One try with a suspend-time hint: the thread sleeps until the phase completes or about ns nanoseconds
+// pass, instead of returning after the hardware's own short limit (so a waiting warp issues almost nothing)
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the completion of the barrier phase with the given parity: at most `limit` tries (each one
+// sleeping up to sleep_ns, or the hardware's own limit when sleep_ns is 0) and at most kPcWaitNs in all;
+// gives up early when another warp has raised *abort, and raises it (with the run's error flag) when its
+// own tries or time run out.  Returns false when the caller must stop.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort, uint32_t *err,
-                                          uint32_t limit = kPcSpinLimit) {
+                                          uint32_t limit = kPcSpinLimit, uint32_t sleep_ns = 0) {
+    unsigned long long t0 = 0;
     for (uint32_t it = 0; it < limit; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (sleep_ns ? mbar_try_wait_sleep(bar, parity, sleep_ns) : mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
+        const unsigned long long now = globaltimer();
+        if (it == 0) t0 = now;
+        else if (now - t0 > kPcWaitNs) break;
     }
     *abort = 1;
     atomicOr(err, 1u);
@@ -936,346 +948,470 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
 // --- gather + filter ---------------------------------------------------------------------------
 
 
-// Position in one warp's entry stream through a PC gather task: block i (relative to the
-// task's first block), next entry s.  sp[i * (kPcWarps + 1) + w] .. [.. + w + 1] bound warp w's entries in
-// block i; blocks where the warp has none are skipped.
-struct PcCursor {
-    uint32_t i, s;
-};
-__device__ __forceinline__ void pc_skip_empty(const uint32_t *sp, uint32_t nb, int w, PcCursor &c) {
-    while (c.i < nb && c.s >= sp[c.i * (kPcWarps + 1) + w + 1]) {
-        ++c.i;
-        if (c.i < nb) c.s = sp[c.i * (kPcWarps + 1) + w];
-    }
+// 32-bit shared-memory accesses at explicit shared addresses (the fold's addresses stay 32-bit; volatile
+// keeps them in program order, which the read-modify-writes of consecutive rounds rely on).  The _if forms
+// do nothing at the address 0xFFFFFFFF (no shared address).
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
 }
-// A round covers entries [s, min(s + C, end of the warp's range)); ranges start 16-aligned and are
-// padded to a multiple of kPcPad, so every round is a whole number of 16-entry groups.
-template <uint32_t C>
-__device__ __forceinline__ uint32_t pc_round_end(const uint32_t *sp, int w, const PcCursor &c) {
-    return min(c.s + C, sp[c.i * (kPcWarps + 1) + w + 1]);
+__device__ __forceinline__ uint32_t lds16(uint32_t a) {
+    uint16_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) { asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v)); }
+__device__ __forceinline__ uint32_t lds32_if(uint32_t a) {
+    uint32_t v;
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %1, -1;\n mov.u32 %0, 0;\n @q ld.shared.u32 %0, [%1];\n}\n"
+                 : "=r"(v)
+                 : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts32_if(uint32_t a, uint32_t v) {
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, -1;\n @q st.shared.u32 [%0], %1;\n}\n" ::"r"(a), "r"(v));
 }
 
-// Serial fold of one lane's K entries (round positions j0 .. j0+K-1), in batches of 8: the batch's
-// message values are loaded first (independent shared loads), runs of equal destination are then found
-// in registers, and the complete inner runs are folded into acc with batched, branch-free
-// read-modify-writes (inner runs of a lane have distinct destinations, and no other lane or warp touches
-// them; positions that end no inner run update the scratch word sink; shared atomics measured slower).
-// Padding entries repeat their range's last destination and read the padding value slot (the identity),
-// so they fold as no-ops.
-template <int ALGO, bool B16, uint32_t K>
-__device__ __forceinline__ void pc_lane(const uint32_t *ent, const uint32_t *wgt, uint32_t j0, const uint32_t *stage,
-                                        uint32_t *acc, uint32_t *sink, bool check_null, uint32_t &fd,
-                                        uint32_t &head, uint32_t &run_d, uint32_t &run_v, bool &in_head) {
+// Serial fold of one lane's K destination entries (its K consecutive positions of the round, held in
+// registers as K / 4 quads), in batches of 8: the batch's message values are loaded first (independent
+// shared loads), runs of equal destination are then found in registers, and the complete inner runs are
+// folded into the accumulator with batched, predicated read-modify-writes (inner runs of a lane have
+// distinct destinations, and no other lane or warp touches them).  Entries are sorted by destination, so a
+// position belongs to the lane's first run exactly when its destination is the first one, fd; head follows
+// that run's value.  Padding entries repeat their range's last destination and read the padding value slot
+// (the identity), so they fold as no-ops.  NULL messages are skipped when NUL (SSSP, PPR, Nibble, and
+// PageRank while some partition is not PC); SSSP adds each entry's edge weight (applyWeight of Alg. 7).
+// stage and acc are shared-memory addresses.
+template <int ALGO, bool B16, uint32_t K, bool NUL>
+__device__ __forceinline__ void pc_lane(const uint4 (&E)[4], const int4 (&W)[4], uint32_t stage, uint32_t acc,
+                                        uint32_t &fd, uint32_t &head, uint32_t &run_d, uint32_t &run_v) {
     using O = Op<ALGO>;
-    static_assert(K == 4 || K % 8 == 0, "a lane folds whole quads of a 16-entry group, 8 entries per batch");
+    static_assert(K == 4 || K == 8 || K == 16, "lanes fold 4, 8 or 16 entries per round");
     constexpr uint32_t HB = K < 8 ? K : 8;  // entries per batch
-    // quads of a 16-entry group are stored swizzled by (group >> 1) & 3 (see the build); the lane's
-    // entries start at round position j0, in group j0 / 16
-    const uint32_t gbase = j0 & ~15u, qsw = ((j0 >> 5) & 3u), q0 = (j0 & 15u) >> 2;
-    const bool nullable = ALGO == ALG_SSSP || ALGO == ALG_PPR || ALGO == ALG_NIBBLE || (ALGO == ALG_PR && check_null);
 #pragma unroll
     for (uint32_t hb = 0; hb < K; hb += HB) {
         uint32_t ee[HB];
         int32_t ww[HB];
 #pragma unroll
         for (uint32_t qq = 0; qq < HB / 4; ++qq) {
-            const uint32_t o = gbase + (((q0 + hb / 4 + qq) ^ qsw) << 2);
-            const uint4 e4 = *reinterpret_cast<const uint4 *>(ent + o);
+            const uint4 e4 = E[hb / 4 + qq];
             ee[4 * qq] = e4.x; ee[4 * qq + 1] = e4.y; ee[4 * qq + 2] = e4.z; ee[4 * qq + 3] = e4.w;
-            if (ALGO == ALG_SSSP) {
-                const int4 w4 = *reinterpret_cast<const int4 *>(wgt + o);
-                ww[4 * qq] = w4.x; ww[4 * qq + 1] = w4.y; ww[4 * qq + 2] = w4.z; ww[4 * qq + 3] = w4.w;
-            } else {
-                ww[4 * qq] = ww[4 * qq + 1] = ww[4 * qq + 2] = ww[4 * qq + 3] = 0;
-            }
+            const int4 w4 = W[hb / 4 + qq];
+            ww[4 * qq] = w4.x; ww[4 * qq + 1] = w4.y; ww[4 * qq + 2] = w4.z; ww[4 * qq + 3] = w4.w;
         }
-        uint32_t d[HB], x[HB];
+        uint32_t x[HB];
 #pragma unroll
         for (uint32_t i = 0; i < HB; ++i) {
-            d[i] = ee[i] >> 16;
             if (B16) {  // BF16 values staged as 16-bit words
-                const uint32_t h = reinterpret_cast<const uint16_t *>(stage)[ee[i] & 0xFFFFu];
-                x[i] = (nullable && h == kNull16) ? kNull : from_bf16(h);
+                const uint32_t h = lds16(stage + (ee[i] & 0xFFFFu) * 2u);
+                x[i] = (NUL && h == kNull16) ? kNull : from_bf16(h);
             } else {
-                x[i] = stage[ee[i] & 0xFFFFu];
+                x[i] = lds32(stage + (ee[i] & 0xFFFFu) * 4u);
             }
         }
-        bool fl[HB];
-        uint32_t fk[HB], fv[HB];
+        // ra: accumulator word of an inner run that ends at this position, or kNoRun
+        constexpr uint32_t kNoRun = 0xFFFFFFFFu;
+        uint32_t ra[HB], fv[HB];
 #pragma unroll
         for (uint32_t i = 0; i < HB; ++i) {
             // NULL (0xFFFFFFFF) is the identity of min and of AND, so BFS, CC and multi-source BFS fold it as is
-            const uint32_t v = (!nullable || x[i] != kNull) ? O::weigh(x[i], ww[i]) : O::identity();
+            const uint32_t v = (!NUL || x[i] != kNull) ? O::weigh(x[i], ww[i]) : O::identity();
+            const uint32_t d = ee[i] >> 16;
             if (hb == 0 && i == 0) {
-                fd = run_d = d[0];
+                fd = run_d = d;
                 run_v = v;
-                fl[0] = false;
+                ra[0] = kNoRun;
+                fv[0] = O::identity();
                 continue;
             }
-            const bool ch = d[i] != run_d;
-            fl[i] = ch && !in_head;
-            fk[i] = run_d;
+            const bool ch = d != run_d, first = run_d == fd;
+            ra[i] = (ch && !first) ? acc + run_d * 4u : kNoRun;
             fv[i] = run_v;
-            head = (ch && in_head) ? run_v : head;
-            in_head = in_head && !ch;
+            head = first ? run_v : head;
             const uint32_t joined = O::combine(run_v, v);
             run_v = ch ? v : joined;
-            run_d = d[i];
+            run_d = d;
         }
-        // branch-free read-modify-writes: positions that end no inner run update a scratch word
-        uint32_t *dst[HB], old[HB];
+        // read-modify-writes of the inner runs that end in this batch
+        uint32_t old[HB];
 #pragma unroll
-        for (uint32_t i = 0; i < HB; ++i) dst[i] = fl[i] ? acc + fk[i] : sink;
+        for (uint32_t i = 0; i < HB; ++i) old[i] = lds32_if(ra[i]);
 #pragma unroll
-        for (uint32_t i = 0; i < HB; ++i) old[i] = *dst[i];
-#pragma unroll
-        for (uint32_t i = 0; i < HB; ++i) *dst[i] = O::combine(old[i], fv[i]);
+        for (uint32_t i = 0; i < HB; ++i) sts32_if(ra[i], O::combine(old[i], fv[i]));
     }
 }
 
-// One warp round: n <= 32 K round positions (a multiple of 16), sorted by destination, all inside this
-// warp's destination slice of the block.  Lane l folds positions [l K, (l+1) K) serially; one segmented warp
-// scan, keyed by destination, joins the lanes' last runs, and a lane's first run takes the scan value of
-// the lane before it when they share the destination.  Every complete run is folded into acc directly:
+// One warp round: n <= kPcRound positions (a multiple of 16), sorted by destination, all inside this
+// warp's destination slice of the block, folded by the n / K lanes that hold them.  A lane's last run is
+// continued by the next lane's first run when they share the destination: the next lane adds it to its
+// first run and writes the sum, unless its whole range is that run, in which case one segmented warp scan
+// (keyed by destination) carries the sum on.  Every complete run is folded into the accumulator directly:
 // a run cut by the round's end continues in the warp's next round, folded after this part.
-template <int ALGO, bool B16, uint32_t K>
-__device__ __forceinline__ void pc_round(const uint32_t *ent, const uint32_t *wgt, uint32_t n, const uint32_t *stage,
-                                         uint32_t *acc, uint32_t *sink, bool check_null, int lane) {
+template <int ALGO, bool B16, uint32_t K, bool NUL>
+__device__ __forceinline__ void pc_round(const uint4 (&E)[4], const int4 (&W)[4], uint32_t n, uint32_t stage,
+                                         uint32_t acc, int lane) {
     using O = Op<ALGO>;
-    const uint32_t j0 = lane * K;
     uint32_t fd = kSent, head = O::identity(), run_d = kSent, run_v = O::identity();
-    bool in_head = true;
-    if (j0 < n) pc_lane<ALGO, B16, K>(ent, wgt, j0, stage, acc, sink, check_null, fd, head, run_d, run_v, in_head);
-    const bool uni = in_head;  // all K positions share one destination
+    if ((uint32_t)lane * K < n) pc_lane<ALGO, B16, K, NUL>(E, W, stage, acc, fd, head, run_d, run_v);
     const uint32_t ld = run_d;
+    const bool uni = ld == fd;  // all K positions share one destination (or the lane is idle: kSent)
     uint32_t S = run_v;
+    if (__any_sync(0xffffffffu, uni && ld != kSent)) {  // a run spans a whole lane: scan
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t vu = __shfl_up_sync(0xffffffffu, S, o);
-        const uint32_t du = __shfl_up_sync(0xffffffffu, ld, o);
-        if (lane >= o && du == ld) S = O::combine(vu, S);
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t vu = __shfl_up_sync(0xffffffffu, S, o);
+            const uint32_t du = __shfl_up_sync(0xffffffffu, ld, o);
+            if (lane >= o && du == ld) S = O::combine(vu, S);
+        }
     }
     const uint32_t prev_S = __shfl_up_sync(0xffffffffu, S, 1);
     const uint32_t prev_d = __shfl_up_sync(0xffffffffu, ld, 1);
     const uint32_t next_fd = __shfl_down_sync(0xffffffffu, fd, 1);
     if (!uni && fd != kSent) {  // first run ends inside this lane
         const uint32_t hv = (lane > 0 && prev_d == fd) ? O::combine(prev_S, head) : head;
-        acc[fd] = O::combine(acc[fd], hv);
+        const uint32_t a = acc + fd * 4u;
+        sts32(a, O::combine(lds32(a), hv));
     }
-    if (ld != kSent && (lane == 31 || next_fd != ld)) acc[ld] = O::combine(acc[ld], S);  // last run ends here
+    if (ld != kSent && (lane == 31 || next_fd != ld)) {  // last run ends here
+        const uint32_t a = acc + ld * 4u;
+        sts32(a, O::combine(lds32(a), S));
+    }
 }
 
-// Issues the bulk copies of a block's message values into a value buffer: its bin runs (row-major source
-// slot, length, offset in the block; all multiples of 4 values, so 16-byte aligned) are dealt to the
-// warps round-robin, one run per lane; thread 0 arms the buffer's "full" mbarrier with the block's byte
-// count.  first is this lane's descriptor of the first batch, loaded one block ahead.
+// Loads lane `lane`'s entries (and SSSP weights) of the round [s, s + n) of the lane-interleaved layout:
+// quad j of the lane at s + (j * n / K + lane) * 4, K = pc_round_k(n); lanes past n / K and quads past
+// K / 4 get zeros (never folded).  Streamed once: no L1 allocation.
+__device__ __forceinline__ uint4 ldg_stream(const uint32_t *ptr) {
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(ptr));
+    return r;
+}
+__device__ __forceinline__ void pc_load_round(const uint32_t *base, uint32_t s, uint32_t n, int lane, uint4 (&R)[4]) {
+    const uint32_t K = pc_round_k(n), nl = n / K;
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j)
+        R[j] = (j < K / 4 && (uint32_t)lane < nl) ? ldg_stream(base + s + (j * nl + (uint32_t)lane) * 4)
+                                                  : make_uint4(0, 0, 0, 0);
+}
+// Bulk prefetch of [ptr, ptr + bytes) into L2 (one instruction, no completion to wait for): 16-byte aligned
+// address, size a multiple of 16
+__device__ __forceinline__ void bulk_prefetch_l2(const void *ptr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(ptr), "r"(bytes) : "memory");
+}
+
+// Barrier 1 joins the consumer warps of k_gather_pc (the producer warp never takes part)
+__device__ __forceinline__ void pc_consumers_sync() {
+    asm volatile("bar.sync 1, %0;\n" ::"n"(kPcGatherWarps * 32) : "memory");
+}
+// the same barrier, returning whether any consumer thread passed a true predicate
+__device__ __forceinline__ bool pc_consumers_or(bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "n"(kPcGatherWarps * 32)
+        : "memory");
+    return r != 0;
+}
+
+// A PC gather task handed from the producer warp to the consumer warps of k_gather_pc
+struct PcSlot {
+    uint4 tk;                                   // column, first block, end block, partial slot (or kNull)
+    uint32_t state;                             // 1: a task, 2: no task left
+    uint32_t nb, na;                            // blocks of the task, blocks holding a PC message this iteration
+    uint32_t run[kPcTaskBlocks + 1];            // bin runs of each block
+    uint32_t nval[kPcTaskBlocks];               // staged values of each block
+    uint32_t sp[kPcTaskBlocks * (kPcGatherWarps + 1)];  // each block's entry splits, one range per consumer warp
+    uint32_t blist[kPcTaskBlocks];              // the active blocks, in order
+};
+
+// Copies n words from global to shared memory with one warp, 16 loads in flight per lane
+__device__ __forceinline__ void warp_copy(uint32_t *dst, const uint32_t *src, uint32_t n, int lane) {
+    constexpr uint32_t U = 16;
+    for (uint32_t i0 = 0; i0 < n; i0 += 32 * U) {
+        uint32_t v[U];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) {
+            const uint32_t i = i0 + u * 32 + (uint32_t)lane;
+            v[u] = i < n ? src[i] : 0u;
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) {
+            const uint32_t i = i0 + u * 32 + (uint32_t)lane;
+            if (i < n) dst[i] = v[u];
+        }
+    }
+}
+
+// Producer warp of k_gather_pc: takes the tasks (largest first, from a device counter), describes each one
+// in a task slot for the consumers, and stages the message values of the task's active blocks, one block
+// per value buffer: once the consumers have released the buffer (its "empty" mbarrier), the block's bin
+// runs are bulk-copied (TMA) into it, counted in on its "full" mbarrier.  The bins are read in order, as
+// the paper's gather streams bin[:][q].  Waits are bounded; an abort stops the issue and every copy still
+// in flight is waited out before the warp leaves.
 template <bool B16>
-__device__ __forceinline__ void pc_issue_values(const Params &p, uint32_t r0, uint32_t r1, uint32_t nval, uint4 first,
-                                                uint32_t *st, uint64_t *full, int lane, int wid) {
-    constexpr uint32_t kB = B16 ? 2u : 4u;  // bytes per staged value
-    if (threadIdx.x == 0) mbar_arrive_expect_tx(full, nval * kB);
-    for (uint32_t rb = r0 + wid, it = 0; rb < r1; rb += 32u * kPcWarps, ++it) {
-        const uint32_t rr = rb + (uint32_t)lane * kPcWarps;
-        const uint4 run = it == 0 ? first : (rr < r1 ? p.pc_runs[rr] : make_uint4(0, 0, 0, 0));
-        if (rr < r1)
-            bulk_g2s(reinterpret_cast<char *>(st) + (size_t)run.z * kB,
-                     reinterpret_cast<const char *>(p.pdata) + (size_t)run.x * kB, run.y * kB, full);
-    }
-}
-__device__ __forceinline__ uint4 pc_first_run(const Params &p, uint32_t r0, uint32_t r1, int lane, int wid) {
-    const uint32_t rr = r0 + wid + (uint32_t)lane * kPcWarps;
-    return rr < r1 ? p.pc_runs[rr] : make_uint4(0, 0, 0, 0);
-}
-
-// PC part of the gather (Alg. 2 gather over the PC bins, Sec. 3.1.2): one CTA per task (a range of
-// consecutive entries of column q's blocks), one task at a time per CTA, largest tasks first.
-//  * A block's message values are copied from the data bins into one of two shared buffers by bulk
-//    copies (TMA) of its bin runs (the bins are read in order, as the paper's gather streams bin[:][q]),
-//    issued while the previous block is being reduced; a "full" mbarrier counts the bytes in.
-//  * Within a block, warp w takes the w-th of 16 entry ranges of about equal size, cut at destination
-//    boundaries and padded to whole 16-entry groups when the graph is built, so no two warps touch one
-//    destination of the block.  Each warp streams its entries through its own ring of rounds, one bulk
-//    copy and one mbarrier per round, several rounds ahead (across block boundaries), and folds them into
-//    the shared column accumulator with lane-serial runs and a segmented warp scan: random accesses touch
-//    shared memory only.  One CTA barrier per block separates the blocks' slices and frees the block's
-//    value buffer.
-// The accumulator stays in shared memory for the whole task; a column split over several tasks writes
-// one partial vector per task.  Every mbarrier wait is bounded: when one runs out, the run's error flag
-// is raised and all warps leave.
-template <int ALGO, bool B16>
-__global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
-    const bool pc_skip = p.pc_skip != 0;  // some partition is not PC: skip blocks whose sources all are not
-    using O = Op<ALGO>;
-    constexpr uint32_t C = PcShape<ALGO>::kRound, kSlotWords = PcShape<ALGO>::kSlotWords;
-    constexpr uint32_t kSp = kPcWarps + 1, kStageWords = kPcBlock + 4;
-    extern __shared__ __align__(16) uint32_t s_pc_dyn[];
-    uint32_t *acc = s_pc_dyn;                     // P values of the column
-    uint32_t *stage = s_pc_dyn + p.P;             // 2 x (kPcBlock message values + the NULL slot)
-    uint32_t *rings = stage + 2 * kStageWords;    // kPcWarps x pc_slots rounds (entries, then SSSP weights)
-    __shared__ __align__(8) uint64_t s_full[2];
-    __shared__ __align__(8) uint64_t s_slot[kPcWarps * kPcMaxSlots];  // one barrier per ring slot
-    __shared__ uint32_t s_state, s_abort, s_sink;  // s_sink: target of the no-op read-modify-writes
-    __shared__ uint4 s_tk;
-    __shared__ uint32_t s_tsp;
-    __shared__ uint32_t s_run[kPcTaskBlocks + 1], s_nval[kPcTaskBlocks];
-    __shared__ uint32_t s_sp[kPcTaskBlocks * kSp];
-    __shared__ uint32_t s_blist[kPcTaskBlocks], s_na;  // blocks with a PC source this iteration
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t ns = p.pc_slots;
-    uint32_t *ring = rings + (uint32_t)wid * ns * kSlotWords;
-    uint64_t *sbar = s_slot + wid * kPcMaxSlots;
-    if (threadIdx.x == 0) {
-        mbar_init(&s_full[0], 1);
-        mbar_init(&s_full[1], 1);
-        for (int i = 0; i < kPcWarps * (int)kPcMaxSlots; ++i) mbar_init(&s_slot[i], 1);
-        fence_mbar_init();
-        s_abort = 0;
-        // value slot of the padding entries (the copies never write it): the monoid identity, so padding
-        // folds as a no-op whether or not NULLs are checked
-        if (B16) {  // BF16 only carries sums: the identity is +0
-            reinterpret_cast<uint16_t *>(stage)[kPcPadIdx] = 0;
-            reinterpret_cast<uint16_t *>(stage + kStageWords)[kPcPadIdx] = 0;
-        } else {
-            stage[kPcPadIdx] = O::identity();
-            stage[kStageWords + kPcPadIdx] = O::identity();
-        }
-    }
-    const unsigned long long t_start = p.t_gpc ? globaltimer() : 0ull;
-    uint32_t gb = 0;         // blocks this CTA has passed through (buffer = gb & 1, use = gb >> 1)
-    uint32_t ph = 0;         // this warp's ring slot phases (bit per slot)
-    uint32_t head_slot = 0;  // this warp's next slot to fold; rounds in flight follow it
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const uint32_t t = atomicAdd(&p.counters[5], 1u);
-            uint32_t state = 2;  // 0 idle column, 1 work, 2 no tasks left (or abort)
-            if (t < p.npct && !s_abort) {
-                const uint4 tk = p.pc_task[t];  // column, first block, end block, partial slot
-                state = p.gflag_pc[tk.x] == p.epoch ? 1u : 0u;
-                s_tk = tk;
-                s_tsp = p.pc_tsp[t];
-            }
-            s_state = state;
-        }
-        __syncthreads();
-        const uint32_t state = s_state;
-        const uint4 tk = s_tk;
-        if (state == 2) break;
-        if (state == 0) {
-            __syncthreads();
-            continue;
-        }
-        const uint32_t nb = tk.z - tk.y;
-        if (threadIdx.x <= nb) s_run[threadIdx.x] = p.pc_blk_run[tk.y + threadIdx.x];
-        if (threadIdx.x < nb) s_nval[threadIdx.x] = p.pc_blk_nval[tk.y + threadIdx.x];
-        for (uint32_t i = threadIdx.x; i < nb * kSp; i += kPcThreads) s_sp[i] = p.pc_wsp[(uint64_t)s_tsp * kSp + i];
-        const uint32_t gq = tk.x << p.shift;
-        const uint32_t wq = min(p.P, p.V - gq);
-        // a block only holds NULLs unless one of its source partitions sent PC messages this iteration
-        if (threadIdx.x < nb) {
-            const uint2 pr = pc_skip ? p.pc_blk_prange[tk.y + threadIdx.x] : make_uint2(0, 0);
-            s_blist[threadIdx.x] = !pc_skip || p.pc_prefix[pr.y + 1] != p.pc_prefix[pr.x];
-        }
-        for (uint32_t i = threadIdx.x; i < wq; i += kPcThreads) acc[i] = O::identity();
-        __syncthreads();
-        if (threadIdx.x == 0) {  // list the active blocks in order; empty the warp ranges of the others
-            uint32_t na = 0;
-            for (uint32_t i = 0; i < nb; ++i) {
-                if (s_blist[i]) {
-                    s_blist[na++] = i;
-                } else {
-                    for (uint32_t w = 1; w < kSp; ++w) s_sp[i * kSp + w] = s_sp[i * kSp];
-                }
-            }
-            s_na = na;
-        }
-        __syncthreads();
-        const uint32_t na = s_na;
-        if (na > 0)
-            pc_issue_values<B16>(p, s_run[s_blist[0]], s_run[s_blist[0] + 1], s_nval[s_blist[0]],
-                            pc_first_run(p, s_run[s_blist[0]], s_run[s_blist[0] + 1], lane, wid),
-                            stage + (gb & 1) * kStageWords, &s_full[gb & 1], lane, wid);
-        uint4 next_run = na > 1 ? pc_first_run(p, s_run[s_blist[1]], s_run[s_blist[1] + 1], lane, wid)
-                                : make_uint4(0, 0, 0, 0);
-        PcCursor pc{0, s_sp[wid]};
-        pc_skip_empty(s_sp, nb, wid, pc);
-        PcCursor cc = pc;
-        uint32_t inflight = 0;  // rounds issued and not yet folded
-        bool ok = true, abort = false;
-        uint32_t j = 0;  // active blocks only: each one takes a value buffer and a barrier phase
-        for (; j < na && !abort; ++j) {
-            const uint32_t i = s_blist[j];
-            const uint32_t g = gb + j, buf = g & 1, use = g >> 1;
-            if (j + 1 < na) {  // the next block's values go to the other buffer, freed by the last barrier
-                const uint32_t i1 = s_blist[j + 1];
-                pc_issue_values<B16>(p, s_run[i1], s_run[i1 + 1], s_nval[i1], next_run,
-                                stage + (buf ^ 1) * kStageWords, &s_full[buf ^ 1], lane, wid);
-                if (j + 2 < na) next_run = pc_first_run(p, s_run[s_blist[j + 2]], s_run[s_blist[j + 2] + 1], lane, wid);
-            }
-            if (ok && cc.i == i && !mbar_wait(&s_full[buf], use & 1, &s_abort, &p.ctrl->error)) ok = false;
-            while (ok && cc.i == i) {
-                while (inflight < ns && pc.i < nb) {  // keep the ring full: one bulk copy per round
-                    const uint32_t e = pc_round_end<C>(s_sp, wid, pc);
-                    uint32_t sl = head_slot + inflight;
-                    sl = sl >= ns ? sl - ns : sl;
-                    if (lane == 0) {
-                        const uint32_t bytes = (e - pc.s) * 4u;
-                        uint32_t *dst = ring + sl * kSlotWords;
-                        mbar_arrive_expect_tx(&sbar[sl], ALGO == ALG_SSSP ? 2 * bytes : bytes);
-                        bulk_g2s(dst, p.pe + pc.s, bytes, &sbar[sl]);
-                        if (ALGO == ALG_SSSP) bulk_g2s(dst + C, p.pw + pc.s, bytes, &sbar[sl]);
-                    }
-                    ++inflight;
-                    pc.s = e;
-                    pc_skip_empty(s_sp, nb, wid, pc);
-                }
-                if (!mbar_wait(&sbar[head_slot], (ph >> head_slot) & 1u, &s_abort, &p.ctrl->error)) {
-                    ok = false;
-                    break;
-                }
-                ph ^= 1u << head_slot;
-                const uint32_t e = pc_round_end<C>(s_sp, wid, cc);
-                const uint32_t *slot = ring + head_slot * kSlotWords;
-                // a short round (the tail of a warp's slice) is spread over all lanes: 8 or 4 positions
-                // per lane instead of K
-                constexpr uint32_t K = PcShape<ALGO>::K;
-                const uint32_t n = e - cc.s;
-                const uint32_t *vals = stage + buf * kStageWords;
-                const bool chk = pc_skip;
-                if (n <= 128) {
-                    pc_round<ALGO, B16, 4>(slot, slot + C, n, vals, acc, &s_sink, chk, lane);
-                } else if (K == 16 && n <= 256) {
-                    pc_round<ALGO, B16, 8>(slot, slot + C, n, vals, acc, &s_sink, chk, lane);
-                } else {
-                    pc_round<ALGO, B16, K>(slot, slot + C, n, vals, acc, &s_sink, chk, lane);
-                }
-                __syncwarp();  // the slot is refilled only after every lane has read it
-                --inflight;
-                head_slot = head_slot + 1 == ns ? 0 : head_slot + 1;
-                cc.s = e;
-                pc_skip_empty(s_sp, nb, wid, cc);
-            }
-            // every block of a task has entries, so some warp has waited for the values before this
-            // barrier, after which the buffer may be refilled; all warps learn of an abort here
-            abort = __syncthreads_or(!ok) != 0;
-        }
-        if (abort) {  // let every copy still in flight land, then leave
-            const uint32_t last = gb + j - 1;  // block whose barrier saw the abort
-            for (uint32_t k = 0; k < inflight; ++k) {
-                const uint32_t sl = head_slot + k >= ns ? head_slot + k - ns : head_slot + k;
-                mbar_drain(&sbar[sl], (ph >> sl) & 1u);
-            }
-            if (threadIdx.x == 0) {
-                mbar_drain(&s_full[last & 1], (last >> 1) & 1u);
-                if (j < na) mbar_drain(&s_full[(last + 1) & 1], ((last + 1) >> 1) & 1u);
-            }
-            __syncthreads();
+__device__ void pc_producer(const Params &p, PcSlot *slots, uint64_t *full, uint64_t *empty, uint64_t *tfull,
+                            uint64_t *tempty, uint32_t *stage, uint32_t nbuf, volatile uint32_t *abort, int lane) {
+    constexpr uint32_t kB = B16 ? 2u : 4u, kSp = kPcGatherWarps + 1, kStageWords = kPcBlock + 4;
+    const bool pc_skip = p.pc_skip != 0;
+    uint32_t issued = 0;  // blocks staged so far: buffer issued % nbuf, use issued / nbuf
+    bool ok = true;
+    for (uint32_t n = 0; ok; ++n) {  // n: tasks handed over
+        const uint32_t ts = n & 1;
+        PcSlot &sl = slots[ts];
+        if (n >= 2 && !__all_sync(0xffffffffu, mbar_wait(&tempty[ts], ((n >> 1) - 1) & 1u, abort, &p.ctrl->error, kPcSpinLimit, kPcSleepNs))) {
+            ok = false;
             break;
         }
-        gb += na;
-        __syncthreads();
-        uint32_t *out = (tk.w == kNull) ? p.pc_sum + gq : p.pc_part + (uint64_t)tk.w * p.P;
-        for (uint32_t i = threadIdx.x; i < wq; i += kPcThreads) out[i] = acc[i];
+        uint32_t state = 2, t = 0;
+        uint4 tk = make_uint4(0, 0, 0, 0);
+        if (lane == 0) {
+            for (;;) {  // the next task whose column received PC messages this iteration
+                t = atomicAdd(&p.counters[5], 1u);
+                if (t >= p.npct || *abort) break;
+                tk = p.pc_task[t];
+                if (p.gflag_pc[tk.x] == p.epoch) {
+                    state = 1;
+                    break;
+                }
+            }
+        }
+        state = __shfl_sync(0xffffffffu, state, 0);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        tk.x = __shfl_sync(0xffffffffu, tk.x, 0);
+        tk.y = __shfl_sync(0xffffffffu, tk.y, 0);
+        tk.z = __shfl_sync(0xffffffffu, tk.z, 0);
+        tk.w = __shfl_sync(0xffffffffu, tk.w, 0);
+        uint32_t na = 0;
+        if (state == 1) {
+            const uint32_t nb = tk.z - tk.y;
+            const uint64_t tsp = (uint64_t)p.pc_tsp[t] * kSp;
+            warp_copy(sl.run, p.pc_blk_run + tk.y, nb + 1, lane);
+            warp_copy(sl.nval, p.pc_blk_nval + tk.y, nb, lane);
+            warp_copy(sl.sp, p.pc_wsp + tsp, nb * kSp, lane);
+            // a block only holds NULLs unless one of its source partitions sent PC messages this iteration
+            bool act = false;
+            if ((uint32_t)lane < nb) {
+                act = true;
+                if (pc_skip) {
+                    const uint2 pr = p.pc_blk_prange[tk.y + lane];
+                    act = p.pc_prefix[pr.y + 1] != p.pc_prefix[pr.x];
+                }
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, act);
+            if (act) sl.blist[__popc(m & ((1u << lane) - 1u))] = lane;
+            na = __popc(m);
+            if (lane == 0) {
+                sl.tk = tk;
+                sl.nb = nb;
+                sl.na = na;
+            }
+        }
+        if (lane == 0) sl.state = state;
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tfull[ts]);
+        if (state != 1) break;
+        for (uint32_t j = 0; j < na; ++j, ++issued) {
+            const uint32_t b = issued % nbuf, u = issued / nbuf;
+            if (u > 0 && !__all_sync(0xffffffffu, mbar_wait(&empty[b], (u - 1) & 1u, abort, &p.ctrl->error, kPcSpinLimit, kPcSleepNs))) {
+                ok = false;
+                break;
+            }
+            const uint32_t i = sl.blist[j], r0 = sl.run[i], r1 = sl.run[i + 1];
+            if (lane == 0) {
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive_expect_tx(&full[b], sl.nval[i] * kB);
+            }
+            char *dst = reinterpret_cast<char *>(stage + b * kStageWords);
+            // the block's bin runs (row-major source slot, length, offset in the block; multiples of 4 values,
+            // so 16-byte aligned), eight descriptor loads in flight per lane
+            for (uint32_t r = r0; r < r1; r += 32 * 8) {
+                uint4 run[8];
+#pragma unroll
+                for (uint32_t u = 0; u < 8; ++u) {
+                    const uint32_t rr = r + u * 32 + (uint32_t)lane;
+                    run[u] = rr < r1 ? p.pc_runs[rr] : make_uint4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < 8; ++u)
+                    if (r + u * 32 + (uint32_t)lane < r1)
+                        bulk_g2s(dst + (size_t)run[u].z * kB,
+                                 reinterpret_cast<const char *>(p.pdata) + (size_t)run[u].x * kB, run[u].y * kB,
+                                 &full[b]);
+            }
+        }
     }
+    // leave no copy in flight: the last phase armed on each buffer has completed (at once, normally)
+    for (uint32_t b = 0; b < nbuf && b < issued; ++b) {
+        const uint32_t last = (issued - 1 - b) / nbuf;  // last use of buffer b
+        if (lane == 0) mbar_drain(&full[b], last & 1u);
+    }
+    __syncwarp();
+}
+
+// Consumer warp w of k_gather_pc: for every task, folds its entries of each active block (those of its
+// destination range [D_w, D_w+1), the same in every block of the task, cut at build time so that no two
+// warps ever touch one destination) into the shared column accumulator, round by round, with the next
+// round's entries already loading into registers and its entries of the blocks two ahead being fetched
+// into L2; then all consumers write the column's result (or the task's partial vector) and reset the
+// accumulator.
+template <int ALGO, bool B16>
+__device__ void pc_consumer(const Params &p, const PcSlot *slots, uint64_t *full, uint64_t *empty, uint64_t *tfull,
+                            uint64_t *tempty, const uint32_t *stage, uint32_t *acc, uint32_t nbuf,
+                            volatile uint32_t *abort, int lane, int w) {
+    using O = Op<ALGO>;
+    constexpr uint32_t kSp = kPcGatherWarps + 1, kStageWords = kPcBlock + 4;
+    const bool chk = p.pc_skip != 0;  // some partition is not PC: NULL messages are possible
+    const uint32_t acc_o = smem_addr(acc);
+    uint32_t used = 0;                // blocks consumed: buffer used % nbuf, use used / nbuf
+    for (uint32_t n = 0;; ++n) {
+        const uint32_t ts = n & 1;
+        const PcSlot &sl = slots[ts];
+        bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[ts], (n >> 1) & 1u, abort, &p.ctrl->error, kPcSpinLimit, kPcSleepNs));
+        const uint32_t state = ok ? sl.state : 2u;
+        if (pc_consumers_or(state != 1)) break;  // all consumers leave together
+        const uint32_t na = sl.na;
+        // cursor over this warp's rounds in the task's active blocks: the next round to load into registers
+        struct Cur {
+            uint32_t j, s, e;  // active block, entries [s, e) of this warp's range left in it
+        };
+        auto seek = [&](Cur &c) {
+            for (; c.j < na; ++c.j) {
+                const uint32_t i = sl.blist[c.j];
+                c.s = sl.sp[i * kSp + w];
+                c.e = sl.sp[i * kSp + w + 1];
+                if (c.s < c.e) break;
+            }
+        };
+        // this warp's entries (and SSSP weights) of active block j, bulk-prefetched into L2 two blocks
+        // ahead of their fold (the entries are 16-byte aligned and padded to whole 16-entry groups)
+        auto prefetch_block = [&](uint32_t j) {
+            if (lane == 0 && j < na) {
+                const uint32_t i = sl.blist[j], s = sl.sp[i * kSp + w], e = sl.sp[i * kSp + w + 1];
+                if (s < e) {
+                    bulk_prefetch_l2(p.pe + s, (e - s) * 4u);
+                    if (ALGO == ALG_SSSP) bulk_prefetch_l2(p.pw + s, (e - s) * 4u);
+                }
+            }
+        };
+        prefetch_block(0);
+        prefetch_block(1);
+        Cur c{0, 0, 0};
+        seek(c);
+        uint4 R[4];
+        if (c.j < na) pc_load_round(p.pe, c.s, min(c.e - c.s, kPcRound), lane, R);
+        for (uint32_t j = 0; j < na; ++j, ++used) {
+            const uint32_t b = used % nbuf;
+            prefetch_block(j + 2);
+            // every consumer waits for every block, so that none is ever more than nbuf blocks ahead
+            if (ok && !__all_sync(0xffffffffu, mbar_wait(&full[b], (used / nbuf) & 1u, abort, &p.ctrl->error, kPcSpinLimit, kPcSleepNs))) ok = false;
+            const uint32_t vals = smem_addr(stage + b * kStageWords);
+            while (ok && c.j == j) {
+                uint4 E[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) E[q] = R[q];
+                const uint32_t cs = c.s, cn = min(c.e - c.s, kPcRound);
+                c.s += cn;
+                if (c.s >= c.e) {
+                    ++c.j;
+                    seek(c);
+                }
+                if (c.j < na) pc_load_round(p.pe, c.s, min(c.e - c.s, kPcRound), lane, R);
+                int4 W[4] = {};
+                if (ALGO == ALG_SSSP) {
+                    uint4 Wu[4];
+                    pc_load_round(reinterpret_cast<const uint32_t *>(p.pw), cs, cn, lane, Wu);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) W[q] = make_int4((int)Wu[q].x, (int)Wu[q].y, (int)Wu[q].z, (int)Wu[q].w);
+                }
+                // NULL messages need a test only where NULL is not the monoid identity
+                constexpr bool kNul = ALGO == ALG_SSSP || ALGO == ALG_PPR || ALGO == ALG_NIBBLE;
+                if (ALGO == ALG_PR && chk) {
+                    if (cn <= 128) pc_round<ALGO, B16, 4, true>(E, W, cn, vals, acc_o, lane);
+                    else if (cn <= 256) pc_round<ALGO, B16, 8, true>(E, W, cn, vals, acc_o, lane);
+                    else pc_round<ALGO, B16, 16, true>(E, W, cn, vals, acc_o, lane);
+                } else {
+                    if (cn <= 128) pc_round<ALGO, B16, 4, kNul>(E, W, cn, vals, acc_o, lane);
+                    else if (cn <= 256) pc_round<ALGO, B16, 8, kNul>(E, W, cn, vals, acc_o, lane);
+                    else pc_round<ALGO, B16, 16, kNul>(E, W, cn, vals, acc_o, lane);
+                }
+            }
+            // the buffer is released only after its values were waited for and read: after an abort it is
+            // not, so that the producer never re-arms a buffer whose copy may still be in flight.  Warps own
+            // the same destinations in every block of the task, so they need not wait for one another here.
+            __syncwarp();
+            if (ok && lane == 0) mbar_arrive(&empty[b]);
+        }
+        if (pc_consumers_or(!ok)) break;  // an abort: all consumers leave together
+        // the column's result, or this task's partial vector of a column split over several tasks; the
+        // accumulator is reset as it is read (each word by the thread that reads it)
+        const uint4 tk = sl.tk;
+        const uint32_t gq = tk.x << p.shift, wq = min(p.P, p.V - gq);
+        uint32_t *out = (tk.w == kNull) ? p.pc_sum + gq : p.pc_part + (uint64_t)tk.w * p.P;
+        for (uint32_t i = threadIdx.x; i < wq; i += kPcGatherWarps * 32) {
+            const uint32_t a = pc_swz(i);
+            out[i] = acc[a];
+            acc[a] = O::identity();
+        }
+        pc_consumers_sync();
+        if (lane == 0) mbar_arrive(&tempty[ts]);
+    }
+}
+
+// PC part of the gather (Alg. 2 gather over the PC bins, Sec. 3.1.2): one CTA per SM takes tasks (ranges of
+// consecutive blocks of one column's message sequence) with a producer warp and kPcGatherWarps consumer warps.
+//  * The producer stages each active block's message values in one of nbuf shared buffers (TMA bulk copies
+//    of its bin runs), up to nbuf blocks ahead of the slowest consumer; "full" / "empty" mbarriers per
+//    buffer replace a CTA barrier per block, so consumer warps drift within that window.
+//  * Consumer warp w folds the w-th destination slice of every block through the prestored destination
+//    entries (loaded straight from global memory into registers, one round ahead) into the shared column
+//    accumulator, with lane-serial runs and a segmented warp scan: random accesses touch shared memory
+//    only, and no atomics are used, so sums are taken in a fixed order.
+// The accumulator stays in shared memory for the whole task (at swizzled positions); a column split over
+// several tasks writes one partial vector per task.  Every mbarrier wait is bounded: when one runs out,
+// the run's error flag is raised and all warps leave, the producer after its copies have landed.
+template <int ALGO, bool B16>
+__global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
+    using O = Op<ALGO>;
+    constexpr uint32_t kStageWords = kPcBlock + 4;
+    extern __shared__ __align__(16) uint32_t s_pc_dyn[];
+    const uint32_t nbuf = p.pc_nbuf;
+    uint32_t *stage = s_pc_dyn;                     // nbuf x (kPcBlock message values + the padding slot)
+    uint32_t *acc = s_pc_dyn + nbuf * kStageWords;  // P values of the column
+    __shared__ __align__(8) uint64_t s_full[kPcMaxBufs], s_empty[kPcMaxBufs], s_tfull[2], s_tempty[2];
+    __shared__ PcSlot s_slot[2];
+    __shared__ uint32_t s_abort;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (uint32_t i = 0; i < nbuf; ++i) {
+            mbar_init(&s_full[i], 1);
+            mbar_init(&s_empty[i], kPcGatherWarps);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&s_tfull[i], 1);
+            mbar_init(&s_tempty[i], kPcGatherWarps);
+        }
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    // value slot of the padding entries (the copies never write it): the monoid identity, so padding folds
+    // as a no-op whether or not NULLs are checked.  BF16 only carries sums: its identity is +0.
+    if (threadIdx.x < nbuf) {
+        if (B16) reinterpret_cast<uint16_t *>(stage + threadIdx.x * kStageWords)[kPcPadIdx] = 0;
+        else stage[threadIdx.x * kStageWords + kPcPadIdx] = O::identity();
+    }
+    for (uint32_t i = threadIdx.x; i < p.P; i += kPcThreads) acc[i] = O::identity();
+    const unsigned long long t_start = p.t_gpc ? globaltimer() : 0ull;
+    __syncthreads();
+    if (wid == kPcGatherWarps)
+        pc_producer<B16>(p, s_slot, s_full, s_empty, s_tfull, s_tempty, stage, nbuf, &s_abort, lane);
+    else
+        pc_consumer<ALGO, B16>(p, s_slot, s_full, s_empty, s_tfull, s_tempty, stage, acc, nbuf, &s_abort,
+                               lane, wid);
     if (p.t_gpc && threadIdx.x == 0) atomicAdd(p.t_gpc, globaltimer() - t_start);
 }
 
@@ -1890,8 +2026,8 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     grid_pc = persistent_grid(k_scatter_pc<B16>, kScatterPcThreads, spc_smem, g->num_sms);
     grid_sc = persistent_grid(k_scatter_sc<ALGO, B16>, kScatterThreads, sc_smem, g->num_sms);
     grid_ga = persistent_grid(k_gather<ALGO, B16>, kGatherThreads, 0, g->num_sms);
-    // k_gather_pc: column accumulator, two block value buffers and as many entry-chunk slots as the
-    // opt-in shared memory holds (at most kPcMaxSlots); dynamic shared memory is opted in explicitly
+    // k_gather_pc: column accumulator and as many block value buffers as the opt-in shared memory holds
+    // (at most kPcMaxBufs); dynamic shared memory is opted in explicitly
     size_t gpc_smem = 0;
     {
         cudaFuncAttributes fa;
@@ -1899,13 +2035,13 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         int optin = 0, dev = 0;
         GPOP_CUDA_TRY(cudaGetDevice(&dev));
         GPOP_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        const size_t fixed = sizeof(uint32_t) * ((size_t)g->P + 2 * (kPcBlock + 4));
-        const size_t slot = sizeof(uint32_t) * PcShape<ALGO>::kSlotWords * kPcWarps;
+        const size_t fixed = sizeof(uint32_t) * (size_t)g->P;
+        const size_t buf = sizeof(uint32_t) * (kPcBlock + 4);
         const size_t avail = (size_t)optin > fixed + fa.sharedSizeBytes ? optin - fixed - fa.sharedSizeBytes : 0;
-        const uint32_t ns = (uint32_t)std::min<size_t>(kPcMaxSlots, avail / slot);
-        if (ns < 2) return fail(GPOP_ERR_INVALID_ARG, "partition size too large for the PC gather's shared memory");
-        p.pc_slots = ns;
-        gpc_smem = fixed + ns * slot;
+        const uint32_t nb = (uint32_t)std::min<size_t>(kPcMaxBufs, avail / buf);
+        if (nb < 2) return fail(GPOP_ERR_INVALID_ARG, "partition size too large for the PC gather's shared memory");
+        p.pc_nbuf = nb;
+        gpc_smem = fixed + nb * buf;
         GPOP_CUDA_TRY(cudaFuncSetAttribute(k_gather_pc<ALGO, B16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)gpc_smem));
     }
@@ -2237,6 +2373,7 @@ extern "C" gpop_status gpop_run_msbfs(gpop_graph *h, const gpop_run_opts *o, con
 extern "C" gpop_status gpop_probe_bounded_wait(uint32_t tries, uint32_t *gave_up) {
     set_error("");
     if (!gave_up) return fail(GPOP_ERR_INVALID_ARG, "gave_up is NULL");
+    if (tries > kPcSpinLimit) return fail(GPOP_ERR_INVALID_ARG, "tries above the engine's own limit (2^24)");
     uint32_t *d_err = nullptr;
     GPOP_CUDA_TRY(cudaMalloc((void **)&d_err, 4));
     uint32_t h = 0;

@@ -28,11 +28,24 @@ constexpr uint32_t kScatterChunk = 131072;  // PNG slots per PC scatter task (on
 constexpr uint32_t kMaxRowBins = 40960;     // SC scatter keeps one cursor per row bin in smem
 constexpr uint32_t kPcBlock = 8192;         // messages staged in shared memory per PC gather block
 constexpr uint32_t kPcTaskBlocks = 20;      // at most this many blocks per PC gather task (static smem per block)
-constexpr uint32_t kPcGatherWarps = 24;     // warps of the PC gather, one destination slice of a block each
+constexpr uint32_t kPcGatherWarps = 23;     // consumer warps of the PC gather, one destination slice of each task each
 constexpr uint32_t kPcPad = 16;             // each warp's entry range of a block is padded to a multiple of this
-                                            // (16-entry groups, quads swizzled by (group >> 1) & 3)
 constexpr uint32_t kPcPadIdx = kPcBlock;    // block index of the padding entries (a value slot that holds NULL)
 constexpr uint32_t kPcTaskMinEntries = 65536;  // PC gather tasks hold about max(this, E / (4 SMs)) entries
+constexpr uint32_t kPcRound = 512;          // destination entries one gather warp folds per round
+
+// A warp's entry range of a block is folded in rounds of kPcRound entries (the last one shorter, a
+// multiple of kPcPad).  A round of n entries is shared by n / K lanes, K consecutive entries each:
+__host__ __device__ constexpr uint32_t pc_round_k(uint32_t n) { return n <= 128 ? 4u : (n <= 256 ? 8u : 16u); }
+// and is stored as K / 4 rows of 16-byte quads, row j holding the j-th quad of every lane, so that a warp
+// reads one row with one coalesced 16-byte load per lane.  Position of entry m of a round of n entries:
+__host__ __device__ constexpr uint32_t pc_round_pos(uint32_t m, uint32_t n) {
+    return ((m % pc_round_k(n)) / 4 * (n / pc_round_k(n)) + m / pc_round_k(n)) * 4 + m % 4;
+}
+// Position of destination d in the gather's shared accumulator: bits 5-9 XORed into bits 0-4, a bijection
+// on every aligned 32-word group that spreads the lanes of one fold step (destinations a near-constant
+// stride apart) over distinct banks.  Destination entries carry the swizzled position.
+__host__ __device__ constexpr uint32_t pc_swz(uint32_t d) { return d ^ ((d >> 5) & 31u); }
 
 enum Mode : uint8_t { kModeNone = 0, kModeSC = 1, kModePC = 2 };
 enum Action : uint8_t { kActSkip = 0, kActPC = 1, kActNull = 2 };
@@ -95,15 +108,18 @@ struct Graph {
     uint4 *pc_task = nullptr;     // npct: (column, first block, end block, partial slot or kNull), largest first
     uint32_t *pc_tsp = nullptr;   // npct: first row of the task's blocks in pc_wsp
     uint32_t *pc_wsp = nullptr;   // per task block: kPcGatherWarps+1 entry offsets splitting its entries by
-                                  // the column's destination slices (one slice per gather warp)
+                                  // the task's destination slices (one slice per gather warp, the same in
+                                  // every block of the task)
     uint32_t *col_ntask = nullptr;   // k: PC gather tasks of the column (0 = no PC in-edges)
     uint32_t *col_part0 = nullptr;   // k: first partial slot of a multi-task column
     uint32_t *pc_part = nullptr;  // npart x P partial results
     uint2 *pc_merge = nullptr;    // nmerge: (column, first destination) of each 1024-destination chunk of a
                                   // column split over several tasks (its partials are merged into pc_sum)
     uint32_t nmerge = 0;
-    uint32_t *pe = nullptr;       // entries, sorted by (block, destination, index); each warp range of a task
-                                  // block starts 16-aligned and is padded to a multiple of kPcPad
+    uint32_t *pe = nullptr;       // entries (swizzled accumulator position << 16 | index in block), sorted by
+                                  // (block, destination, index); each warp range of a task block starts
+                                  // 16-aligned, is padded to a multiple of kPcPad and is stored round by round
+                                  // in lane-interleaved order (pc_round_pos)
     int32_t *pw = nullptr;        // null or weights aligned with pe (padding: 0)
     uint32_t npcb = 0, npct = 0, npart = 0;
 
