@@ -220,8 +220,8 @@ def run_ours(a, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    # one rank compiles if the library is out of date; the others load it after the barrier
-    if rank == 0:
+    # one rank per node compiles if the library is out of date; the others load it after the barrier
+    if local_rank == 0:
         gp.build()
     if dist is not None:
         dist.barrier()

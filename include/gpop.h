@@ -227,12 +227,16 @@ gpop_status gpop_run_msbfs(gpop_graph *g, const gpop_run_opts *opts, const uint3
  * number of iterations behind it and the L1 change of its last gather.
  *   gpop_state_export  writes the checkpoint into the caller's HOST buffer of `capacity` bytes and its
  *                      size into *size; with buffer NULL only the size is returned.
- *   gpop_state_import  loads a checkpoint (of a graph with the same vertex count) into this graph, for a
- *                      following gpop_run with opts.resume set.
- * The layout is a 48-byte header (magic "GPST", version 1, algorithm, V, iterations, frontier words,
- * L1 change) then V words each of values, levels and messages and the frontier words, little endian.
- * Errors: GPOP_ERR_INVALID_ARG (no state held, buffer too small, header or size that does not match),
- * GPOP_ERR_OOM, GPOP_ERR_CUDA.
+ *   gpop_state_import  loads a checkpoint of the same graph (vertex and edge counts, partition size and a
+ *                      fingerprint of its edges and weights must match) into this graph, for a following
+ *                      gpop_run with opts.resume set.  That run must repeat the saved run's options that
+ *                      shape the result (source, damping, epsilon, msg_bf16, where the algorithm uses them);
+ *                      otherwise it returns GPOP_ERR_INVALID_ARG.
+ * The layout is an 80-byte header (magic "GPST", version 2, algorithm, V, iterations, frontier words,
+ * L1 change, E, graph fingerprint, P, msg_bf16, source, damping, epsilon) then V words each of values,
+ * levels and messages and the frontier words, little endian.
+ * Errors: GPOP_ERR_INVALID_ARG (no state held, buffer too small, header or size that does not match,
+ * another graph or partition size), GPOP_ERR_OOM, GPOP_ERR_CUDA.
  */
 gpop_status gpop_state_export(const gpop_graph *g, void *buffer, uint64_t capacity, uint64_t *size);
 gpop_status gpop_state_import(gpop_graph *g, const void *buffer, uint64_t size);

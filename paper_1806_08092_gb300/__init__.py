@@ -198,7 +198,7 @@ class Graph:
         return buf
 
     def state_import(self, buf) -> None:
-        """Loads a checkpoint written by state_export (of a graph with the same vertex count)."""
+        """Loads a checkpoint written by state_export of the same graph (same edges, weights and partition size)."""
         b = np.ascontiguousarray(buf, dtype=np.uint8)
         _lib.check(_lib.load().gpop_state_import(self._h, ctypes.c_void_p(b.ctypes.data), b.size))
 

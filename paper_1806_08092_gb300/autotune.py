@@ -22,8 +22,8 @@ def pick_partition_size(row_ptr, col, weights=None, runs=(("pagerank", {"max_ite
 
     runs: (algorithm, keyword arguments of Graph.run) pairs timed together; each is run once to warm up,
     then `reps` times, and its median device time is summed over the runs.  A candidate the library
-    rejects (an out-of-range P, or a layout that does not fit in device memory) is listed with None and
-    the library's message, and skipped.  Raises ValueError when no candidate works."""
+    rejects when building it (an out-of-range P, a layout that does not fit in device memory) or when
+    running on it (run buffers that do not fit) is listed with None and the library's message, and skipped.  Raises ValueError when no candidate works."""
     import time
     table = []
     best = None
@@ -41,6 +41,9 @@ def pick_partition_size(row_ptr, col, weights=None, runs=(("pagerank", {"max_ite
                 G.run(algo, **kw)
                 ts = sorted(G.run(algo, **kw).stats["device_ms"] for _ in range(reps))
                 total += ts[len(ts) // 2]
+        except GpopError as e:  # e.g. run buffers that do not fit, or a gather shape the layout rejects
+            table.append((int(P), None, build_s, str(e)))
+            continue
         finally:
             G.close()
         table.append((int(P), total, build_s, ""))

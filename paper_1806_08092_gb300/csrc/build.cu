@@ -273,6 +273,26 @@ __global__ void k_edge_sub(uint64_t E, uint32_t shift, const uint32_t *src, cons
     }
 }
 
+// splitmix64's output function (Steele, Lea, Flood 2014): a bijective 64-bit mix
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+// Fingerprint of the graph for checkpoints: the sum (mod 2^64) over edges of a mixed (source, destination,
+// weight) key, so it depends on the edge multiset only, not on the order of the sums
+__global__ void k_fingerprint(uint64_t E, const uint32_t *src, const uint32_t *col, const int32_t *w,
+                              unsigned long long *out) {
+    unsigned long long acc = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < E; e += stride) {
+        const uint64_t wt = w ? (uint32_t)w[e] : 0u;
+        acc += mix64((((uint64_t)src[e] << 32) | col[e]) ^ mix64(wt + 0x9E3779B97F4A7C15ull));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
 // first entry of [l, h) (sorted by destination) whose destination is at least D
 __device__ __forceinline__ uint32_t first_dest_at_least(const uint32_t *pe, uint32_t l, uint32_t h, uint32_t D) {
     while (l < h) {
@@ -468,6 +488,15 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         k_unpack_dst<<<blocks_for(E), kThreads, 0, s>>>(E, k1, g->col);
         t.release(k0);
         t.release(k1);
+    }
+    {  // the graph's fingerprint (checkpoints of another graph are refused)
+        unsigned long long *d_fp, h_fp = 0;
+        GPOP_CUDA_TRY(t.alloc(&d_fp, 1));
+        GPOP_CUDA_TRY(cudaMemsetAsync(d_fp, 0, 8, s));
+        if (E) k_fingerprint<<<std::min<uint64_t>(blocks_for(E), 8ull * g->num_sms), kThreads, 0, s>>>(E, src, g->col, g->w, d_fp);
+        GPOP_CUDA_TRY(cudaMemcpyAsync(&h_fp, d_fp, 8, cudaMemcpyDeviceToHost, s));
+        GPOP_CUDA_TRY(cudaStreamSynchronize(s));
+        g->fingerprint = h_fp ^ ((uint64_t)V << 32) ^ (E * 0x9E3779B97F4A7C15ull) ^ (uint64_t)g->weighted;
     }
 
     // 3. messages: one per (source, destination partition), sorted by (p, q, source)

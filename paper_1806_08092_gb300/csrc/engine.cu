@@ -658,6 +658,8 @@ __global__ void k_wait_probe(uint32_t tries, uint32_t *err) {
 }
 
 // Bounded wait used while leaving after an abort: lets copies still in flight land before the CTA exits.
+// Should it run out too (a copy that never completes, which no test can cause without a fault), the CTA
+// leaves with that copy still in flight; the run has reported GPOP_ERR_TIMEOUT by then.
 __device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
     for (uint32_t it = 0; it < kPcSpinLimit && !mbar_try_wait(bar, parity); ++it) {
     }
@@ -1805,6 +1807,9 @@ struct RunBuffers {
     int state_algo = -1;
     uint32_t state_iter = 0;
     double state_res = 0.0;
+    // the options of that run that shape its result (a resumed run must repeat them)
+    uint32_t state_source = 0, state_bf16 = 0;
+    double state_damping = 0.0, state_epsilon = 0.0;
 };
 
 static void release_runbufs(RunBuffers *rb) {
@@ -1996,6 +2001,18 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     // counts this call's iterations, and its first plan tests the saved L1 change
     const bool resume = o->resume != 0;
     if (resume && rb->state_algo != ALGO) return fail(GPOP_ERR_INVALID_ARG, "resume: no saved state of this algorithm");
+    if (resume) {  // the options that shape the result must be those of the saved run
+        const bool src = ALGO == ALG_BFS || ALGO == ALG_SSSP || ALGO == ALG_PPR || ALGO == ALG_NIBBLE;
+        const bool damp = ALGO == ALG_PR || ALGO == ALG_PPR;
+        if (src && o->source != rb->state_source)
+            return fail(GPOP_ERR_INVALID_ARG, "resume: another source than the saved run's");
+        if (damp && o->damping != rb->state_damping)
+            return fail(GPOP_ERR_INVALID_ARG, "resume: another damping than the saved run's");
+        if (ALGO == ALG_NIBBLE && o->epsilon != rb->state_epsilon)
+            return fail(GPOP_ERR_INVALID_ARG, "resume: another threshold than the saved run's");
+        if ((uint32_t)(B16 ? 1 : 0) != rb->state_bf16)
+            return fail(GPOP_ERR_INVALID_ARG, "resume: another message format than the saved run's");
+    }
     const uint32_t base = resume ? rb->state_iter : 0u;
     p.source = o->source; p.tol = o->tol_l1;
     p.max_iters = o->max_iters > 0xFFFFFFFEu - base ? 0xFFFFFFFEu : base + o->max_iters;
@@ -2212,6 +2229,10 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         rb->state_algo = ALGO;
         rb->state_iter = base + iter;
         rb->state_res = st.residual;
+        rb->state_source = o->source;
+        rb->state_damping = o->damping;
+        rb->state_epsilon = o->epsilon;
+        rb->state_bf16 = B16 ? 1u : 0u;
     }
 
     // outputs
@@ -2393,14 +2414,20 @@ extern "C" gpop_status gpop_probe_bounded_wait(uint32_t tries, uint32_t *gave_up
 // --- checkpoint ---------------------------------------------------------------------------------
 
 namespace {
+// version 2: the graph (vertex and edge counts, partition size, fingerprint of its edges and weights) and
+// the options of the saved run that shape its result, so that a checkpoint is never continued on another
+// graph or with other options
 struct StateHeader {
     uint32_t magic, version;
     int32_t algo;
     uint32_t V, iterations, nwords;
     double residual;
-    uint64_t pad[2];
+    uint64_t E, fingerprint;
+    uint32_t P, msg_bf16, source, pad;
+    double damping, epsilon;
 };
-static_assert(sizeof(StateHeader) == 48, "checkpoint header is 48 bytes");
+static_assert(sizeof(StateHeader) == 80, "checkpoint header is 80 bytes");
+constexpr uint32_t kStateVersion = 2;
 constexpr uint32_t kStateMagic = 0x54535047u;  // "GPST"
 uint64_t state_bytes(uint32_t V) { return sizeof(StateHeader) + 12ull * V + 4ull * ((V + 31) / 32); }
 }  // namespace
@@ -2417,12 +2444,19 @@ extern "C" gpop_status gpop_state_export(const gpop_graph *h, void *buffer, uint
     if (capacity < need) return fail(GPOP_ERR_INVALID_ARG, "checkpoint buffer too small");
     StateHeader hd{};
     hd.magic = kStateMagic;
-    hd.version = 1;
+    hd.version = kStateVersion;
     hd.algo = rb->state_algo;
     hd.V = g->V;
     hd.iterations = rb->state_iter;
     hd.nwords = (g->V + 31) / 32;
     hd.residual = rb->state_res;
+    hd.E = g->E;
+    hd.fingerprint = g->fingerprint;
+    hd.P = g->P;
+    hd.msg_bf16 = rb->state_bf16;
+    hd.source = rb->state_source;
+    hd.damping = rb->state_damping;
+    hd.epsilon = rb->state_epsilon;
     char *out = static_cast<char *>(buffer);
     memcpy(out, &hd, sizeof hd);
     out += sizeof hd;
@@ -2441,9 +2475,14 @@ extern "C" gpop_status gpop_state_import(gpop_graph *h, const void *buffer, uint
     if (size < sizeof(StateHeader)) return fail(GPOP_ERR_INVALID_ARG, "checkpoint shorter than its header");
     StateHeader hd;
     memcpy(&hd, buffer, sizeof hd);
-    if (hd.magic != kStateMagic || hd.version != 1) return fail(GPOP_ERR_INVALID_ARG, "not a checkpoint of this format");
+    if (hd.magic != kStateMagic || hd.version != kStateVersion)
+        return fail(GPOP_ERR_INVALID_ARG, "not a checkpoint of this format");
     if (hd.V != g->V || size != state_bytes(g->V) || hd.nwords != (g->V + 31) / 32)
         return fail(GPOP_ERR_INVALID_ARG, "checkpoint of a graph with another vertex count");
+    if (hd.E != g->E || hd.fingerprint != g->fingerprint)
+        return fail(GPOP_ERR_INVALID_ARG, "checkpoint of another graph (its edges or weights differ)");
+    if (hd.P != g->P) return fail(GPOP_ERR_INVALID_ARG, "checkpoint of another partition size");
+    if (hd.msg_bf16 > 1) return fail(GPOP_ERR_INVALID_ARG, "checkpoint with an unknown message format");
     if (hd.algo < GPOP_PAGERANK || hd.algo > GPOP_NIBBLE) return fail(GPOP_ERR_INVALID_ARG, "checkpoint of an unknown algorithm");
     RunBuffers *rb = static_cast<RunBuffers *>(g->run);
     if (!rb) {
@@ -2460,5 +2499,9 @@ extern "C" gpop_status gpop_state_import(gpop_graph *h, const void *buffer, uint
     rb->state_algo = hd.algo;
     rb->state_iter = hd.iterations;
     rb->state_res = hd.residual;
+    rb->state_source = hd.source;
+    rb->state_damping = hd.damping;
+    rb->state_epsilon = hd.epsilon;
+    rb->state_bf16 = hd.msg_bf16;
     return GPOP_OK;
 }

@@ -149,6 +149,7 @@ struct Graph {
     int pdata_fmt = 0;  // message format of the data rows: 0 FP32/u32, 1 BF16
 
     uint64_t device_bytes = 0;
+    uint64_t fingerprint = 0;     // of the edge multiset with weights, V and E (checkpoints name their graph)
     int device = 0, num_sms = 0;
     void *run = nullptr;          // cached per-run buffers (engine.cu)
 };

@@ -24,7 +24,10 @@ class _FakeGraph:
         return cls(partition_size)
 
     def run(self, algo, **kw):
-        return _FakeRun(self.times[self.P][algo])
+        t = self.times[self.P][algo]
+        if t is None:
+            raise GpopError(2, "run buffers: out of memory")
+        return _FakeRun(t)
 
     def close(self):
         self.closed.append(self.P)
@@ -47,3 +50,13 @@ def test_no_candidate_raises(monkeypatch):
     monkeypatch.setattr(autotune, "Graph", _FakeGraph)
     with pytest.raises(ValueError):
         autotune.pick_partition_size(None, None, None, candidates=(3000,))
+
+
+def test_a_candidate_whose_runs_fail_is_listed_and_skipped(monkeypatch):
+    _FakeGraph.times = {2048: {"bfs": 3.0}, 16384: {"bfs": None}}
+    _FakeGraph.closed = []
+    monkeypatch.setattr(autotune, "Graph", _FakeGraph)
+    best, table = autotune.pick_partition_size(None, None, None, runs=[("bfs", {})], candidates=(2048, 16384))
+    assert best == 2048
+    assert table[1][0] == 16384 and table[1][1] is None and "out of memory" in table[1][3]
+    assert _FakeGraph.closed == [2048, 16384]  # the failing layout is released too

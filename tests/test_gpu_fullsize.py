@@ -2,9 +2,12 @@
 
 RMAT scale 22 (4.2M vertices, ~65M edges): BFS levels and parents, SSSP distances (weights 1..255) and
 CC labels (symmetrised graph) bit-exact against the full oracle.  RMAT scale 24 (16.8M vertices, ~263M
-edges): PageRank 10 iterations against the FP64 oracle (L-inf relative <= 1e-5), and the run to an L1
-residual below 1e-9 checked on sampled vertices against the fixed-point equation of Alg. 6 evaluated in
-FP64 from the GPU's own ranks.
+edges): PageRank 10 iterations, and PageRank to an L1 residual below 1e-9, element by element against
+the FP64 oracle run to the same tolerance (L-inf relative <= 1e-5, iteration counts compared; BF16
+messages reported), plus the fixed-point equation of Alg. 6 on sampled vertices.  The uniform random
+graph of the same size (2^24 vertices, 16 x 2^24 edge draws): PageRank 10 iterations.  Seeded PPR at
+the bench's partition size on RMAT 18 and 22, and parallel Nibble at eps = 0 (no threshold, so the
+frontiers are exact) on a uniform 2^20 graph.
 """
 import numpy as np
 import pytest
@@ -126,3 +129,91 @@ def test_rmat24_pagerank_converged_fixed_point_sampled(rmat24):
     # rank mass: sum x = (1-d) + d (sum x - sink mass) at the fixed point
     sink = deg == 0
     assert abs(x.sum() - ((1 - 0.85) + 0.85 * (x.sum() - x[sink].sum()))) <= 1e-5 * x.sum()
+
+
+@pytest.fixture(scope="module")
+def rmat24_converged(rmat24):
+    # the FP64 oracle run to the bench's tolerance (about 90 power iterations of Alg. 6)
+    g, _ = rmat24
+    return O.pagerank(g, 0.85, max_iters=300, tol=1e-9)
+
+
+def test_rmat24_pagerank_to_1e9_against_oracle(rmat24, rmat24_converged):
+    g, G = rmat24
+    ref, it_ref, res_ref = rmat24_converged
+    r = G.run("pagerank", max_iters=300, tol=1e-9)
+    x = r.values.cpu().numpy().astype(np.float64)
+    err = float(np.max(np.abs(x - ref) / ref))
+    print(f"RMAT-24 PageRank to L1 < 1e-9: GPU {r.stats['iterations']} iterations (residual "
+          f"{r.stats['residual']:.3e}), oracle {it_ref} (residual {res_ref:.3e}); L-inf rel error {err:.2e}")
+    assert res_ref < 1e-9 and r.stats["converged"] == 1 and r.stats["residual"] < 1e-9
+    # the FP32 residual tracks the FP64 one until both fall below the tolerance
+    assert abs(r.stats["iterations"] - it_ref) <= 2
+    assert err <= 1e-5
+
+
+def test_rmat24_pagerank_bf16_messages_at_convergence(rmat24, rmat24_converged):
+    g, G = rmat24
+    ref, _, _ = rmat24_converged
+    r = G.run("pagerank", max_iters=300, tol=1e-9, msg_bf16=True)
+    x = r.values.cpu().numpy().astype(np.float64)
+    e16 = float(np.max(np.abs(x - ref) / ref))
+    print(f"RMAT-24 PageRank with BF16 messages to L1 < 1e-9: {r.stats['iterations']} iterations, "
+          f"L-inf rel error vs the FP64 oracle {e16:.2e} (reported; BF16 keeps 8 bits of a message)")
+    assert r.stats["converged"] == 1
+    assert e16 <= 2e-2  # 2^-9 per message, amplified at most d / (1 - d) by the iteration
+
+
+def test_uniform24_pagerank_10_iterations(gp):
+    g = gg.uniform(1 << 24, 16 << 24)
+    G = gp.Graph.from_csr(g.row_ptr, g.col, partition_size=P_BENCH)
+    ref, _, _ = O.pagerank(g, 0.85, max_iters=10)
+    x = G.run("pagerank", max_iters=10).values.cpu().numpy().astype(np.float64)
+    G.close()
+    err = float(np.max(np.abs(x - ref) / ref))
+    print(f"uniform 2^24 PageRank 10 iterations: L-inf rel error {err:.2e}")
+    assert err <= 1e-5
+
+
+def _ppr_error_profile(x, ref):
+    """Largest relative error over the oracle's support, by floor of the oracle value."""
+    out = {}
+    for floor in (0.0, 1e-30, 1e-20, 1e-10):
+        m = ref > floor
+        out[floor] = float(np.max(np.abs(x[m] - ref[m]) / ref[m])) if m.any() else 0.0
+    return out
+
+
+@pytest.mark.parametrize("scale", [18, 22])
+def test_ppr_bench_partition_size(gp, scale):
+    g = gg.rmat(scale)
+    G = gp.Graph.from_csr(g.row_ptr, g.col, partition_size=P_BENCH)
+    s = int(gg.roots(g, 1)[0])
+    ref, _, _ = O.ppr(g, s, 0.15, max_iters=40)
+    x = G.run("ppr", source=s, damping=0.85, max_iters=40).values.cpu().numpy().astype(np.float64)
+    G.close()
+    prof = _ppr_error_profile(x, ref)
+    print(f"RMAT-{scale} PPR 40 iterations, P = {P_BENCH}: max rel error by oracle floor {prof}; "
+          f"support {(ref > 0).sum()}, smallest {ref[ref > 0].min():.2e}")
+    assert np.all(np.abs(x[ref == 0]) <= 1e-12)
+    assert prof[0.0] <= 1e-5
+
+
+def test_nibble_eps0_uniform20_exact_frontiers(gp):
+    # at eps = 0 every reached vertex with out-edges stays on (PR >= 0 always holds), so no FP32 rounding
+    # can move a vertex across the threshold: the frontier sizes are exact, the values FP32 sums of the
+    # lazy walk's probabilities
+    g = gg.uniform(1 << 20, 16 << 20)
+    G = gp.Graph.from_csr(g.row_ptr, g.col, partition_size=P_BENCH)
+    seed = int(gg.roots(g, 1)[0])
+    ref, it, fr = O.nibble(g, seed, 0.0, max_iters=8)
+    r = G.run("nibble", source=seed, epsilon=0.0, max_iters=8, trace=True)
+    G.close()
+    x = r.values.cpu().numpy().astype(np.float64)
+    assert r.stats["iterations"] == it
+    assert np.array_equal(r.frontier[:, 0], fr)
+    sup = ref > 0
+    assert np.array_equal(x > 0, sup)
+    err = float(np.max(np.abs(x[sup] - ref[sup]) / ref[sup]))
+    print(f"uniform 2^20 Nibble eps = 0, {it} iterations: frontiers {[int(f) for f in fr]}; L-inf rel error {err:.2e}")
+    assert err <= 1e-5

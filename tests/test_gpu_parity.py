@@ -248,6 +248,31 @@ def test_checkpoint_errors():
     bad[0] ^= 0xFF
     with pytest.raises(gp.GpopError):
         G(g, 64).state_import(bad)  # not a checkpoint
+    # another graph with the same vertex and edge counts: one edge's destination moved
+    col = g.col.copy()
+    row = int(np.flatnonzero(np.diff(g.row_ptr) == 1)[0])  # a vertex with a single out-edge
+    e0 = int(g.row_ptr[row])
+    col[e0] = (col[e0] + 1) % g.num_vertices if (col[e0] + 1) % g.num_vertices != row else (col[e0] + 2) % g.num_vertices
+    other = gp.Graph.from_csr(g.row_ptr, col, partition_size=64)
+    with pytest.raises(gp.GpopError, match="another graph"):
+        other.state_import(blob)
+    with pytest.raises(gp.GpopError, match="partition size"):
+        G(g, 128).state_import(blob)  # the same graph, another partition size
+    # a resumed run must repeat the options that shape the saved run's result
+    fresh = G(g, 64)
+    fresh.state_import(blob)
+    other_root = int(gg.roots(g, 2)[1])
+    with pytest.raises(gp.GpopError, match="source"):
+        fresh.run("bfs", source=other_root, resume=True)
+    assert fresh.run("bfs", source=root, resume=True).stats["converged"] == 1
+    Gd.run("ppr", source=root, max_iters=3)
+    with pytest.raises(gp.GpopError, match="damping"):
+        Gd.run("ppr", source=root, damping=0.8, max_iters=3, resume=True)
+    with pytest.raises(gp.GpopError, match="message format"):
+        Gd.run("ppr", source=root, max_iters=3, resume=True, msg_bf16=True)
+    Gd.run("nibble", source=root, epsilon=1e-4, max_iters=2)
+    with pytest.raises(gp.GpopError, match="threshold"):
+        Gd.run("nibble", source=root, epsilon=1e-5, max_iters=2, resume=True)
 
 
 def test_partition_size_autotuner():

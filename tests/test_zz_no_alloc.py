@@ -53,15 +53,23 @@ def call_noalloc(lib, w, X, Y):
 
 def test_noalloc_matches_allocating_entry_point_on_consecutive_calls(lib):
     gp, raw = lib
-    # two calls in a row share the scratch array; the second is smaller, so stale partials of the first
-    # call must not leak into its result
-    for n, seed in ((5000, 1), (777, 2), (64, 3)):
+    from oracle import mlp
+    # calls in a row share the scratch array: the largest accepted size (16384 samples fills every
+    # scratch block and the loss slot) and one below it, then smaller calls, so stale partials of a
+    # larger call must not leak into a smaller one's result
+    for n, seed in ((16384, 4), (16383, 5), (5000, 1), (777, 2), (64, 3)):
         w, X, Y = problem(n, seed)
         pred, grad, loss = call_noalloc(raw, w, X, Y)
         ref_pred, ref_grad, ref_loss = gp.selector_grad(w, X, Y)
         assert np.max(np.abs(pred - ref_pred)) <= 1e-4 * max(1.0, float(np.max(np.abs(ref_pred))))
         assert np.max(np.abs(grad - ref_grad)) <= 1e-4 * float(np.max(np.abs(ref_grad)))
         assert loss == pytest.approx(ref_loss, rel=1e-4)
+        # and directly against the FP64 reference of the network (oracle/mlp.py), same tolerance
+        w64, X64, Y64 = w.astype(np.float64), X.astype(np.float64), Y.astype(np.float64)
+        o_pred, o_grad = mlp.forward(w64, X64), mlp.grad(w64, X64, Y64)
+        assert np.max(np.abs(pred - o_pred)) <= 1e-4 * max(1.0, float(np.max(np.abs(o_pred))))
+        assert np.max(np.abs(grad - o_grad)) <= 1e-4 * float(np.max(np.abs(o_grad)))
+        assert loss == pytest.approx(mlp.loss(w64, X64, Y64), rel=1e-4)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
