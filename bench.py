@@ -244,33 +244,42 @@ def run_ours(a, rank, world, local_rank):
             lv = G.run("bfs", source=r).values
             te_of[r] = int(deg_t[lv.to(torch.int64) != INF].sum().item())
 
-    def step(r):
+    def step(r, profile):
         out = {}
         if "pr" in parts:
-            out["pr"] = G.run("pagerank", max_iters=a.pr_max_iters, tol=a.pr_tol, profile=True).stats
+            out["pr"] = G.run("pagerank", max_iters=a.pr_max_iters, tol=a.pr_tol, profile=profile).stats
         if "bfs" in parts:
-            out["bfs"] = G.run("bfs", source=r, profile=True).stats
+            out["bfs"] = G.run("bfs", source=r, profile=profile).stats
         if "sssp" in parts:
-            out["sssp"] = G.run("sssp", source=r, profile=True).stats
+            out["sssp"] = G.run("sssp", source=r, profile=profile).stats
         return out
 
     for i in range(a.warmup):
-        step(my_roots[i])
+        step(my_roots[i], False)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()
+    # the timed region: the steps without per-kernel timing events
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    stats = [step(my_roots[a.warmup + i]) for i in range(a.steps)]
+    stats = [step(my_roots[a.warmup + i], False) for i in range(a.steps)]
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop() if clocks else None
+    # the same steps again with per-kernel CUDA events (outside the timed region): kernel times and launches
+    torch.cuda.synchronize()
+    evp0, evp1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evp0.record(stream)
+    pstats = [step(my_roots[a.warmup + i], True) for i in range(a.steps)]
+    evp1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = evp0.elapsed_time(evp1)
 
     edges = 0
     for i, s in enumerate(stats):
@@ -279,60 +288,84 @@ def run_ours(a, rank, world, local_rank):
     t_all, edges_all = reduce_over_ranks(ms / 1e3, float(edges), dist, "cuda")
     value = edges_all / t_all / 1e9
 
-    # per-application device throughput and the roofline of the dominant kernel (PageRank gather)
-    def total(key, field):
-        return sum(s[key][field] for s in stats if key in s)
+    hbm, peak_kind = peaks()
+    # per-application device throughput, and the fraction of the HBM peak the bytes of Sec. 3.2's model
+    # (Eq. (SC) / (PC) of the modes chosen) represent over the run's device time
+    def total(key, field, ss=stats):
+        return sum(s[key][field] for s in ss if key in s)
     te = sum(te_of.get(my_roots[a.warmup + i], 0) for i in range(a.steps))
     kern = np.zeros(6)
     launches = np.zeros(6, dtype=np.int64)
-    for s in stats:
+    for s in pstats:
         for key in s:
             kern += np.array(s[key]["kernel_ms"])
             launches += np.array(s[key]["kernel_launches"], dtype=np.int64)
     per_algo = {}
-    if "pr" in parts:
-        pr_ms, pr_it = total("pr", "device_ms"), total("pr", "iterations")
-        per_algo["pagerank"] = {"iterations": pr_it / a.steps, "gteps": E * pr_it / (pr_ms / 1e3) / 1e9,
-                                "ms": pr_ms / a.steps, "residual": stats[-1]["pr"]["residual"]}
-    for key in ("bfs", "sssp"):
-        if key in parts:
-            ms_ = total(key, "device_ms")
-            per_algo[key] = {"gteps": te / (ms_ / 1e3) / 1e9, "ms": ms_ / a.steps,
-                             "iterations": total(key, "iterations") / a.steps}
-    def pr_kernel(i):
-        ms_ = sum(s["pr"]["kernel_ms"][i] for s in stats)
-        n_ = sum(s["pr"]["kernel_launches"][i] for s in stats)
-        return ms_ / max(n_, 1) / 1e3, n_
+    for key, name in (("pr", "pagerank"), ("bfs", "bfs"), ("sssp", "sssp")):
+        if key not in parts:
+            continue
+        ms_, it_ = total(key, "device_ms"), total(key, "iterations")
+        mb = total(key, "model_bytes")
+        d = {"ms": ms_ / a.steps, "iterations": it_ / a.steps,
+             "model_bytes_per_run": mb / a.steps, "model_frac": mb / (ms_ / 1e3) / 1e9 / hbm}
+        if key == "pr":
+            d.update(gteps=E * it_ / (ms_ / 1e3) / 1e9, ms_per_iteration=ms_ / max(it_, 1),
+                     residual=stats[-1]["pr"]["residual"])
+        else:
+            d.update(gteps=te / (ms_ / 1e3) / 1e9)
+        per_algo[name] = d
+
+    def kernel(key, i):
+        ms_ = sum(s[key]["kernel_ms"][i] for s in pstats)
+        n_ = sum(s[key]["kernel_launches"][i] for s in pstats)
+        return ms_ / 1e3, n_
 
     npng, k = info["num_png"], info["num_partitions"]
-    # Algorithmic bytes per launch of an all-PC PageRank iteration (every vertex active):
-    #  PC scatter: PNG source ID (2 B) + message value (4 B) per message, one message value per vertex;
-    #  PC gather (k_gather_pc): every message value once (4 B per PNG entry, staged bin by bin), the
-    #    destination-list word of every in-entry (4 B) and the per-vertex PC result written (4 B);
-    #  task gather + filter (k_gather): per vertex the PC result read, rank read + write, next message
-    #    value, two row offsets (one per vertex in a stream) and the frontier bits.
-    per_kernel_bytes = {
-        1: 6 * npng + 4 * V,
-        4: 4 * E + 4 * npng + 4 * V,
-        3: 4 * V + 16 * V + V // 4,
-    }
-    names = {1: "k_scatter_pc", 3: "k_gather", 4: "k_gather_pc"}
-    hbm, peak_kind = peaks()
+    # Algorithmic bytes (what the method moves) of each kernel, from the run's own counts:
+    #  PageRank (all partitions PC every iteration), per launch:
+    #   k_scatter_pc: PNG source ID (2 B) + message value written (4 B) per message, the partition's
+    #     values read once (4 B per vertex);
+    #   k_gather_pc: every message value once (4 B per message) and the destination word of every
+    #     in-edge (4 B per edge) -- the method's bytes only;
+    #   k_gather: per vertex the PC result read, rank read + write, next message value, row offsets and
+    #     frontier bits (20.25 B).
+    #  BFS / SSSP, over the run (SC partitions' V_a and E_a summed over iterations):
+    #   k_scatter_sc: two row offsets per active vertex (8 B), the destination of every active edge (4 B)
+    #     and its (destination, value) pair written (8 B), + its weight (4 B) for SSSP;
+    #   k_gather: every pair read (8 B) + the per-vertex filter bytes above for every destination visited.
+    def entry(name, key, i, nbytes, launches_=None):
+        t_s, n_ = kernel(key, i)
+        if n_ == 0 or t_s <= 0:
+            return None
+        per = nbytes / n_
+        ach = nbytes / t_s / 1e9
+        return {"kernel": name, "achieved": ach, "frac": ach / hbm, "algorithmic_bytes_per_launch": int(per),
+                "avg_launch_ms": t_s * 1e3 / n_, "launches": int(n_), "total_ms": t_s * 1e3}
+
     roofline = None
+    all_k = []
     if "pr" in parts:
-        kinfo = {}
-        for i in (1, 3, 4):
-            avg_s, n_ = pr_kernel(i)
-            ach = per_kernel_bytes[i] / avg_s / 1e9 if avg_s > 0 else 0.0
-            kinfo[i] = {"kernel": names[i] + "<PageRank>", "achieved": ach, "frac": ach / hbm,
-                        "algorithmic_bytes_per_launch": int(per_kernel_bytes[i]), "avg_launch_ms": avg_s * 1e3,
-                        "launches": int(n_), "total_ms": avg_s * 1e3 * n_}
-        dom = max(kinfo, key=lambda i: kinfo[i]["total_ms"])
-        roofline = {"bound": "hbm", "kernel": kinfo[dom]["kernel"], "achieved": kinfo[dom]["achieved"],
-                    "peak": hbm, "unit": "GB/s", "frac": kinfo[dom]["frac"],
-                    "traffic": traffic_from_profile(kinfo[dom]["kernel"]), "peak_kind": peak_kind,
-                    "algorithmic_bytes_per_launch": kinfo[dom]["algorithmic_bytes_per_launch"],
-                    "avg_launch_ms": kinfo[dom]["avg_launch_ms"], "all_kernels": [kinfo[i] for i in (1, 3, 4)]}
+        it_pr = total("pr", "iterations", pstats)
+        pr_k = [entry("k_scatter_pc<PageRank>", "pr", 1, (6 * npng + 4 * V) * it_pr),
+                entry("k_gather<PageRank>", "pr", 3, (20 * V + V // 4) * it_pr),
+                entry("k_gather_pc<PageRank>", "pr", 4, (4 * E + 4 * npng) * it_pr)]
+        all_k += [x for x in pr_k if x]
+    for key, nm in (("bfs", "BFS"), ("sssp", "SSSP")):
+        if key not in parts:
+            continue
+        sv, se = total(key, "sc_vertices_scattered", pstats), total(key, "sc_edges_scattered", pstats)
+        gv = total(key, "gathered_vertices", pstats)
+        wb = 4 if key == "sssp" else 0
+        for x in (entry(f"k_scatter_sc<{nm}>", key, 2, 8 * sv + (12 + wb) * se),
+                  entry(f"k_gather<{nm}>", key, 3, 8 * se + 20.25 * gv)):
+            if x:
+                all_k.append(x)
+    if all_k:
+        dom = max(all_k, key=lambda x: x["total_ms"])
+        roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["achieved"], "peak": hbm,
+                    "unit": "GB/s", "frac": dom["frac"], "traffic": traffic_from_profile(dom["kernel"]),
+                    "peak_kind": peak_kind, "algorithmic_bytes_per_launch": dom["algorithmic_bytes_per_launch"],
+                    "avg_launch_ms": dom["avg_launch_ms"], "all_kernels": all_k}
 
     # end-to-end through the public API: host CSR in pinned memory -> build -> three runs -> host results
     e2e = None
@@ -392,7 +425,8 @@ def run_ours(a, rank, world, local_rank):
         cpu = cpu_baseline(g, roots, a.cpu_pr_iters)
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms / a.steps, "ms_per_step_with_kernel_events": ms_prof / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/u32", "data": "synthetic",
         "config": {"workload": f"rmat{a.scale}_" + "_".join(parts), "scale": a.scale, "edge_factor": 16, "vertices": V,
                    "edges": E, "partition_size": info["partition_size"], "partitions": k,

@@ -171,6 +171,11 @@ typedef struct {
        an iteration is not launched) */
     double kernel_ms[6];
     uint64_t kernel_launches[6];
+    uint64_t sc_vertices_scattered;  /* sum over iterations of V_a of the partitions scattered in SC mode */
+    uint64_t sc_edges_scattered;     /* sum over iterations of E_a of the partitions scattered in SC mode */
+    uint64_t gathered_vertices;      /* sum over iterations of the destinations the task gather visited
+                                        (every vertex of each gather task whose column had messages or
+                                        active vertices) */
 } gpop_run_stats;
 
 /* Fills opts with defaults: PageRank, d = 0.85, max_iters 1000, tol 0,

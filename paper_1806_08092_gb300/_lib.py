@@ -50,7 +50,9 @@ class RunStats(ctypes.Structure):
                 ("edges_scattered", ctypes.c_uint64), ("vertices_scattered", ctypes.c_uint64),
                 ("pc_partition_steps", ctypes.c_uint64), ("sc_partition_steps", ctypes.c_uint64),
                 ("model_bytes", ctypes.c_double), ("device_ms", ctypes.c_double), ("log_records", ctypes.c_uint64),
-                ("kernel_ms", ctypes.c_double * 6), ("kernel_launches", ctypes.c_uint64 * 6)]
+                ("kernel_ms", ctypes.c_double * 6), ("kernel_launches", ctypes.c_uint64 * 6),
+                ("sc_vertices_scattered", ctypes.c_uint64), ("sc_edges_scattered", ctypes.c_uint64),
+                ("gathered_vertices", ctypes.c_uint64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -118,6 +118,7 @@ struct Params {
     unsigned long long *t_task;  // per-task CTA durations (ns) or null
     unsigned long long *t_gpc;   // LOG_BOTH: CTA time of k_gather_pc (ns, all CTAs) or null
     unsigned long long *t_gsc;   // LOG_BOTH: CTA time of k_gather's SC passes (ns) or null
+    unsigned long long *gath;    // destinations visited by k_gather over the run
     uint4 *all_list;             // LOG_BOTH: units of every partition scattered this iteration
     float *feat;                 // LOG_BOTH: per-partition selector features [k][8]
     uint32_t *part_va;           // LOG_BOTH: V_a per partition
@@ -457,12 +458,13 @@ __global__ void k_task_stats(Params p) {
 __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
     __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_ub[kPlanThreads], s_ue[kPlanThreads], s_uq[kPlanThreads], s_uea[kPlanThreads];
-    __shared__ unsigned long long s_v[kPlanThreads / 32], s_e[kPlanThreads / 32];
+    __shared__ unsigned long long s_v[kPlanThreads / 32], s_e[kPlanThreads / 32], s_sv[kPlanThreads / 32],
+        s_se[kPlanThreads / 32];
     __shared__ double s_r[kPlanThreads / 32], s_b[kPlanThreads / 32];
     __shared__ uint32_t s_pc[kPlanThreads / 32], s_sc[kPlanThreads / 32], s_nl[kPlanThreads / 32], s_fb[kPlanThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t prev = p.epoch - 1;
-    unsigned long long tv = 0, te = 0;
+    unsigned long long tv = 0, te = 0, tsv = 0, tse = 0;
     double tr = 0.0, tb = 0.0;
     uint32_t npc = 0, nsc = 0, nnull = 0, nfb = 0, sc_base = 0, pc_base = 0;
 
@@ -504,6 +506,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
             if (Va > 0) p.gflag[q] = p.epoch;  // active partitions are gathered (reInit of Alg. 2)
             npc += (m == kModePC);
             nsc += (m == kModeSC);
+            if (m == kModeSC) {
+                tsv += Va;
+                tse += Ea;
+            }
             uint8_t act = m == kModePC ? kActPC : (p.pc_state[q] ? kActNull : kActSkip);
             nnull += (act == kActNull);
             p.action[q] = act;
@@ -536,6 +542,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
     for (int o = 16; o > 0; o >>= 1) {
         tv += __shfl_xor_sync(0xffffffffu, tv, o);
         te += __shfl_xor_sync(0xffffffffu, te, o);
+        tsv += __shfl_xor_sync(0xffffffffu, tsv, o);
+        tse += __shfl_xor_sync(0xffffffffu, tse, o);
         tr += __shfl_xor_sync(0xffffffffu, tr, o);
         tb += __shfl_xor_sync(0xffffffffu, tb, o);
         npc += __shfl_xor_sync(0xffffffffu, npc, o);
@@ -544,17 +552,17 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
     }
     if (lane == 0) {
-        s_v[wid] = tv; s_e[wid] = te; s_r[wid] = tr; s_b[wid] = tb;
+        s_v[wid] = tv; s_e[wid] = te; s_r[wid] = tr; s_b[wid] = tb; s_sv[wid] = tsv; s_se[wid] = tse;
         s_pc[wid] = npc; s_sc[wid] = nsc; s_nl[wid] = nnull; s_fb[wid] = nfb;
     }
     __syncthreads();
     __shared__ uint32_t s_done;
     if (threadIdx.x == 0) {
-        unsigned long long a = 0, b = 0;
+        unsigned long long a = 0, b = 0, sa = 0, sb = 0;
         double r = 0.0, by = 0.0;
         uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            a += s_v[i]; b += s_e[i]; r += s_r[i]; by += s_b[i];
+            a += s_v[i]; b += s_e[i]; r += s_r[i]; by += s_b[i]; sa += s_sv[i]; sb += s_se[i];
             c0 += s_pc[i]; c1 += s_sc[i]; c2 += s_nl[i]; c3 += s_fb[i];
         }
         uint32_t done = (a == 0) || (p.iter > p.max_iters);
@@ -565,6 +573,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         c.n_sc_units = sc_base;
         p.pc_prefix[p.k] = pc_base;
         c.pad = 0;
+        c.sc_v = sa;
+        c.sc_e = sb;
         *p.ctrl = c;
         p.ctrl_snap[(p.iter - 1) & 1] = c;  // read by the host once the plan has finished
         __threadfence_system();
@@ -1517,6 +1527,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
         const uint32_t gq = q << p.shift;
         const uint32_t gbase = gq + gt.d0;
         const uint32_t wv = min(width, p.V - gbase);  // destinations that exist
+        if (tid == 0 && p.gath) atomicAdd(p.gath, (unsigned long long)wv);
         // the column's PC result (pc_sum: written by its k_gather_pc task, or merged by k_merge_pc from the
         // partial vectors of a split column); none when no partition sent PC messages to the column this
         // iteration or the column has no PC in-edges.  Without SC pairs the filter reads it directly.
@@ -1793,6 +1804,7 @@ struct RunBuffers {
     uint4 *sc_list = nullptr;
     uint32_t *sc_gcur = nullptr, *sc_udone = nullptr, *pc_prefix = nullptr;
     uint32_t *task_sc_cnt = nullptr, *task_sc_list = nullptr, *pc_sum = nullptr;
+    unsigned long long *gath = nullptr;  // destinations visited by k_gather in the current run
     Control *ctrl = nullptr, *h_ctrl = nullptr, *d_ctrl_snap = nullptr;
     // LOG_BOTH only (allocated on first use)
     uint32_t *shadow = nullptr, *part_va = nullptr;
@@ -1815,7 +1827,7 @@ struct RunBuffers {
 static void release_runbufs(RunBuffers *rb) {
     void *ptrs[] = {rb->val, rb->lvl, rb->sval, rb->bits, rb->t_va, rb->t_stamp, rb->t_ea, rb->t_res,
                     rb->mode, rb->action, rb->sel_mode, rb->col_done, rb->gflag, rb->gflag_pc, rb->sc_list, rb->sc_gcur, rb->sc_udone, rb->pc_prefix, rb->counters,
-                    rb->ctrl, rb->task_sc_cnt, rb->task_sc_list, rb->pc_sum, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_gpc, rb->t_gsc,
+                    rb->ctrl, rb->task_sc_cnt, rb->task_sc_list, rb->pc_sum, rb->gath, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_gpc, rb->t_gsc,
                     rb->feat, rb->msrc, rb->lvl_ms};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -1854,6 +1866,7 @@ static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
     A(&rb->counters, 8);
     A(&rb->task_sc_cnt, g->ngt);
     A(&rb->pc_sum, g->V);
+    A(&rb->gath, 1);
     A(&rb->task_sc_list, g->nsub);
     A(&rb->ctrl, 1);
     // the plans' snapshots: two slots of mapped pinned memory that k_plan writes directly (no copy in the
@@ -1968,7 +1981,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     p.sub_cap = g->sub_cap; p.sub_task = g->sub_task; p.row_sub = g->row_sub; p.task_sub_ptr = g->task_sub_ptr;
     p.task_sc_cnt = rb->task_sc_cnt; p.task_sc_list = rb->task_sc_list;
     p.col_ntask = g->col_ntask; p.col_part0 = g->col_part0; p.pe = g->pe; p.pw = g->pw; p.pc_part = g->pc_part;
-    p.npct = g->npct; p.pc_sum = rb->pc_sum;
+    p.npct = g->npct; p.pc_sum = rb->pc_sum; p.gath = rb->gath;
     p.Ep = g->Ep; p.npng_p = g->npng_p;
     p.gtask = g->gtask; p.ngt = g->ngt; p.col_task = g->col_task;
     p.stask = g->stask; p.nst = g->nst; p.pc_state = g->pc_state;
@@ -2069,6 +2082,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     // split-SC cursors are zero at rest; reset them in case an earlier run stopped part-way
     GPOP_CUDA_TRY(cudaMemsetAsync(rb->sc_gcur, 0, 4ull * std::max<uint64_t>(g->nsub, 1), s));
     GPOP_CUDA_TRY(cudaMemsetAsync(rb->sc_udone, 0, 4ull * g->k, s));
+    GPOP_CUDA_TRY(cudaMemsetAsync(rb->gath, 0, 8, s));
     rb->rate_pc = rb->rate_sc = 0.0;
     const bool learned = p.policy == GPOP_MODE_LEARNED && p.selector;
     p.col_done = learned ? rb->col_done : nullptr;
@@ -2181,6 +2195,8 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         st.pc_partition_steps += c.n_pc;
         st.sc_partition_steps += c.n_sc;
         st.model_bytes += c.model_bytes;
+        st.sc_vertices_scattered += c.sc_v;
+        st.sc_edges_scattered += c.sc_e;
         return true;
     };
     // Each iteration: the plan, the host's read of its snapshot (mapped memory written by k_plan, no copy
@@ -2225,6 +2241,11 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     }
     st.iterations = iter;
     st.device_ms = ms;
+    {
+        unsigned long long gv = 0;
+        GPOP_CUDA_TRY(cudaMemcpy(&gv, rb->gath, 8, cudaMemcpyDeviceToHost));
+        st.gathered_vertices = gv;
+    }
     if (ALGO != ALG_MSBFS) {
         rb->state_algo = ALGO;
         rb->state_iter = base + iter;
@@ -2381,6 +2402,9 @@ extern "C" gpop_status gpop_run_msbfs(gpop_graph *h, const gpop_run_opts *o, con
         total.sc_partition_steps += st.sc_partition_steps;
         total.model_bytes += st.model_bytes;
         total.device_ms += st.device_ms;
+        total.sc_vertices_scattered += st.sc_vertices_scattered;
+        total.sc_edges_scattered += st.sc_edges_scattered;
+        total.gathered_vertices += st.gathered_vertices;
         total.log_records += st.log_records;
         for (int i = 0; i < 6; ++i) {
             total.kernel_ms[i] += st.kernel_ms[i];

@@ -62,6 +62,7 @@ struct Control {
     uint32_t error;                  // device check flags
     uint32_t n_sc_units;             // SC scatter work units (split hub partitions count several)
     uint32_t pad;
+    unsigned long long sc_v, sc_e;   // V_a and E_a of the partitions scattered in SC mode
 };
 
 // Static gather task: destinations [d0, d1) (local IDs) of column q, which have `entries` in-edges.
