@@ -50,6 +50,8 @@ def args_parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-pr-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bw-ratio", type=int, default=8,
+                    help="BW_PC / BW_SC of Eq. (mode) for BFS and SSSP (measured on GB300 by autotune.pick_bw_ratio)")
     ap.add_argument("--algos", default="pr,bfs,sssp",
                     help="parts of the step to run (profiling of one part); the reported metric needs all three")
     return ap.parse_args()
@@ -249,9 +251,9 @@ def run_ours(a, rank, world, local_rank):
         if "pr" in parts:
             out["pr"] = G.run("pagerank", max_iters=a.pr_max_iters, tol=a.pr_tol, profile=profile).stats
         if "bfs" in parts:
-            out["bfs"] = G.run("bfs", source=r, profile=profile).stats
+            out["bfs"] = G.run("bfs", source=r, profile=profile, bw_ratio=(a.bw_ratio, 1)).stats
         if "sssp" in parts:
-            out["sssp"] = G.run("sssp", source=r, profile=profile).stats
+            out["sssp"] = G.run("sssp", source=r, profile=profile, bw_ratio=(a.bw_ratio, 1)).stats
         return out
 
     for i in range(a.warmup):
@@ -382,8 +384,8 @@ def run_ours(a, rank, world, local_rank):
             r = my_roots[(a.warmup + i) % nsteps]
             He = gp.Graph.from_csr(rp_h.view(torch.uint64), col_h.view(torch.uint32), w_h, partition_size=a.partition)
             pr = He.run("pagerank", max_iters=a.pr_max_iters, tol=a.pr_tol, device_out=False)
-            He.run("bfs", source=r, device_out=False)
-            He.run("sssp", source=r, device_out=False)
+            He.run("bfs", source=r, device_out=False, bw_ratio=(a.bw_ratio, 1))
+            He.run("sssp", source=r, device_out=False, bw_ratio=(a.bw_ratio, 1))
             He.close()
             e_edges += E * pr.stats["iterations"] + 2 * te_of[r]
         torch.cuda.synchronize()
@@ -431,6 +433,7 @@ def run_ours(a, rank, world, local_rank):
         "config": {"workload": f"rmat{a.scale}_" + "_".join(parts), "scale": a.scale, "edge_factor": 16, "vertices": V,
                    "edges": E, "partition_size": info["partition_size"], "partitions": k,
                    "png_entries": npng, "r": npng / max(E, 1), "pr_tol_l1": a.pr_tol,
+                   "bw_ratio": f"{a.bw_ratio}/1 (BW_PC/BW_SC of Eq. (mode) for BFS and SSSP, measured on this GPU; the paper's CPUs: 2/1)",
                    "l2": f"inputs larger than L2 (layout {info['device_bytes'] / 1e9:.1f} GB vs 129 MB L2); no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "per_algo": per_algo,

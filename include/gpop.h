@@ -166,7 +166,7 @@ typedef struct {
     double device_ms;             /* CUDA-event time of the iteration loop */
     uint64_t log_records;         /* LOG_BOTH records written */
     /* with opts.profile_kernels: per kernel kind (0 plan (+ learned selection), 1 PC scatter,
-       2 SC scatter, 3 task gather + filter, 4 PC gather, 5 merge of split columns' PC partials) the
+       2 SC scatter (with its per-segment active-edge counts), 3 task gather + filter, 4 PC gather, 5 merge of split columns' PC partials) the
        summed CUDA-event duration and the number of launches (a kind the plan gives nothing to do in
        an iteration is not launched) */
     double kernel_ms[6];

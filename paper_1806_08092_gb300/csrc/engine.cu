@@ -49,7 +49,8 @@ constexpr int kScatterThreads = 256;    // k_scatter_sc
 constexpr int kScatterPcThreads = 512;  // k_scatter_pc
 constexpr int kPlanThreads = 1024;
 constexpr uint32_t kSent = 0xFFFFFFFFu;
-constexpr uint32_t kScUnitEdges = 1u << 12;  // active edges per SC scatter unit of a split partition
+constexpr uint32_t kScUnitEdges = 1u << 12;  // active edges per SC scatter unit (a partition with more is split)
+constexpr uint32_t kScSegs = 16;              // 1024-vertex segments per partition (P <= 16384)
 constexpr uint32_t kBigScBin = 2048;     // SC bins at least this large are folded by the whole gather CTA
 constexpr uint32_t kMaxBigScBins = 64;
 constexpr int kPcWarps = kPcGatherWarps;          // k_gather_pc consumer warps (one destination slice of a block each)
@@ -103,6 +104,7 @@ struct Params {
     uint8_t *mode, *action;
     uint32_t *gflag, *gflag_pc, *counters;
     uint4 *sc_list;                   // SC scatter units: (partition, unit, units, active edges)
+    uint32_t *sc_seg;                 // active out-edges of each 1024-vertex segment of the SC partitions [k][16]
     uint32_t *sc_gcur, *sc_udone;     // split SC partitions: bin cursors and finished units (zero at rest)
     Control *ctrl;
     Control *ctrl_snap;     // the plan's snapshot for the host: mapped pinned memory, slot (iter - 1) & 1
@@ -520,12 +522,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
             if (valid) p.pc_prefix[q] = pc_base + offp;
             pc_base += totp;
         }
-        // SC scatter units: a partition with many active edges is split into ranges of about
-        // max(kScUnitEdges, V_a) active edges, scattered by several CTAs (every unit first sums its
-        // partition's active out-edges per segment, about V_a loads, so a unit is never made smaller
-        // than that)
-        const unsigned long long unit = max((unsigned long long)kScUnitEdges, (unsigned long long)Va);
-        const uint32_t nu = Ea > 2ull * unit ? (uint32_t)min((unsigned long long)((Ea + unit - 1) / unit), 65535ull) : 1u;
+        // SC scatter units: a partition's active edges are cut into ranges of about kScUnitEdges, each
+        // scattered by one CTA (k_sc_segments has counted every segment's active edges, so a unit only
+        // visits the segments its range overlaps)
+        const uint32_t nu = (uint32_t)max(1ull, min((unsigned long long)((Ea + kScUnitEdges - 1) / kScUnitEdges), 65535ull));
         uint32_t total;
         const uint32_t nsc_u = (valid && m == kModeSC) ? nu : 0u;
         uint32_t off = block_excl_scan(nsc_u, s_warp, &total);
@@ -789,25 +789,58 @@ __global__ void __launch_bounds__(kScatterPcThreads) k_scatter_pc(Params p) {
 
 // --- SC scatter (Alg. 2 scatter in source-centric mode) ---------------------------------------
 
-// One CTA per work unit: a whole SC partition, or one range of about max(kScUnitEdges, V_a) active edges
-// of a partition with many (split partitions).  A unit first sums the active out-edges of each of its
-// partition's 1024-vertex segments and passes over the empty ones and those before its range.  The
-// partition's active vertices are taken in ascending order, 1024 at a time, and their out-edges
-// expanded one per thread; each pair goes to the sub-bin of its
-// (partition, gather task) at a cursor bumped once per distinct sub-bin per warp.  Whole partitions keep
-// their cursors in shared memory and publish the counts at the end; split partitions bump global cursors
-// (zero at rest), and their last unit to finish publishes the counts and resets the cursors.
+// Active out-edges of every 1024-vertex segment of the partitions scattered in SC mode this iteration (of
+// every scattered partition when a LOG_BOTH shadow pass times both modes), one warp per segment from the
+// frontier bits and the row offsets; the SC scatter's units find their edge ranges in these counts.
+__global__ void k_sc_segments(Params p) {
+    const uint32_t nseg = (p.P + 1023) / 1024;
+    const int lane = threadIdx.x & 31;
+    const uint64_t nw = (uint64_t)p.k * nseg, step = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t wg = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wg < nw; wg += step) {
+        const uint32_t q = (uint32_t)(wg / nseg), si = (uint32_t)(wg % nseg);
+        const uint8_t m = p.mode[q];
+        if (p.log_both ? m == kModeNone : m != kModeSC) continue;
+        const uint32_t gend = min((q << p.shift) + p.P, p.V);
+        const uint32_t gw = (q << p.shift) + si * 1024 + (uint32_t)lane * 32;
+        uint32_t word = gw < gend ? p.bits[gw >> 5] : 0u;
+        if (gw < gend && gend - gw < 32) word &= (1u << (gend - gw)) - 1u;
+        uint32_t cnt = 0;
+        if (word == 0xFFFFFFFFu) {
+            cnt = p.rowptr[gw + 32] - p.rowptr[gw];
+        } else {
+            while (word) {
+                const uint32_t u = gw + (uint32_t)(__ffs(word) - 1);
+                word &= word - 1;
+                cnt += p.rowptr[u + 1] - p.rowptr[u];
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) p.sc_seg[(uint64_t)q * kScSegs + si] = cnt;
+    }
+}
+
+// One CTA per work unit: about kScUnitEdges consecutive active edges of one SC partition (in the order of
+// its active vertices), or all of a partition with fewer.  The unit passes over the segments before its
+// range (their active-edge counts come from k_sc_segments); for each segment it overlaps, all threads
+// build the segment's active vertices in ascending order with the prefix of their out-degrees (four
+// vertices per thread), then expand the unit's edges one per thread; each pair goes to the sub-bin of its
+// (partition, gather task) at a cursor bumped once per distinct sub-bin per warp.  A partition of one unit
+// keeps its cursors in shared memory and publishes the counts at the end; the units of a split partition
+// bump global cursors (zero at rest), and the last unit to finish publishes the counts and resets them.
 template <int ALGO, bool B16>
 __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
-    extern __shared__ uint32_t s_cursor[];  // one insertion point per bin of the row (whole partitions)
-    __shared__ uint32_t s_list[1024];       // active local IDs of the current 1024-vertex segment
-    __shared__ uint32_t s_pref[1025];       // exclusive prefix of their out-degrees
+    extern __shared__ uint32_t s_cursor[];  // per sub-bin of the row: its next free slot (a partition of one unit)
+                                            // or its first slot (a split partition, cursors in global memory)
+    // the current segment's active vertices, ascending: exclusive prefix of their out-degrees, first
+    // out-edge (row offset) and message value (scatterFunc)
+    __shared__ uint32_t s_pref[1025], s_row[1024], s_msg[1024];
     __shared__ uint32_t s_warp[33];
-    __shared__ uint32_t s_sege[16];         // active out-edges of each 1024-vertex segment of the partition
-    __shared__ uint32_t s_task, s_nact, s_last;
+    __shared__ uint32_t s_task, s_last;
     __shared__ unsigned long long s_t0;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const uint32_t nunits = *p.list_count;
+    const uint32_t nseg = (p.P + 1023) / 1024;
     for (;;) {
         if (threadIdx.x == 0) s_task = atomicAdd(&p.counters[p.counter_slot], 1u);
         __syncthreads();
@@ -822,65 +855,57 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
         const uint64_t ub = split ? (uint64_t)un.w * (un.y + 1) / un.z : ~0ull;
         if (p.t_task && threadIdx.x == 0) s_t0 = globaltimer();
         const uint32_t rb0 = p.row_sub[part], nbr = p.row_sub[part + 1] - rb0;
-        if (!split)
-            for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) s_cursor[i] = 0;
-        uint32_t *cur = split ? p.sc_gcur + rb0 : s_cursor;
+        // the row's sub-bin first slots are staged when the unit has at least as many edges as the row has
+        // sub-bins (and always for a split partition); otherwise cursors count from 0 and the leader of each
+        // warp's group looks its sub-bin up
+        const bool staged = split || un.w >= nbr;
+        for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) s_cursor[i] = staged ? p.sub_cap[rb0 + i] : 0u;
+        uint32_t *gcur = p.sc_gcur + rb0;  // a split partition's cursors (relative to the sub-bin's first slot)
         const uint32_t g0 = part << p.shift;
         const uint32_t gend = min(g0 + p.P, p.V);
-        // active out-edges of every segment (one warp per segment, from the frontier bits and the row
-        // offsets), so that empty segments, and those before a split unit's range, are passed over
-        // without building their active lists
-        const uint32_t nseg = (gend - g0 + 1023) / 1024;  // at most 16 (P <= 16384)
-        for (uint32_t si = wid; si < nseg; si += kScatterThreads / 32) {
-            const uint32_t gw = g0 + si * 1024 + (uint32_t)lane * 32;
-            uint32_t word = gw < gend ? p.bits[gw >> 5] : 0u;
-            uint32_t e = 0;
-            if (word == 0xFFFFFFFFu && gw + 32 <= gend) {
-                e = p.rowptr[gw + 32] - p.rowptr[gw];
-            } else {
-                while (word) {
-                    const uint32_t u = gw + (uint32_t)(__ffs(word) - 1);
-                    word &= word - 1;
-                    e += p.rowptr[u + 1] - p.rowptr[u];
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-            if (lane == 0) s_sege[si] = e;
-        }
-        __syncthreads();
         uint64_t run0 = 0;  // active edges of the partition before this segment
-        for (uint32_t seg = g0, si = 0; seg < gend && run0 < ub; seg += 1024, ++si) {
-            const uint32_t seg_e = s_sege[si];
-            if (seg_e == 0 || run0 + seg_e <= ua) {  // nothing to scatter here (uniform over the CTA)
+        for (uint32_t si = 0; si < nseg && run0 < ub; ++si) {
+            const uint32_t seg_e = p.sc_seg[(uint64_t)part * kScSegs + si];  // the same for every thread
+            if (seg_e == 0 || run0 + seg_e <= ua) {  // nothing to scatter here
                 run0 += seg_e;
                 continue;
             }
-            // active vertices of this segment, ascending
-            if (threadIdx.x < 32) {
-                uint32_t gw = seg + threadIdx.x * 32;
-                uint32_t word = gw < gend ? p.bits[gw >> 5] : 0u;
-                uint32_t c = __popc(word);
-                uint32_t off = warp_incl_scan(c, lane) - c;
-                while (word) {
-                    int b = __ffs(word) - 1;
-                    word &= word - 1;
-                    s_list[off++] = gw + b;
+            // this segment's active vertices (thread i: vertices 4i .. 4i+3 of the segment) and the
+            // exclusive prefix of their out-degrees
+            const uint32_t v0 = g0 + si * 1024 + threadIdx.x * 4;
+            uint32_t nib = 0;
+            if (v0 < gend) {
+                nib = (p.bits[v0 >> 5] >> (v0 & 31)) & 0xFu;
+                if (gend - v0 < 4) nib &= (1u << (gend - v0)) - 1u;
+            }
+            uint32_t rp[5] = {0, 0, 0, 0, 0}, cnt = 0, esum = 0;
+            if (nib) {
+                rp[4] = p.rowptr[min(v0 + 4, p.V)];
+                if (v0 + 4 <= p.V) {
+                    const uint4 r = *reinterpret_cast<const uint4 *>(p.rowptr + v0);
+                    rp[0] = r.x; rp[1] = r.y; rp[2] = r.z; rp[3] = r.w;
+                } else {
+                    for (uint32_t c = 0; c < 4; ++c) rp[c] = v0 + c <= p.V ? p.rowptr[v0 + c] : rp[4];
                 }
-                if (lane == 31) s_nact = off;
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if ((nib >> c) & 1u) {
+                        ++cnt;
+                        esum += rp[c + 1] - rp[c];
+                    }
             }
-            __syncthreads();
-            const uint32_t nact = s_nact;
-            // out-degree prefix
-            uint32_t total = 0;
-            for (uint32_t base = 0; base < nact; base += blockDim.x) {
-                uint32_t i = base + threadIdx.x;
-                uint32_t d = i < nact ? p.rowptr[s_list[i] + 1] - p.rowptr[s_list[i]] : 0;
-                uint32_t tt;
-                uint32_t ex = block_excl_scan(d, s_warp, &tt);
-                if (i < nact) s_pref[i] = total + ex;
-                total += tt;
-            }
+            uint32_t nact, total;
+            uint32_t k = block_excl_scan(cnt, s_warp, &nact);
+            uint32_t ek = block_excl_scan(esum, s_warp, &total);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if ((nib >> c) & 1u) {  // list entry k: edge prefix, row offset, message value
+                    s_pref[k] = ek;
+                    s_row[k] = rp[c];
+                    s_msg[k] = p.sval[v0 + c];
+                    ++k;
+                    ek += rp[c + 1] - rp[c];
+                }
             if (threadIdx.x == 0) s_pref[nact] = total;
             __syncthreads();
             // this segment's active edges [run0, run0 + total) that belong to the unit
@@ -898,12 +923,11 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
                         uint32_t mid = (lo + hi) >> 1;
                         if (s_pref[mid] <= e) lo = mid; else hi = mid;
                     }
-                    uint32_t u = s_list[lo];
-                    uint32_t edge = p.rowptr[u] + (e - s_pref[lo]);
-                    uint32_t dst = p.col[edge];
+                    const uint32_t edge = s_row[lo] + (e - s_pref[lo]);
+                    const uint32_t dst = p.col[edge];
                     lb = p.esub[edge];
                     dloc = dst & (p.P - 1);
-                    val = p.sval[u];
+                    val = s_msg[lo];
                     if (ALGO == ALG_SSSP) val = Op<ALGO>::weigh(val, p.w[edge]);
                 }
                 // warp-aggregated insertion: one cursor bump per distinct bin in the warp
@@ -911,10 +935,13 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
                 int leader = __ffs(peers) - 1;
                 uint32_t rank = __popc(peers & ((1u << lane) - 1));
                 uint32_t basepos = 0;
-                if (live && lane == leader) basepos = atomicAdd(&cur[lb], (uint32_t)__popc(peers));
+                if (live && lane == leader)
+                    basepos = split    ? s_cursor[lb] + atomicAdd(&gcur[lb], (uint32_t)__popc(peers))
+                              : staged ? atomicAdd(&s_cursor[lb], (uint32_t)__popc(peers))
+                                       : p.sub_cap[rb0 + lb] + atomicAdd(&s_cursor[lb], (uint32_t)__popc(peers));
                 basepos = __shfl_sync(0xffffffffu, basepos, leader);
                 if (live) {
-                    slot = p.sub_cap[rb0 + lb] + basepos + rank;
+                    slot = basepos + rank;
                     if (B16) reinterpret_cast<uint32_t *>(p.scpair)[slot] = dloc | (to_bf16(val) << 16);
                     else p.scpair[slot] = make_uint2(dloc, val);
                 }
@@ -936,7 +963,9 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
         }
         if (publish) {
             for (uint32_t i = threadIdx.x; i < nbr; i += blockDim.x) {
-                const uint32_t c = split ? atomicExch(&cur[i], 0u) : cur[i];
+                const uint32_t c = split    ? atomicExch(&gcur[i], 0u)
+                                   : staged ? s_cursor[i] - p.sub_cap[rb0 + i]
+                                            : s_cursor[i];
                 if (c && !p.dry) {
                     uint32_t b = rb0 + i;
                     p.sccnt[b] = c;
@@ -1802,7 +1831,7 @@ struct RunBuffers {
     uint32_t *col_done = nullptr;
     uint32_t *gflag = nullptr, *gflag_pc = nullptr, *counters = nullptr;
     uint4 *sc_list = nullptr;
-    uint32_t *sc_gcur = nullptr, *sc_udone = nullptr, *pc_prefix = nullptr;
+    uint32_t *sc_gcur = nullptr, *sc_udone = nullptr, *pc_prefix = nullptr, *sc_seg = nullptr;
     uint32_t *task_sc_cnt = nullptr, *task_sc_list = nullptr, *pc_sum = nullptr;
     unsigned long long *gath = nullptr;  // destinations visited by k_gather in the current run
     Control *ctrl = nullptr, *h_ctrl = nullptr, *d_ctrl_snap = nullptr;
@@ -1826,7 +1855,7 @@ struct RunBuffers {
 
 static void release_runbufs(RunBuffers *rb) {
     void *ptrs[] = {rb->val, rb->lvl, rb->sval, rb->bits, rb->t_va, rb->t_stamp, rb->t_ea, rb->t_res,
-                    rb->mode, rb->action, rb->sel_mode, rb->col_done, rb->gflag, rb->gflag_pc, rb->sc_list, rb->sc_gcur, rb->sc_udone, rb->pc_prefix, rb->counters,
+                    rb->mode, rb->action, rb->sel_mode, rb->col_done, rb->gflag, rb->gflag_pc, rb->sc_list, rb->sc_gcur, rb->sc_udone, rb->pc_prefix, rb->sc_seg, rb->counters,
                     rb->ctrl, rb->task_sc_cnt, rb->task_sc_list, rb->pc_sum, rb->gath, rb->shadow, rb->all_list, rb->part_va, rb->part_ea, rb->t_pc, rb->t_sc, rb->t_gpc, rb->t_gsc,
                     rb->feat, rb->msrc, rb->lvl_ms};
     for (void *q : ptrs)
@@ -1861,6 +1890,7 @@ static gpop_status alloc_runbufs(Graph *g, RunBuffers **out) {
     A(&rb->gflag_pc, g->k);
     A(&rb->sc_list, sc_unit_capacity(g));
     A(&rb->sc_gcur, std::max<uint64_t>(g->nsub, 1));
+    A(&rb->sc_seg, (uint64_t)g->k * kScSegs);
     A(&rb->sc_udone, g->k);
     A(&rb->pc_prefix, (uint64_t)g->k + 1);
     A(&rb->counters, 8);
@@ -1988,7 +2018,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     p.val = rb->val; p.lvl = rb->lvl; p.sval = rb->sval; p.bits = rb->bits;
     p.t_va = rb->t_va; p.t_ea = rb->t_ea; p.t_res = rb->t_res; p.t_stamp = rb->t_stamp;
     p.mode = rb->mode; p.action = rb->action; p.sel_mode = rb->sel_mode; p.gflag = rb->gflag; p.gflag_pc = rb->gflag_pc;
-    p.sc_list = rb->sc_list; p.sc_gcur = rb->sc_gcur; p.sc_udone = rb->sc_udone; p.pc_prefix = rb->pc_prefix; p.counters = rb->counters; p.ctrl = rb->ctrl; p.ctrl_snap = rb->d_ctrl_snap;
+    p.sc_list = rb->sc_list; p.sc_seg = rb->sc_seg; p.sc_gcur = rb->sc_gcur; p.sc_udone = rb->sc_udone; p.pc_prefix = rb->pc_prefix; p.counters = rb->counters; p.ctrl = rb->ctrl; p.ctrl_snap = rb->d_ctrl_snap;
     p.selector = (o->mode == GPOP_MODE_LEARNED) ? selector_device_params_transposed() : nullptr;
     p.list = rb->sc_list; p.list_count = &rb->ctrl->n_sc_units; p.counter_slot = 0; p.dry = 0; p.t_task = nullptr;
     p.t_gpc = nullptr;
@@ -2145,7 +2175,10 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         if (prof && first_select) st.kernel_launches[0] += 1;  // k_select
     };
     // scatter and gather of one iteration, as the plan c decided
+    const int grid_seg = std::max(1, std::min((int)(((uint64_t)g->k * ((g->P + 1023) / 1024) + 7) / 8), 16 * g->num_sms));
     auto launch_work = [&](const Params &pp, const Control &c) -> cudaError_t {
+        // per-segment active edges of the partitions the SC scatter (or the LOG_BOTH shadow) will visit
+        if (p.log_both || c.n_sc > 0) timed(2, [&] { k_sc_segments<<<grid_seg, 256, 0, s>>>(pp); });
         if (p.log_both) {
             // time both modes for every partition picked this iteration (shadow launches first:
             // the real SC scatter below rewrites the same bins with the same pairs)

@@ -60,3 +60,26 @@ def test_a_candidate_whose_runs_fail_is_listed_and_skipped(monkeypatch):
     assert best == 2048
     assert table[1][0] == 16384 and table[1][1] is None and "out of memory" in table[1][3]
     assert _FakeGraph.closed == [2048, 16384]  # the failing layout is released too
+
+
+class _FakeRatioGraph:
+    """A built graph whose run time depends on the bandwidth ratio (U-shaped, minimum at 8)."""
+    def __init__(self):
+        self.calls = []
+
+    def run(self, algo, bw_ratio=(2, 1), **kw):
+        self.calls.append((algo, bw_ratio))
+        r = bw_ratio[0] / bw_ratio[1]
+        if r == 0:
+            raise GpopError(1, "bandwidth ratio must be positive")
+        return _FakeRun({"bfs": 1.0, "sssp": 3.0}[algo] * (1.0 + abs(__import__("math").log2(r / 8.0)) / 4))
+
+
+def test_bw_ratio_picks_the_fastest_and_lists_rejected():
+    G = _FakeRatioGraph()
+    best, table = autotune.pick_bw_ratio(G, runs=[("bfs", {}), ("sssp", {})], candidates=(0, 2, 8, 32), reps=3)
+    assert best == (8, 1)
+    assert table[0][0] == 0 and table[0][1] is None and "positive" in table[0][2]
+    assert [t[0] for t in table[1:]] == [2, 8, 32] and table[2][1] == 4.0
+    # every candidate's runs are timed at its own ratio: one warm-up + reps per run
+    assert G.calls.count(("bfs", (8, 1))) == 4 and G.calls.count(("sssp", (32, 1))) == 4

@@ -293,6 +293,25 @@ def test_partition_size_autotuner():
     assert np.array_equal(Gd.run("bfs", source=root).values.cpu().numpy(), O.bfs(g, root)[0])
 
 
+def test_bw_ratio_autotuner():
+    # every candidate ratio is timed through the library on one layout; the results at any ratio are the
+    # exact ones (the ratio only moves partitions between the modes)
+    from paper_1806_08092_gb300.autotune import pick_bw_ratio
+    g = gg.rmat(14).with_weights()
+    root = int(gg.roots(g, 1)[0])
+    Gd = G(g, 1024)
+    best, table = pick_bw_ratio(Gd, runs=[("bfs", {"source": root}), ("sssp", {"source": root})],
+                                candidates=(1, 2, 8, 64), reps=2)
+    assert [t[0] for t in table] == [1, 2, 8, 64] and all(t[1] is not None for t in table)
+    assert best == (min(table, key=lambda t: t[1])[0], 1)
+    level, parent = O.bfs(g, root)
+    for ratio in (1, 8, 64):
+        r = Gd.run("bfs", source=root, bw_ratio=(ratio, 1))
+        assert np.array_equal(r.values.cpu().numpy(), level) and np.array_equal(r.parent.cpu().numpy(), parent)
+        t2 = O.gpop(g, 1024, "bfs", root, bw_ratio=(ratio, 1))
+        assert np.array_equal(Gd.run("bfs", source=root, bw_ratio=(ratio, 1), trace=True).modes, t2.modes)
+
+
 # --- parallel Nibble (Alg. 4) ---------------------------------------------------------------------
 # FP32 on the GPU against the FP64 oracle: PR values are probabilities (they sum to 1), compared in
 # absolute terms.  The threshold PR >= eps deg is decided on FP32 values on the GPU and on FP64 values
