@@ -52,6 +52,8 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bw-ratio", type=int, default=8,
                     help="BW_PC / BW_SC of Eq. (mode) for BFS and SSSP (measured on GB300 by autotune.pick_bw_ratio)")
+    ap.add_argument("--selector-scale", type=int, default=25,
+                    help="RMAT scale of the learned-vs-analytic comparison (0: skip it)")
     ap.add_argument("--algos", default="pr,bfs,sssp",
                     help="parts of the step to run (profiling of one part); the reported metric needs all three")
     return ap.parse_args()
@@ -394,29 +396,42 @@ def run_ours(a, rank, world, local_rank):
                "d2h_bytes_per_step": int(d2h), "steps": a.e2e_steps,
                "includes": "H2D of the CSR from pinned memory, gpop_graph_build, three gpop_run calls, D2H of results"}
 
-    # learned vs analytic mode choice (outside the timed region): BFS and SSSP from two roots on this
-    # graph, median of 3 runs each, with the selector trained by selector_train.py
+    # learned vs analytic mode choice (outside the timed region), on the configuration the selector is
+    # evaluated on: BFS and SSSP on RMAT-25 from two roots, median of 5 runs each, with Eq. (mode) at the
+    # paper's BW_PC/BW_SC = 2/1 (the model the selector replaces), the trained selector, and Eq. (mode) at
+    # the ratio measured on this GPU
     sel = None
-    if rank == 0 and os.path.exists(SELECTOR) and ("bfs" in parts or "sssp" in parts):
+    if rank == 0 and os.path.exists(SELECTOR) and ("bfs" in parts or "sssp" in parts) and a.selector_scale > 0:
+        import graphgen as gg
+        g25 = gg.rmat(a.selector_scale).with_weights(hi=255)
+        G25 = gp.Graph.from_csr(g25.row_ptr, g25.col, g25.weights, partition_size=a.partition)
         params = np.fromfile(SELECTOR, dtype=np.float32)
         gp.selector_set(params)
         try:
-            t = {"analytic": 0.0, "learned": 0.0}
+            t = {"analytic": 0.0, "learned": 0.0, "calibrated": 0.0}
             same = True
-            for r in roots[:2]:
+            fallbacks = 0
+            for r in gg.roots(g25, 2):
                 for algo in ("bfs", "sssp"):
                     modes = {}
-                    for mode in ("analytic", "learned"):
-                        ms_ = [G.run(algo, source=int(r), mode=mode, trace=True) for _ in range(3)]
-                        t[mode] += float(np.median([x.stats["device_ms"] for x in ms_]))
-                        modes[mode] = ms_[-1].modes
+                    for mode in ("analytic", "learned", "calibrated"):
+                        kw = {"bw_ratio": (a.bw_ratio, 1)} if mode == "calibrated" else {}
+                        runs_ = [G25.run(algo, source=int(r), mode="learned" if mode == "learned" else "analytic",
+                                         trace=True, **kw) for _ in range(5)]
+                        t[mode] += float(np.median([x.stats["device_ms"] for x in runs_]))
+                        modes[mode] = runs_[-1].modes
                     same &= bool(np.array_equal(modes["analytic"], modes["learned"]))
             sel = {"speedup": t["analytic"] / t["learned"], "analytic_ms": t["analytic"], "learned_ms": t["learned"],
-                   "same_modes": same, "workload": f"rmat{a.scale} BFS + SSSP, 2 roots, median of 3 runs each",
+                   "calibrated_ms": t["calibrated"], "calibrated_speedup": t["analytic"] / t["calibrated"],
+                   "same_modes": same,
+                   "workload": f"rmat{a.selector_scale} BFS + SSSP, 2 roots, median of 5 runs each; analytic = Eq. (mode) "
+                               f"at BW_PC/BW_SC 2/1, calibrated = Eq. (mode) at {a.bw_ratio}/1",
                    "selector": "selector_rmat.f32: MLP 8-32-32-1 trained by selector_train.py on LOG_BOTH timings "
-                               "of BFS/SSSP on RMAT 20-23 and uniform graphs"}
+                               "of BFS/SSSP on RMAT 20-24 and uniform graphs"}
         finally:
             gp.selector_set(None)
+            G25.close()
+            del g25
 
     if rank != 0:
         if dist:

@@ -1933,11 +1933,13 @@ static int persistent_grid(K kernel, int threads, size_t smem, int num_sms) {
 }
 
 // LOG_BOTH: turns this iteration's per-task CTA durations into one record per scattered partition:
-// 8 features, t_PC and t_SC in CTA-microseconds (scatter of that mode + that mode's share of the
-// gather, attributed by gather bytes at the iteration's measured gather time per byte), the mode
-// Eq. (mode) chose, the partition and the iteration.
+// 8 features, t_PC and t_SC in microseconds (the partition's share of that mode's shadow scatter wall
+// time, in proportion to its CTA time there, + that mode's share of the gather, attributed by gather bytes
+// at the iteration's measured gather SM time per byte), the mode Eq. (mode) chose, the partition and the
+// iteration.  occ: resident CTAs per SM of k_scatter_pc, k_scatter_sc and k_gather; ev: events before the
+// shadow PC scatter, between the shadows and after the shadow SC scatter.
 static gpop_status log_iteration(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cudaStream_t s, uint32_t iter,
-                                 gpop_run_stats *st) {
+                                 gpop_run_stats *st, const double occ[3], cudaEvent_t const ev[3]) {
     const uint32_t k = g->k;
     std::vector<float> feat(8ull * k);
     std::vector<uint32_t> va(k);
@@ -1959,6 +1961,19 @@ static gpop_status log_iteration(Graph *g, RunBuffers *rb, const gpop_run_opts *
     std::vector<double> pc_ns(k, 0.0);
     for (uint32_t t = 0; t < g->nst; ++t)
         if (mode[stask[t].p] != kModeNone) pc_ns[stask[t].p] += (double)tpc[t];
+    // each shadow scatter's wall time (CUDA events around it), shared among the partitions in proportion to
+    // their CTA times: the scatter part of a label then adds up to that mode's measured wall time
+    float w_pc_ms = 0.f, w_sc_ms = 0.f;
+    GPOP_CUDA_TRY(cudaEventElapsedTime(&w_pc_ms, ev[0], ev[1]));
+    GPOP_CUDA_TRY(cudaEventElapsedTime(&w_sc_ms, ev[1], ev[2]));
+    double sum_pc = 0.0, sum_sc = 0.0;
+    for (uint32_t q = 0; q < k; ++q)
+        if (mode[q] != kModeNone) {
+            sum_pc += pc_ns[q];
+            sum_sc += (double)tsc[q];
+        }
+    const double f_pc = sum_pc > 0 ? 1e6 * w_pc_ms / sum_pc : 1.0 / occ[0];
+    const double f_sc = sum_sc > 0 ? 1e6 * w_sc_ms / sum_sc : 1.0 / occ[1];
     // gather time per mode, attributed to the partitions of that mode by the bytes their messages make
     // the gather read (PC: 4 B per message value + 4 B per destination entry, folded by k_gather_pc; SC:
     // 8 B per pair, folded by k_gather's SC pass); the mode Eq. (mode) did not pick is charged at the last
@@ -1971,15 +1986,18 @@ static gpop_status log_iteration(Graph *g, RunBuffers *rb, const gpop_run_opts *
         if (mode[q] == kModePC) bytes_pc += gb(q, kModePC);
         if (mode[q] == kModeSC) bytes_sc += gb(q, kModeSC);
     }
+    // CTA times become SM times (divided by the kernel's resident CTAs per SM: k_gather_pc has one per SM,
+    // the SC scatter and the task gather several), so that both modes are charged in the unit that adds up
+    // to wall time on a full GPU
     if (bytes_pc > 0) rb->rate_pc = (double)tgpc[0] / bytes_pc;
-    if (bytes_sc > 0) rb->rate_sc = (double)tgsc[0] / bytes_sc;
+    if (bytes_sc > 0) rb->rate_sc = (double)tgsc[0] / occ[2] / bytes_sc;
     const double rpc = rb->rate_pc > 0 ? rb->rate_pc : rb->rate_sc, rsc = rb->rate_sc > 0 ? rb->rate_sc : rb->rate_pc;
     for (uint32_t q = 0; q < k; ++q) {
         if (mode[q] == kModeNone || st->log_records >= o->log_capacity) continue;
         float *r = o->log_buffer + st->log_records * GPOP_LOG_RECORD_FLOATS;
         for (int i = 0; i < 8; ++i) r[i] = feat[8ull * q + i];
-        r[8] = (float)((pc_ns[q] + rpc * gb(q, kModePC)) / 1e3);
-        r[9] = (float)(((double)tsc[q] + rsc * gb(q, kModeSC)) / 1e3);
+        r[8] = (float)((pc_ns[q] * f_pc + rpc * gb(q, kModePC)) / 1e3);
+        r[9] = (float)(((double)tsc[q] * f_sc + rsc * gb(q, kModeSC)) / 1e3);
         r[10] = (float)mode[q];
         r[11] = (float)q;
         r[12] = (float)iter;
@@ -2137,6 +2155,10 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     // next host synchronisation (which the plan's control read provides every iteration)
     // Launches between two host synchronisations form a chain of events: one record before the first
     // launch and one after each, so that launch j takes from event j to event j + 1.
+    // LOG_BOTH: events around the two shadow scatters of an iteration (their wall times)
+    cudaEvent_t lev[3] = {};
+    if (p.log_both)
+        for (auto &ev : lev) GPOP_CUDA_TRY(cudaEventCreate(&ev));
     const bool prof = o->profile_kernels != 0;
     cudaEvent_t kev[8] = {};
     int kind_of[7] = {};
@@ -2186,12 +2208,15 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
             cudaMemsetAsync(rb->t_gsc, 0, 8, s);
             Params q1 = pp;
             q1.pdata = rb->shadow; q1.dry = 1; q1.counter_slot = 3; q1.t_task = rb->t_pc;
+            cudaEventRecord(lev[0], s);
             k_scatter_pc<B16><<<grid_pc, kScatterPcThreads, spc_smem, s>>>(q1);
+            cudaEventRecord(lev[1], s);
             Params q2 = pp;
             q2.dry = 1; q2.counter_slot = 4; q2.list = rb->all_list; q2.list_count = &rb->counters[7];
             q2.t_task = rb->t_sc;
             cudaMemsetAsync(rb->t_sc, 0, 8ull * g->k, s);  // split partitions add their units' CTA times
             k_scatter_sc<ALGO, B16><<<grid_sc, kScatterThreads, sc_smem, s>>>(q2);
+            cudaEventRecord(lev[2], s);
         }
         Params ps = pp;
         ps.counter_slot = 1;
@@ -2254,7 +2279,9 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         ce = launch_work(p, c);
         if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(ce)); break; }
         if (p.log_both) {
-            status = log_iteration(g, rb, o, s, iter, &st);
+            const double occ[3] = {(double)grid_pc / g->num_sms, (double)grid_sc / g->num_sms,
+                                   (double)grid_ga / g->num_sms};
+            status = log_iteration(g, rb, o, s, iter, &st, occ, lev);
             if (status != GPOP_OK) break;
         }
     }
@@ -2264,6 +2291,8 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         resolve();
         for (auto &ev : kev) cudaEventDestroy(ev);
     }
+    if (p.log_both)
+        for (auto &ev : lev) cudaEventDestroy(ev);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
     cudaEventDestroy(ev0);

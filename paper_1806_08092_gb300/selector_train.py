@@ -1,7 +1,7 @@
 """Train and evaluate the learned SC/PC selector.
 
 1. collect: run BFS and SSSP with GPOP_MODE_LOG_BOTH on training graphs; every scattered partition of
-   every iteration yields one record (8 features, t_PC, t_SC in CTA-microseconds, chosen mode, ...).
+   every iteration yields one record (8 features, t_PC, t_SC in SM-microseconds, chosen mode, ...).
 2. train: fit y = log(t_PC / t_SC) with the library's GPU training kernels (gpop_selector_train).
 3. evaluate: end-to-end time of BFS and SSSP with Eq. (mode) (analytic) and with the trained MLP
    (learned) on a held-out graph, same GPU, median over repetitions; plus the mispredicted-bytes regret
@@ -23,7 +23,7 @@ import time
 
 import numpy as np
 
-from . import Graph, selector_set, selector_train
+from . import Graph, SELECTOR_WEIGHTS as GPOP_WEIGHTS, selector_set, selector_train
 
 
 def _gen():
@@ -34,7 +34,7 @@ def _gen():
     return graphgen
 
 
-def training_graphs(scales=(20, 21, 22, 23), uniform_scales=(21, 22)):
+def training_graphs(scales=(20, 21, 22, 23, 24), uniform_scales=(21, 22)):
     gg = _gen()
     for s in scales:
         yield f"rmat{s}", gg.rmat(s).with_weights()
@@ -66,12 +66,31 @@ def targets(records):
     return np.log(np.maximum(records[:, 8], 1e-3) / np.maximum(records[:, 9], 1e-3)).astype(np.float32)
 
 
+# features that scale with the graph (log1p E^p, log1p n_png, log1p k): the network extrapolates in them
+# (it is piecewise linear), so they get no range limit; the others keep 10 % of their range as margin
+SCALE_FEATURES = (2, 5, 6)
+
+
+def widen_ranges(params):
+    nw = GPOP_WEIGHTS
+    p = np.array(params, dtype=np.float32).copy()
+    fmin, fmax = p[nw + 16:nw + 24], p[nw + 24:nw + 32]
+    span = fmax - fmin
+    fmin -= 0.1 * span
+    fmax += 0.1 * span
+    for k in SCALE_FEATURES:
+        fmin[k], fmax[k] = -1e30, 1e30  # no limit (parameters must be finite)
+    p[nw + 16:nw + 24], p[nw + 24:nw + 32] = fmin, fmax
+    return p
+
+
 def train(records, epochs=3000, lr=3e-3, seed=7):
-    return selector_train(records[:, :8], targets(records), epochs=epochs, lr=lr, seed=seed)
+    params, loss = selector_train(records[:, :8], targets(records), epochs=epochs, lr=lr, seed=seed)
+    return widen_ranges(params), loss
 
 
 def regret_report(params, records):
-    """Extra time (CTA-us) over the per-record best mode, for Eq. (mode) and for the trained MLP."""
+    """Extra time (SM-us) over the per-record best mode, for Eq. (mode) and for the trained MLP."""
     t_pc, t_sc = records[:, 8].astype(np.float64), records[:, 9].astype(np.float64)
     best = np.minimum(t_pc, t_sc)
     model_pc = records[:, 7] <= 0  # feature 7: log of Eq. (mode)'s cost ratio; <= 0 means PC
@@ -89,26 +108,37 @@ def regret_report(params, records):
             "agree_with_best_learned": float(np.mean(learned_pc == (t_pc <= t_sc)))}
 
 
-def evaluate(g, params, partition_size=16384, roots=4, reps=5, algos=("bfs", "sssp"), run_kw=None):
-    """Median device time per (root, algorithm) with Eq. (mode) and with the trained selector."""
+def evaluate(g, params, partition_size=16384, roots=4, reps=5, algos=("bfs", "sssp"), run_kw=None,
+             calibrated_ratio=(8, 1)):
+    """Median device time per (root, algorithm) with Eq. (mode) at the paper's BW_PC/BW_SC = 2 (the model
+    the selector replaces), with the trained selector, and with Eq. (mode) at the ratio measured on this GPU
+    (autotune.pick_bw_ratio); whether the selector's per-partition modes differ from Eq. (mode)'s."""
     gg = _gen()
     G = Graph.from_csr(g.row_ptr, g.col, g.weights, partition_size=partition_size)
-    out = {"analytic_ms": 0.0, "learned_ms": 0.0, "fallbacks": 0}
+    out = {"analytic_ms": 0.0, "learned_ms": 0.0, "calibrated_ms": 0.0, "fallbacks": 0, "same_modes": True}
     selector_set(params)
     try:
         for root in gg.roots(g, roots):
             for algo in algos:
-                t = {"analytic": [], "learned": []}
+                t = {"analytic": [], "learned": [], "calibrated": []}
+                modes = {}
                 for _ in range(reps):
-                    for mode in ("analytic", "learned"):
-                        r = G.run(algo, source=int(root), mode=mode, **(run_kw or {}))
+                    for mode in ("analytic", "learned", "calibrated"):
+                        kw = dict(run_kw or {})
+                        if mode == "calibrated":
+                            kw["bw_ratio"] = calibrated_ratio
+                        r = G.run(algo, source=int(root), mode="analytic" if mode == "calibrated" else mode,
+                                  trace=True, **kw)
                         t[mode].append(r.stats["device_ms"])
-                out["analytic_ms"] += float(np.median(t["analytic"]))
-                out["learned_ms"] += float(np.median(t["learned"]))
+                        modes[mode] = r.modes
+                for m in t:
+                    out[m + "_ms"] += float(np.median(t[m]))
+                out["same_modes"] &= bool(np.array_equal(modes["analytic"], modes["learned"]))
     finally:
         selector_set(None)
         G.close()
     out["speedup"] = out["analytic_ms"] / out["learned_ms"] if out["learned_ms"] > 0 else None
+    out["calibrated_speedup"] = out["analytic_ms"] / out["calibrated_ms"] if out["calibrated_ms"] > 0 else None
     return out
 
 
