@@ -227,6 +227,32 @@ gpop_status gpop_run_msbfs(gpop_graph *g, const gpop_run_opts *opts, const uint3
                            uint32_t *out_levels, int out_is_device, gpop_run_stats *stats);
 
 /*
+ * Batched seeded personalized PageRank: the PPR vector of every seed (restart 1 - damping, the iteration
+ * of gpop_run's GPOP_PPR) in passes of up to 32 seeds, each pass one traversal of the partition-centric
+ * scatter / gather in which a message carries one FP32 value per seed of the pass (Alg. 2 with Alg. 3's
+ * PC layout; the single-seed application's scatter, gather and filter functions applied per seed).  Every
+ * partition holding a vertex active for some seed of the pass (the union frontier) is scattered in PC mode.
+ *   seeds        HOST array of num_seeds vertex IDs (< V; repeats allowed)
+ *   out_values   num_seeds x V floats, row j = the PPR vector of seeds[j], caller-owned; device memory if
+ *                out_is_device, else host memory
+ *   opts         damping (restart alpha = 1 - damping), max_iters (per pass), tol_l1 (a pass stops once
+ *                every one of its seeds' L1 change is below it; 0: run max_iters), cuda_stream,
+ *                profile_kernels; msg_bf16 and resume must be 0; mode, bw ratio and trace buffers are
+ *                not used
+ *   stats        iterations summed over passes, converged = every pass met tol_l1, residual = the largest
+ *                L1 change of the last iteration of the last pass, device_ms, edges_scattered (out-edges
+ *                of the partitions scattered, summed over iterations and passes)
+ * The combined message of 32 seeds per destination is kept in shared memory, so the graph's partition
+ * size must be at most 1024.  All working memory (about 3 x 128 B per vertex and 128 B per PNG slot) is
+ * allocated by the call and released before it returns.  Sums are taken in a fixed order: results do
+ * not change from run to run.
+ * Errors: GPOP_ERR_INVALID_ARG (seed out of range, partition size above 1024, damping outside (0, 1),
+ * msg_bf16 or resume set), GPOP_ERR_OOM, GPOP_ERR_CUDA.  num_seeds = 0 returns GPOP_OK without work.
+ */
+gpop_status gpop_run_ppr_batch(gpop_graph *g, const gpop_run_opts *opts, const uint32_t *seeds, uint32_t num_seeds,
+                               float *out_values, int out_is_device, gpop_run_stats *stats);
+
+/*
  * Checkpoint of a run (all applications but multi-source BFS): the vertex values, BFS levels, next
  * messages and frontier bitmap the last successful gpop_run on this graph left, with its algorithm, the
  * number of iterations behind it and the L1 change of its last gather.

@@ -244,6 +244,33 @@ class Graph:
             frontier = frontier[: it * 2].reshape(it, 2)
         return RunResult(out, None, stats, modes, frontier, None)
 
+    def run_ppr_batch(self, seeds, damping: float = 0.85, max_iters: int = 1000, tol: float = 0.0,
+                      device_out: bool = True, stream=None, out=None, profile: bool = False) -> RunResult:
+        """Seeded personalized PageRank for every seed (gpop_run_ppr_batch: up to 32 seeds per pass, one FP32
+        value per seed in every message); values is a (len(seeds), V) float32 array, row j the vector of
+        seeds[j].  The graph's partition size must be at most 1024."""
+        torch = _torch()
+        lib = _lib.load()
+        n = self.info()["num_vertices"]
+        sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.int64).astype(np.uint32))
+        ns = sd.shape[0]
+        o = _lib.RunOpts()
+        lib.gpop_run_opts_default(ctypes.byref(o))
+        o.algo = ALGOS["ppr"]
+        o.damping = damping
+        o.max_iters = max_iters
+        o.tol_l1 = tol
+        o.cuda_stream = _stream_handle(stream)
+        o.profile_kernels = int(profile)
+        if out is None:
+            out = (torch.empty((ns, n), dtype=torch.float32, device="cuda") if device_out
+                   else np.empty((ns, n), dtype=np.float32))
+        pv = out.data_ptr() if device_out else out.ctypes.data
+        st = _lib.RunStats()
+        _lib.check(lib.gpop_run_ppr_batch(self._h, ctypes.byref(o), ctypes.c_void_p(sd.ctypes.data if ns else None),
+                                          ns, ctypes.c_void_p(pv if ns else None), int(device_out), ctypes.byref(st)))
+        return RunResult(out, None, st.as_dict(), None, None, None)
+
 
 def probe_bounded_wait(tries: int) -> bool:
     """Runs the engine's bounded mbarrier wait against a phase nothing completes (gpop_probe_bounded_wait);

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgpop.so")
-SOURCES = ["build.cu", "engine.cu", "selector.cu"]
+SOURCES = ["build.cu", "engine.cu", "selector.cu", "batch.cu"]
 HEADERS = ["gpop_internal.cuh", os.path.join("..", "..", "include", "gpop.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
