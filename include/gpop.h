@@ -227,6 +227,36 @@ gpop_status gpop_run_msbfs(gpop_graph *g, const gpop_run_opts *opts, const uint3
                            uint32_t *out_levels, int out_is_device, gpop_run_stats *stats);
 
 /*
+ * Many graphs at once.  gpop_graph_build_union builds num_graphs graphs as one graph, their disjoint union
+ * (graph i's vertices follow graph i-1's, its edges shifted with them), so that the partitions, bins and
+ * gather tasks of Sec. 3.1 span graphs of uneven size and one traversal of the scatter / gather serves all
+ * of them.  Arguments per graph, HOST arrays: num_vertices[i] (> 0), num_edges[i], row_ptrs[i] (V_i + 1
+ * offsets starting at 0), cols[i] (E_i local destinations < V_i), weights NULL or weights[i] (E_i values,
+ * for every graph with edges); partition_size as gpop_graph_build.  The union must have fewer than 2^31
+ * vertices and 2^32 edges.  The caller keeps its arrays; the result is a gpop_graph like any other (any
+ * application can run on the union), which also knows its graphs' first vertices:
+ *   gpop_graph_union_offsets   writes num_graphs + 1 offsets (graph i = vertices [offsets[i], offsets[i+1])
+ *                              of the union) into the caller's HOST array, or only *num_graphs when
+ *                              offsets is NULL; *num_graphs = 0 for a graph not built as a union.
+ *   gpop_run_bfs_union         the BFS levels (Alg. 5) of every graph from its own source: sources[i] is a
+ *                              LOCAL vertex of graph i; out_levels (V of the union, caller-owned, device
+ *                              memory if out_is_device) receives graph i's levels at offsets[i] ..
+ *                              (0xFFFFFFFF = unreached).  Up to 32 graphs per traversal: one source each in
+ *                              the multi-source BFS of gpop_run_msbfs, whose levels inside a graph are that
+ *                              graph's BFS because no edge leaves it.  opts as gpop_run_msbfs.
+ * Errors: GPOP_ERR_INVALID_ARG (a graph without vertices, a destination outside its graph, too large a
+ * union, weights for some graphs only, a source outside its graph, a graph not built as a union),
+ * GPOP_ERR_OOM, GPOP_ERR_CUDA, and those of gpop_graph_build and gpop_run_msbfs.
+ */
+gpop_status gpop_graph_build_union(uint32_t num_graphs, const uint32_t *num_vertices, const uint64_t *num_edges,
+                                   const uint64_t *const *row_ptrs, const uint32_t *const *cols,
+                                   const int32_t *const *weights, uint32_t partition_size, void *cuda_stream,
+                                   gpop_graph **out);
+gpop_status gpop_graph_union_offsets(const gpop_graph *g, uint32_t *offsets, uint32_t *num_graphs);
+gpop_status gpop_run_bfs_union(gpop_graph *g, const gpop_run_opts *opts, const uint32_t *sources, uint32_t *out_levels,
+                               int out_is_device, gpop_run_stats *stats);
+
+/*
  * Batched seeded personalized PageRank: the PPR vector of every seed (restart 1 - damping, the iteration
  * of gpop_run's GPOP_PPR) in passes of up to 32 seeds, each pass one traversal of the partition-centric
  * scatter / gather in which a message carries one FP32 value per seed of the pass (Alg. 2 with Alg. 3's

@@ -100,6 +100,68 @@ class Graph:
         del rp_keep, cl_keep, w_keep
         return cls(h)
 
+    @classmethod
+    def from_many(cls, graphs, partition_size: int = 0, stream=None) -> "Graph":
+        """Builds several graphs as one, their disjoint union (gpop_graph_build_union).  graphs: a list of
+        (row_ptr, col) or (row_ptr, col, weights) host arrays, local vertex IDs per graph."""
+        lib = _lib.load()
+        ng = len(graphs)
+        keep = []
+        nv = np.zeros(ng, dtype=np.uint32)
+        ne = np.zeros(ng, dtype=np.uint64)
+        rps = (ctypes.c_void_p * ng)()
+        cols = (ctypes.c_void_p * ng)()
+        weighted = ng > 0 and len(graphs[0]) > 2 and graphs[0][2] is not None
+        ws = (ctypes.c_void_p * ng)() if weighted else None
+        for i, gr in enumerate(graphs):
+            rp = np.ascontiguousarray(gr[0], dtype=np.uint64)
+            cl = np.ascontiguousarray(gr[1], dtype=np.uint32)
+            nv[i], ne[i] = rp.shape[0] - 1, cl.shape[0]
+            rps[i], cols[i] = rp.ctypes.data, cl.ctypes.data if cl.size else None
+            keep += [rp, cl]
+            if weighted:
+                w = np.ascontiguousarray(gr[2], dtype=np.int32)
+                ws[i] = w.ctypes.data if w.size else None
+                keep.append(w)
+        h = ctypes.c_void_p()
+        _lib.check(lib.gpop_graph_build_union(ng, ctypes.c_void_p(nv.ctypes.data), ctypes.c_void_p(ne.ctypes.data),
+                                              rps, cols, ws, partition_size, _stream_handle(stream), ctypes.byref(h)))
+        del keep
+        return cls(h)
+
+    def union_offsets(self) -> np.ndarray:
+        """First vertex of every graph of a union (and V at the end); empty for a graph not built as one."""
+        lib = _lib.load()
+        n = ctypes.c_uint32(0)
+        _lib.check(lib.gpop_graph_union_offsets(self._h, None, ctypes.byref(n)))
+        off = np.zeros(n.value + 1, dtype=np.uint32)
+        if n.value:
+            _lib.check(lib.gpop_graph_union_offsets(self._h, ctypes.c_void_p(off.ctypes.data), ctypes.byref(n)))
+        return off if n.value else np.zeros(0, dtype=np.uint32)
+
+    def run_bfs_union(self, sources, max_iters: int = 1000, mode: str = "analytic", bw_ratio=(2, 1),
+                      device_out: bool = True, stream=None, profile: bool = False) -> RunResult:
+        """BFS of every graph of a union from its own (local) source (gpop_run_bfs_union); values holds the
+        union's V levels, graph i's at union_offsets()[i] onwards (0xFFFFFFFF = unreached)."""
+        torch = _torch()
+        lib = _lib.load()
+        n = self.info()["num_vertices"]
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64).astype(np.uint32))
+        o = _lib.RunOpts()
+        lib.gpop_run_opts_default(ctypes.byref(o))
+        o.algo = ALGOS["bfs"]
+        o.max_iters = max_iters
+        o.mode = MODES[mode]
+        o.bw_ratio_num, o.bw_ratio_den = bw_ratio
+        o.cuda_stream = _stream_handle(stream)
+        o.profile_kernels = int(profile)
+        out = torch.empty(n, dtype=torch.uint32, device="cuda") if device_out else np.empty(n, dtype=np.uint32)
+        pv = out.data_ptr() if device_out else out.ctypes.data
+        st = _lib.RunStats()
+        _lib.check(lib.gpop_run_bfs_union(self._h, ctypes.byref(o), ctypes.c_void_p(src.ctypes.data),
+                                          ctypes.c_void_p(pv), int(device_out), ctypes.byref(st)))
+        return RunResult(out, None, st.as_dict(), None, None, None)
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value:

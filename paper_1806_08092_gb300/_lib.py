@@ -74,6 +74,10 @@ SIGNATURES = {
                                       ctypes.POINTER(RunStats)]),
     "gpop_run_ppr_batch": (ctypes.c_int, [_vp, ctypes.POINTER(RunOpts), _vp, ctypes.c_uint32, _vp, ctypes.c_int,
                                           ctypes.POINTER(RunStats)]),
+    "gpop_graph_build_union": (ctypes.c_int, [_u32, _vp, _vp, _vp, _vp, _vp, _u32, _vp, ctypes.POINTER(_vp)]),
+    "gpop_graph_union_offsets": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_u32)]),
+    "gpop_run_bfs_union": (ctypes.c_int, [_vp, ctypes.POINTER(RunOpts), _vp, _vp, ctypes.c_int,
+                                          ctypes.POINTER(RunStats)]),
     "gpop_probe_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "gpop_state_export": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "gpop_state_import": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64]),

@@ -1099,6 +1099,59 @@ extern "C" gpop_status gpop_graph_build(uint32_t num_vertices, uint64_t num_edge
     return GPOP_OK;
 }
 
+extern "C" gpop_status gpop_graph_build_union(uint32_t num_graphs, const uint32_t *num_vertices,
+                                              const uint64_t *num_edges, const uint64_t *const *row_ptrs,
+                                              const uint32_t *const *cols, const int32_t *const *weights,
+                                              uint32_t partition_size, void *cuda_stream, gpop_graph **out) {
+    set_error("");
+    if (!out || !num_vertices || !num_edges || !row_ptrs || !cols) return fail(GPOP_ERR_INVALID_ARG, "NULL argument");
+    if (num_graphs == 0) return fail(GPOP_ERR_INVALID_ARG, "no graphs");
+    // the union's CSR: graph i's vertices follow graph i-1's, its edges shifted by its first vertex
+    std::vector<uint32_t> goff(num_graphs + 1, 0);
+    uint64_t V = 0, E = 0;
+    for (uint32_t i = 0; i < num_graphs; ++i) {
+        if (num_vertices[i] == 0) return fail(GPOP_ERR_INVALID_ARG, "a graph without vertices");
+        if (!row_ptrs[i] || (num_edges[i] && !cols[i])) return fail(GPOP_ERR_INVALID_ARG, "a graph's row_ptr/col is NULL");
+        if ((weights != nullptr) && !weights[i] && num_edges[i]) return fail(GPOP_ERR_INVALID_ARG, "weights for some graphs only");
+        if (row_ptrs[i][0] != 0 || row_ptrs[i][num_vertices[i]] != num_edges[i])
+            return fail(GPOP_ERR_INVALID_ARG, "a graph's row_ptr does not span its edges");
+        goff[i] = (uint32_t)std::min<uint64_t>(V, 0xFFFFFFFFull);
+        V += num_vertices[i];
+        E += num_edges[i];
+        if (V >= (1ull << 31)) return fail(GPOP_ERR_INVALID_ARG, "the union has 2^31 vertices or more");
+        if (E >= (1ull << 32)) return fail(GPOP_ERR_INVALID_ARG, "the union has 2^32 edges or more");
+    }
+    goff[num_graphs] = (uint32_t)V;
+    std::vector<uint64_t> rp(V + 1);
+    std::vector<uint32_t> col(std::max<uint64_t>(E, 1));
+    std::vector<int32_t> w(weights ? std::max<uint64_t>(E, 1) : 0);
+    uint64_t eo = 0;
+    for (uint32_t i = 0; i < num_graphs; ++i) {
+        const uint32_t n = num_vertices[i], base = goff[i];
+        for (uint32_t v = 0; v < n; ++v) rp[base + v] = eo + row_ptrs[i][v];
+        for (uint64_t e = 0; e < num_edges[i]; ++e) {
+            if (cols[i][e] >= n) return fail(GPOP_ERR_INVALID_ARG, "a destination outside its graph");
+            col[eo + e] = base + cols[i][e];
+            if (weights) w[eo + e] = weights[i][e];
+        }
+        eo += num_edges[i];
+    }
+    rp[V] = E;
+    gpop_status st = gpop_graph_build((uint32_t)V, E, rp.data(), col.data(), weights ? w.data() : nullptr,
+                                      partition_size, 0, cuda_stream, out);
+    if (st == GPOP_OK) (*out)->g.goff = std::move(goff);
+    return st;
+}
+
+extern "C" gpop_status gpop_graph_union_offsets(const gpop_graph *h, uint32_t *offsets, uint32_t *num_graphs) {
+    if (!h || !num_graphs) return fail(GPOP_ERR_INVALID_ARG, "NULL argument");
+    const uint32_t n = h->g.goff.empty() ? 0u : (uint32_t)h->g.goff.size() - 1;
+    *num_graphs = n;
+    if (offsets)
+        for (uint32_t i = 0; i <= n && n; ++i) offsets[i] = h->g.goff[i];
+    return GPOP_OK;
+}
+
 extern "C" gpop_status gpop_graph_get_info(const gpop_graph *h, gpop_graph_info *info) {
     if (!h || !info) return fail(GPOP_ERR_INVALID_ARG, "NULL argument");
     const Graph &g = h->g;

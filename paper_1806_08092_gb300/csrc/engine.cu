@@ -2477,6 +2477,102 @@ extern "C" gpop_status gpop_run_msbfs(gpop_graph *h, const gpop_run_opts *o, con
     return GPOP_OK;
 }
 
+// Graphs built as one disjoint union: the BFS levels of graph b0 + j (j < n) are row j of the pass's
+// multi-source BFS over that graph's own vertices (no edge leaves a graph); one thread per vertex of the
+// pass's graphs, the graph found by binary search over their first vertices
+__global__ void k_union_levels(const uint32_t *rows, uint32_t V, const uint32_t *goff, uint32_t b0, uint32_t n,
+                               uint32_t *out) {
+    const uint32_t v0 = goff[b0], v1 = goff[b0 + n];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < v1 - v0; x += stride) {
+        const uint32_t v = v0 + (uint32_t)x;
+        uint32_t lo = 0, hi = n;  // the last j with goff[b0 + j] <= v
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (goff[b0 + mid] <= v) lo = mid; else hi = mid;
+        }
+        out[v] = rows[(uint64_t)lo * V + v];
+    }
+}
+
+extern "C" gpop_status gpop_run_bfs_union(gpop_graph *h, const gpop_run_opts *o, const uint32_t *sources,
+                                          uint32_t *out_levels, int out_is_device, gpop_run_stats *stats) {
+    set_error("");
+    if (!h || !o || !sources || !out_levels) return fail(GPOP_ERR_INVALID_ARG, "NULL argument");
+    Graph *g = &h->g;
+    if (g->goff.size() < 2) return fail(GPOP_ERR_INVALID_ARG, "the graph was not built by gpop_graph_build_union");
+    const uint32_t ng = (uint32_t)g->goff.size() - 1;
+    for (uint32_t i = 0; i < ng; ++i)
+        if (sources[i] >= g->goff[i + 1] - g->goff[i]) return fail(GPOP_ERR_INVALID_ARG, "source out of its graph's range");
+    if (o->msg_bf16 || o->resume) return fail(GPOP_ERR_INVALID_ARG, "msg_bf16 and resume must be 0");
+    gpop_status cs = check_common_opts(o);
+    if (cs != GPOP_OK) return cs;
+    cudaStream_t s = (cudaStream_t)o->cuda_stream;
+    RunBuffers *rb = nullptr;
+    gpop_status ps = prepare_run(g, 0, s, &rb);
+    if (ps != GPOP_OK) return ps;
+    if (!rb->msrc) {
+        cudaError_t e = dalloc(g, &rb->msrc, kMsBfsWidth);
+        if (e != cudaSuccess) return fail(GPOP_ERR_OOM, std::string("source list: ") + cudaGetErrorString(e));
+    }
+    if (!rb->lvl_ms) {  // one pass's level rows (32 x V)
+        cudaError_t e = dalloc(g, &rb->lvl_ms, (uint64_t)kMsBfsWidth * g->V);
+        if (e != cudaSuccess) return fail(GPOP_ERR_OOM, std::string("level rows: ") + cudaGetErrorString(e));
+    }
+    uint32_t *d_goff = nullptr, *d_out = nullptr;
+    cudaError_t e = cudaMalloc(&d_goff, 4ull * (ng + 1));
+    if (e == cudaSuccess && !out_is_device) e = cudaMalloc(&d_out, 4ull * g->V);
+    if (e != cudaSuccess) {
+        cudaFree(d_goff);
+        return fail(GPOP_ERR_OOM, std::string("union buffers: ") + cudaGetErrorString(e));
+    }
+    gpop_run_stats total;
+    memset(&total, 0, sizeof total);
+    total.converged = 1;
+    gpop_status status = GPOP_OK;
+    e = cudaMemcpyAsync(d_goff, g->goff.data(), 4ull * (ng + 1), cudaMemcpyHostToDevice, s);
+    uint32_t *dst = out_is_device ? out_levels : d_out;
+    std::vector<uint32_t> src(kMsBfsWidth);
+    for (uint32_t b0 = 0; b0 < ng && e == cudaSuccess; b0 += kMsBfsWidth) {
+        const uint32_t n = std::min<uint32_t>(kMsBfsWidth, ng - b0);
+        for (uint32_t j = 0; j < n; ++j) src[j] = g->goff[b0 + j] + sources[b0 + j];
+        e = cudaMemcpyAsync(rb->msrc, src.data(), 4ull * n, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) break;
+        MsPass mp{rb->msrc, n, rb->lvl_ms};
+        gpop_run_stats st;
+        status = run_algo<ALG_MSBFS, false>(g, rb, o, s, nullptr, nullptr, 1, &st, &mp);
+        if (status != GPOP_OK) break;
+        const uint32_t nv = g->goff[b0 + n] - g->goff[b0];
+        k_union_levels<<<std::max(1u, std::min((nv + 255) / 256, 8u * g->num_sms)), 256, 0, s>>>(rb->lvl_ms, g->V, d_goff,
+                                                                                               b0, n, dst);
+        e = cudaGetLastError();
+        total.iterations += st.iterations;
+        total.converged &= st.converged;
+        total.edges_scattered += st.edges_scattered;
+        total.vertices_scattered += st.vertices_scattered;
+        total.pc_partition_steps += st.pc_partition_steps;
+        total.sc_partition_steps += st.sc_partition_steps;
+        total.model_bytes += st.model_bytes;
+        total.device_ms += st.device_ms;
+        total.sc_vertices_scattered += st.sc_vertices_scattered;
+        total.sc_edges_scattered += st.sc_edges_scattered;
+        total.gathered_vertices += st.gathered_vertices;
+        for (int i = 0; i < 6; ++i) {
+            total.kernel_ms[i] += st.kernel_ms[i];
+            total.kernel_launches[i] += st.kernel_launches[i];
+        }
+    }
+    if (status == GPOP_OK && e == cudaSuccess && !out_is_device)
+        e = cudaMemcpyAsync(out_levels, d_out, 4ull * g->V, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_goff);
+    if (d_out) cudaFree(d_out);
+    if (status != GPOP_OK) return status;
+    if (e != cudaSuccess) return fail(GPOP_ERR_CUDA, std::string("union BFS: ") + cudaGetErrorString(e));
+    if (stats) *stats = total;
+    return GPOP_OK;
+}
+
 extern "C" gpop_status gpop_probe_bounded_wait(uint32_t tries, uint32_t *gave_up) {
     set_error("");
     if (!gave_up) return fail(GPOP_ERR_INVALID_ARG, "gave_up is NULL");

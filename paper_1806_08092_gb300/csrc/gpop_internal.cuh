@@ -151,6 +151,7 @@ struct Graph {
 
     uint64_t device_bytes = 0;
     uint64_t fingerprint = 0;     // of the edge multiset with weights, V and E (checkpoints name their graph)
+    std::vector<uint32_t> goff;   // graphs built as one disjoint union: first vertex of each (+ V at the end)
     int device = 0, num_sms = 0;
     void *run = nullptr;          // cached per-run buffers (engine.cu)
 };

@@ -86,6 +86,31 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.gpop_run(None, None, None, None, 0, None) == 1
 
 
+def test_union_build_arguments_are_checked_on_the_host(lib):
+    # the union's CSR is assembled and checked on the host before any CUDA call
+    h = ctypes.c_void_p()
+    nv = np.array([3, 2], dtype=np.uint32)
+    ne = np.array([2, 1], dtype=np.uint64)
+    rp0 = np.array([0, 1, 2, 2], dtype=np.uint64)
+    rp1 = np.array([0, 1, 1], dtype=np.uint64)
+    c0 = np.array([1, 2], dtype=np.uint32)
+    c1_bad = np.array([2], dtype=np.uint32)  # graph 1 has 2 vertices: destination 2 is outside it
+    rps = (ctypes.c_void_p * 2)(rp0.ctypes.data, rp1.ctypes.data)
+    cols = (ctypes.c_void_p * 2)(c0.ctypes.data, c1_bad.ctypes.data)
+    st = lib.gpop_graph_build_union(2, ctypes.c_void_p(nv.ctypes.data), ctypes.c_void_p(ne.ctypes.data), rps, cols,
+                                    None, 32, None, ctypes.byref(h))
+    assert st == 1 and b"outside its graph" in lib.gpop_last_error()
+    assert lib.gpop_graph_build_union(0, None, None, None, None, None, 32, None, ctypes.byref(h)) == 1
+    rp1_short = np.array([0, 0, 0], dtype=np.uint64)  # row_ptr ends at 0 but the graph has one edge
+    rps2 = (ctypes.c_void_p * 2)(rp0.ctypes.data, rp1_short.ctypes.data)
+    st = lib.gpop_graph_build_union(2, ctypes.c_void_p(nv.ctypes.data), ctypes.c_void_p(ne.ctypes.data), rps2, cols,
+                                    None, 32, None, ctypes.byref(h))
+    assert st == 1 and b"row_ptr" in lib.gpop_last_error()
+    n = ctypes.c_uint32(7)
+    assert lib.gpop_graph_union_offsets(None, None, ctypes.byref(n)) == 1
+    assert lib.gpop_run_bfs_union(None, None, None, None, 0, None) == 1
+
+
 def test_no_cpu_fallback_when_library_missing(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):

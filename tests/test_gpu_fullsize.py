@@ -239,3 +239,24 @@ def test_rmat22_ppr_batch_64_seeds(gp, rmat22):
     assert max(errs) <= 1e-5
     mass = vals.astype(np.float64).sum(axis=1)
     assert np.all(mass <= 1.0 + 1e-5) and np.all(vals[np.arange(64), seeds] >= 0.15 - 1e-6)
+
+
+def test_128_uneven_rmat_graphs_bfs_union(gp):
+    # 128 RMAT graphs of scales 10 to 18 and edge factors 8 to 32 (drawn from a fixed seed) as one union:
+    # every graph's levels from its own root, eight of them against the oracle and all against the
+    # properties that fix BFS levels
+    rng = np.random.default_rng(128)
+    gs = [gg.rmat(int(rng.integers(10, 19)), int(rng.choice([8, 16, 32]))) for _ in range(128)]
+    G = gp.Graph.from_many([(g.row_ptr, g.col) for g in gs], partition_size=16384)
+    off = G.union_offsets()
+    src = [int(gg.roots(g, 1)[0]) for g in gs]
+    lv = G.run_bfs_union(src).values.cpu().numpy()
+    G.close()
+    for i in (0, 1, 31, 32, 63, 64, 100, 127):
+        assert np.array_equal(lv[off[i]:off[i + 1]], O.bfs(gs[i], src[i])[0]), i
+    for i, g in enumerate(gs):
+        L = lv[off[i]:off[i + 1]].astype(np.int64)
+        assert L[src[i]] == 0
+        u, v = g.src().astype(np.int64), g.col.astype(np.int64)
+        reached = L[u] != O.U32_INF
+        assert np.all(L[v][reached] <= L[u][reached] + 1)
