@@ -148,6 +148,15 @@ typedef struct {
                                   same results as one uninterrupted run.  source is not used.  Not for
                                   gpop_run_msbfs.  GPOP_ERR_INVALID_ARG when no state of the algorithm
                                   is held. */
+    uint32_t isg_waves;        /* CC and SSSP: interleaved scatter-gather (Sec. 3.3) with this many waves
+                                  (0 or 1: bulk-synchronous).  Iteration i scatters only the active
+                                  partitions p with p mod isg_waves == (i - 1) mod isg_waves; its gather
+                                  updates every destination, and active vertices of the partitions that did
+                                  not scatter stay active.  A partition thus scatters the values its vertices
+                                  received from the waves before it in the same sweep, the paper's "gather
+                                  the messages already received, then scatter" with the wave order in place
+                                  of thread timing.  Results are the same fixed point; iteration counts (one
+                                  wave each) change.  GPOP_ERR_INVALID_ARG for other algorithms. */
 } gpop_run_opts;
 
 /* Floats per LOG_BOTH record: 8 selector features, t_PC (us), t_SC (us),

@@ -190,12 +190,13 @@ class Graph:
     def run(self, algo: str, source: int = 0, damping: float = 0.85, max_iters: int = 1000, tol: float = 0.0,
             mode: str = "analytic", bw_ratio=(2, 1), device_out: bool = True, trace: bool = False,
             log_capacity: int = 0, stream=None, out=None, out_parent=None, profile: bool = False,
-            msg_bf16: bool = False, epsilon: float = 1e-9, resume: bool = False) -> RunResult:
+            msg_bf16: bool = False, epsilon: float = 1e-9, resume: bool = False, isg_waves: int = 0) -> RunResult:
         """Runs one application; outputs are torch tensors on cuda (device_out) or host numpy arrays.
         msg_bf16: PageRank / PPR messages travel through the bins as BF16 (gathered in FP32).
         epsilon: Nibble's threshold (a vertex stays on while PR >= epsilon * out-degree).
         resume: continue the state this graph holds (its last run of `algo`, or state_import) for up to
-        max_iters more iterations, with the results of one uninterrupted run."""
+        max_iters more iterations, with the results of one uninterrupted run.
+        isg_waves: CC and SSSP only, interleaved scatter-gather with this many waves (0: off)."""
         torch = _torch()
         lib = _lib.load()
         info = self.info()
@@ -214,6 +215,7 @@ class Graph:
         o.msg_bf16 = int(msg_bf16)
         o.epsilon = epsilon
         o.resume = int(resume)
+        o.isg_waves = int(isg_waves)
         modes = frontier = log = None
         if trace:
             modes = np.zeros(max(max_iters, 1) * k, dtype=np.uint8)

@@ -42,7 +42,8 @@ class RunOpts(ctypes.Structure):
                 ("bw_ratio_num", ctypes.c_uint32), ("bw_ratio_den", ctypes.c_uint32), ("msg_bf16", ctypes.c_int32),
                 ("profile_kernels", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p), ("trace_modes", ctypes.c_void_p),
                 ("trace_frontier", ctypes.c_void_p), ("log_buffer", ctypes.c_void_p),
-                ("log_capacity", ctypes.c_uint64), ("epsilon", ctypes.c_double), ("resume", ctypes.c_int32)]
+                ("log_capacity", ctypes.c_uint64), ("epsilon", ctypes.c_double), ("resume", ctypes.c_int32),
+                ("isg_waves", ctypes.c_uint32)]
 
 
 class RunStats(ctypes.Structure):

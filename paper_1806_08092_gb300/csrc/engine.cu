@@ -137,6 +137,7 @@ struct Params {
     double tol;
     int algo, policy;
     uint32_t bw_num, bw_den;
+    uint32_t isg_w;         // interleaved scatter-gather: waves (0: off)
 };
 
 // --- small device helpers ----------------------------------------------------------------------
@@ -502,6 +503,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
             if (lm == 0xFF) nfb++;
             else if (lm != kModeNone) m = lm;
         }
+        // interleaved scatter-gather: only this iteration's wave scatters; the others keep their frontier
+        if (p.isg_w >= 2 && valid && q % p.isg_w != (p.iter - 1) % p.isg_w) m = kModeNone;
         if (valid) {
             p.mode[q] = m;
             tb += mode_bytes(m, p.k, Ep, np, Va, Ea);
@@ -1735,11 +1738,16 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
                             ns[c] = g;
                         }
                     } else {
-                        // Alg. 7 / CC: keep the minimum distance or label, activate on improvement
+                        // Alg. 7 / CC: keep the minimum distance or label, activate on improvement; with
+                        // interleaved scatter-gather, an active vertex whose partition was not in this
+                        // iteration's wave stays active (it has not scattered yet)
                         if (m < vals[c]) {
                             nv[c] = m;
                             act = true;
                             ns[c] = m;
+                        } else if (p.isg_w >= 2 && was && q % p.isg_w != (p.iter - 1) % p.isg_w) {
+                            act = true;
+                            ns[c] = vals[c];
                         }
                     }
                     if (act) {
@@ -2084,6 +2092,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     }
     p.algo = ALGO; p.policy = o->mode == GPOP_MODE_LOG_BOTH ? GPOP_MODE_ANALYTIC : o->mode;
     p.bw_num = o->bw_ratio_num; p.bw_den = o->bw_ratio_den;
+    p.isg_w = o->isg_waves >= 2 ? o->isg_waves : 0u;
     if (ALGO == ALG_PR) {
         p.c0 = (float)((1.0 - o->damping) / (double)g->V);
         p.c1 = (float)o->damping;
@@ -2393,6 +2402,8 @@ extern "C" gpop_status gpop_run(gpop_graph *h, const gpop_run_opts *o, void *out
         return fail(GPOP_ERR_INVALID_ARG, "damping must be in (0, 1)");
     if (o->algo == GPOP_NIBBLE && !(o->epsilon >= 0.0 && std::isfinite(o->epsilon)))
         return fail(GPOP_ERR_INVALID_ARG, "Nibble threshold must be finite and >= 0");
+    if (o->isg_waves >= 2 && o->algo != GPOP_CC && o->algo != GPOP_SSSP)
+        return fail(GPOP_ERR_INVALID_ARG, "interleaved scatter-gather is for CC and SSSP (monotone minimum applications)");
     cudaStream_t s = (cudaStream_t)o->cuda_stream;
     const int fmt = o->msg_bf16 ? 1 : 0;
     RunBuffers *rb = nullptr;
@@ -2423,6 +2434,7 @@ extern "C" gpop_status gpop_run_msbfs(gpop_graph *h, const gpop_run_opts *o, con
         if (sources[j] >= g->V) return fail(GPOP_ERR_INVALID_ARG, "source out of range");
     if (o->msg_bf16) return fail(GPOP_ERR_INVALID_ARG, "BF16 messages are for PageRank and PPR (BFS stays exact)");
     if (o->resume) return fail(GPOP_ERR_INVALID_ARG, "multi-source BFS does not resume");
+    if (o->isg_waves >= 2) return fail(GPOP_ERR_INVALID_ARG, "interleaved scatter-gather is for CC and SSSP");
     gpop_status cs = check_common_opts(o);
     if (cs != GPOP_OK) return cs;
     gpop_run_stats total;
@@ -2504,7 +2516,8 @@ extern "C" gpop_status gpop_run_bfs_union(gpop_graph *h, const gpop_run_opts *o,
     const uint32_t ng = (uint32_t)g->goff.size() - 1;
     for (uint32_t i = 0; i < ng; ++i)
         if (sources[i] >= g->goff[i + 1] - g->goff[i]) return fail(GPOP_ERR_INVALID_ARG, "source out of its graph's range");
-    if (o->msg_bf16 || o->resume) return fail(GPOP_ERR_INVALID_ARG, "msg_bf16 and resume must be 0");
+    if (o->msg_bf16 || o->resume || o->isg_waves >= 2)
+        return fail(GPOP_ERR_INVALID_ARG, "msg_bf16, resume and isg_waves must be 0");
     gpop_status cs = check_common_opts(o);
     if (cs != GPOP_OK) return cs;
     cudaStream_t s = (cudaStream_t)o->cuda_stream;

@@ -309,12 +309,40 @@ def ablation():
     Gs.close()
 
 
+def isg(waves=(0, 2, 4, 8), ratio=8):
+    """Interleaved scatter-gather (Sec. 3.3) against bulk-synchronous iterations, the paper's GPOP_DI / GPOP_DC
+    comparison: SSSP on RMAT-24 (4 roots) and CC on symmetrised RMAT-24, Eq. (mode) at the measured ratio;
+    device time, iterations (one wave each) and sweeps."""
+    gg = _gen()
+    g = gg.rmat(24).with_weights()
+    roots = [int(r) for r in gg.roots(g, 4)]
+    G = Graph.from_csr(g.row_ptr, g.col, g.weights, partition_size=16384)
+    for w in waves:
+        ms = its = 0.0
+        for root in roots:
+            r = _median_run(G, "sssp", source=root, isg_waves=w, bw_ratio=(ratio, 1))
+            ms += r.stats["device_ms"]
+            its += r.stats["iterations"]
+        _emit({"config": "isg", "graph": "rmat24", "algo": "sssp", "isg_waves": w, "roots": len(roots),
+               "ms_mean": ms / len(roots), "iterations_mean": its / len(roots),
+               "sweeps_mean": its / len(roots) / max(w, 1)})
+    G.close()
+    del g
+    gs = gg.symmetrized(gg.rmat(24))
+    Gs = Graph.from_csr(gs.row_ptr, gs.col, None, partition_size=16384)
+    for w in waves:
+        r = _median_run(Gs, "cc", isg_waves=w, bw_ratio=(ratio, 1))
+        _emit({"config": "isg", "graph": "rmat24_sym", "algo": "cc", "isg_waves": w, "ms": r.stats["device_ms"],
+               "iterations": r.stats["iterations"], "sweeps": r.stats["iterations"] / max(w, 1)})
+    Gs.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--configs", default="c1,c2,c3,c4,c4_graphs,nibble,ablation,degree")
+    ap.add_argument("--configs", default="c1,c2,c3,c4,c4_graphs,nibble,ablation,isg,degree")
     a = ap.parse_args()
     fns = {"c1": c1, "c2": c2, "c3": c3, "c4": c4, "c4_graphs": c4_graphs, "nibble": nibble, "ablation": ablation,
-           "degree": degree}
+           "isg": isg, "degree": degree}
     for c in a.configs.split(","):
         fns[c]()
 

@@ -312,6 +312,54 @@ def test_bw_ratio_autotuner():
         assert np.array_equal(Gd.run("bfs", source=root, bw_ratio=(ratio, 1), trace=True).modes, t2.modes)
 
 
+# --- interleaved scatter-gather (Sec. 3.3) --------------------------------------------------------
+
+@pytest.mark.parametrize("name,g", SMALL, ids=[s[0] for s in SMALL])
+@pytest.mark.parametrize("P,waves", [(32, 2), (256, 4), (4096, 2)])
+def test_isg_cc_sssp_exact(name, g, P, waves):
+    # the waves change the order in which partitions scatter, not the fixed point: labels and distances
+    # stay bit-exact, in every mode policy
+    gw = g.with_weights()
+    Gd = G(gw, P)
+    gs = gg.symmetrized(g)
+    ref_cc = O.cc(gs)
+    Gs = G(gs, P)
+    for pol in POLICIES:
+        assert np.array_equal(Gs.run("cc", mode=pol, isg_waves=waves).values.cpu().numpy(), ref_cc), pol
+    for root in gg.roots(g, 2):
+        root = int(root)
+        ref = u64_to_u32(O.sssp(gw, root))
+        for pol in POLICIES:
+            r = Gd.run("sssp", source=root, mode=pol, isg_waves=waves)
+            assert np.array_equal(r.values.cpu().numpy(), ref), pol
+            assert r.stats["converged"] == 1
+
+
+def test_isg_errors_and_iterations():
+    import paper_1806_08092_gb300 as gp
+    g = gg.rmat(14).with_weights()
+    Gd = G(g, 512)
+    root = int(gg.roots(g, 1)[0])
+    for algo, kw in (("bfs", dict(source=root)), ("pagerank", dict(max_iters=2)), ("ppr", dict(source=root)),
+                     ("nibble", dict(source=root))):
+        with pytest.raises(gp.GpopError, match="interleaved"):
+            Gd.run(algo, isg_waves=2, **kw)
+    # multi-source BFS through the C ABI: its levels depend on the iteration structure
+    import ctypes
+    from paper_1806_08092_gb300 import _lib
+    o = _lib.RunOpts()
+    _lib.load().gpop_run_opts_default(ctypes.byref(o))
+    o.isg_waves = 2
+    src = np.array([root], dtype=np.uint32)
+    out = torch.empty(g.num_vertices, dtype=torch.uint32, device="cuda")
+    assert _lib.load().gpop_run_msbfs(Gd._h, ctypes.byref(o), ctypes.c_void_p(src.ctypes.data), 1,
+                                      ctypes.c_void_p(out.data_ptr()), 1, None) == 1
+    # the same distances with and without waves
+    bsp = Gd.run("sssp", source=root)
+    isg = Gd.run("sssp", source=root, isg_waves=2)
+    assert np.array_equal(bsp.values.cpu().numpy(), isg.values.cpu().numpy())
+
+
 # --- parallel Nibble (Alg. 4) ---------------------------------------------------------------------
 # FP32 on the GPU against the FP64 oracle: PR values are probabilities (they sum to 1), compared in
 # absolute terms.  The threshold PR >= eps deg is decided on FP32 values on the GPU and on FP64 values
