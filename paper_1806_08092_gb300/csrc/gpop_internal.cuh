@@ -26,7 +26,7 @@ constexpr uint64_t kGatherTaskMinEdges = 65536;  // in-edges a gather task may t
 constexpr uint32_t kGatherEntries = 32768;  // target in-entries per gather task
 constexpr uint32_t kScatterChunk = 131072;  // PNG slots per PC scatter task (one staging of the partition's values)
 constexpr uint32_t kMaxRowBins = 40960;     // SC scatter keeps one cursor per row bin in smem
-constexpr uint32_t kPcBlock = 8192;         // messages staged in shared memory per PC gather block
+constexpr uint32_t kPcBlock = 16384;        // messages staged in shared memory per PC gather block
 constexpr uint32_t kPcTaskBlocks = 20;      // at most this many blocks per PC gather task (static smem per block)
 constexpr uint32_t kPcGatherWarps = 23;     // consumer warps of the PC gather, one destination slice of each task each
 constexpr uint32_t kPcPad = 16;             // each warp's entry range of a block is padded to a multiple of this
