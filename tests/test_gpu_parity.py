@@ -125,8 +125,8 @@ def test_modes_and_frontiers_match_tier2(scale, P):
 
 
 def _dense_column_graph():
-    # every one of 16384 sources sends 16 edges into partition 0 (P = 1024): two message blocks of
-    # 131072 entries each, so each block is split over several PC gather tasks
+    # every one of 16384 sources sends 16 edges into partition 0 (P = 1024): one message block of 262144
+    # entries (16384 messages), split over several PC gather tasks
     n, P, fan = 16384, 1024, 16
     u = np.repeat(np.arange(n, dtype=np.int64), fan)
     j = np.tile(np.arange(fan, dtype=np.int64), n)
