@@ -654,7 +654,7 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
     //    that the gather stages in shared memory by coalesced copies of bin runs ("runs": row-major
     //    source offset, length, offset in the block).  Every PC in-entry becomes a 4-byte word
     //    (local destination << 16 | index in its block), sorted by (block, destination, index).
-    //    Gather tasks cover consecutive entries of one column: about max(kPcTaskMinEntries, E / (4 x
+    //    Gather tasks cover consecutive entries of one column: about max(kPcTaskMinEntries, E / (2 x
     //    SMs)) entries and at most kPcTaskBlocks blocks each, a block's entries split over several
     //    tasks when it is larger; a column with several tasks leaves one partial vector per task,
     //    merged in column order by the filter.  Tasks are listed largest first.
@@ -758,7 +758,7 @@ static gpop_status build_impl(Graph *g, uint32_t V, uint64_t E, const uint64_t *
         GPOP_CUDA_TRY(cudaStreamSynchronize(s));
 
         // gather tasks over each column's entries
-        const uint64_t target = std::max<uint64_t>(kPcTaskMinEntries, E / (4ull * (uint64_t)std::max(1, g->num_sms)));
+        const uint64_t target = std::max<uint64_t>(kPcTaskMinEntries, E / (2ull * (uint64_t)std::max(1, g->num_sms)));
         std::vector<uint4> ptasks;
         std::vector<uint2> prng;
         std::vector<uint32_t> col_ntask(k, 0), col_part0(k, 0);

@@ -683,7 +683,7 @@ __device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
 // One CTA per scatter task: a chunk of one partition's PNG row (Alg. 3 for a PC partition, or a row
 // chunk refilled with NULL when the partition's data row must be cleared).  A PC task stages the
 // partition's P message values in shared memory with one bulk copy (TMA; bounded mbarrier wait) and
-// streams its chunk of the row: each thread reads four 16-byte groups of 8 PNG source IDs ahead and
+// streams its chunk of the row: each thread reads eight 16-byte groups of 8 PNG source IDs ahead and
 // writes the 8 values of each group as two 16-byte stores.
 template <bool B16>
 __global__ void __launch_bounds__(kScatterPcThreads) k_scatter_pc(Params p) {
@@ -745,16 +745,16 @@ __global__ void __launch_bounds__(kScatterPcThreads) k_scatter_pc(Params p) {
             if (!s_ok) return;  // the run reports the error; the copy has landed or been waited out
         }
         const uint32_t stride = blockDim.x * 8;
-        for (uint32_t i0 = st.beg + threadIdx.x * 8; i0 < st.end; i0 += 4 * stride) {
-            uint4 sx[4];
+        for (uint32_t i0 = st.beg + threadIdx.x * 8; i0 < st.end; i0 += 8 * stride) {
+            uint4 sx[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {  // up to four independent 16-byte loads in flight
+            for (int u = 0; u < 8; ++u) {  // up to eight independent 16-byte loads in flight
                 const uint32_t i = i0 + u * stride;
                 sx[u] = (act == kActPC && i < st.end) ? *reinterpret_cast<const uint4 *>(p.png + i)
                                                        : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const uint32_t i = i0 + u * stride;
                 if (i >= st.end) break;
                 uint4 o0, o1;

@@ -31,7 +31,7 @@ constexpr uint32_t kPcTaskBlocks = 20;      // at most this many blocks per PC g
 constexpr uint32_t kPcGatherWarps = 23;     // consumer warps of the PC gather, one destination slice of each task each
 constexpr uint32_t kPcPad = 16;             // each warp's entry range of a block is padded to a multiple of this
 constexpr uint32_t kPcPadIdx = kPcBlock;    // block index of the padding entries (a value slot that holds NULL)
-constexpr uint32_t kPcTaskMinEntries = 65536;  // PC gather tasks hold about max(this, E / (4 SMs)) entries
+constexpr uint32_t kPcTaskMinEntries = 65536;  // PC gather tasks hold about max(this, E / (2 SMs)) entries
 constexpr uint32_t kPcRound = 512;          // destination entries one gather warp folds per round
 
 // A warp's entry range of a block is folded in rounds of kPcRound entries (the last one shorter, a
