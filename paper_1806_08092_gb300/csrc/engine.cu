@@ -48,6 +48,11 @@ constexpr int kGatherWarps = kGatherThreads / 32;
 constexpr int kScatterThreads = 256;    // k_scatter_sc
 constexpr int kScatterPcThreads = 512;  // k_scatter_pc
 constexpr int kPlanThreads = 1024;
+constexpr uint32_t kPlanLoads = 3;  // gather-task statistics a plan thread loads at once
+// The L1 change of a gather task (at most 2: a change of probability mass) is passed to the plan as an
+// unsigned fixed-point number with 62 fraction bits, so that the plan sums it exactly, in any order,
+// with integer adds (FP64 arithmetic is scarce on this GPU); the rounding is below 2^-62 per task.
+constexpr double kResOne = 0x1p62, kResUnit = 0x1p-62;
 constexpr uint32_t kSent = 0xFFFFFFFFu;
 constexpr uint32_t kScUnitEdges = 1u << 12;  // active edges per SC scatter unit (a partition with more is split)
 constexpr uint32_t kScSegs = 16;              // 1024-vertex segments per partition (P <= 16384)
@@ -99,7 +104,7 @@ struct Params {
     uint32_t *val, *lvl, *sval, *bits;
     uint32_t *t_va;
     unsigned long long *t_ea;
-    double *t_res;
+    unsigned long long *t_res;  // L1 change of each gather task: fixed point, kResOne = 1
     uint32_t *t_stamp;
     uint8_t *mode, *action;
     uint32_t *gflag, *gflag_pc, *counters;
@@ -207,8 +212,9 @@ __device__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_warp, uint32_t *tota
 
 // Work units of one chunk of partitions, written by every thread of the block: thread t has cnt units,
 // the first at position beg (an exclusive scan over the chunk, tot units in all), for partition q with ea
-// active edges.  A hub partition can have thousands of units, so each unit finds its partition by a
-// binary search over the chunk's unit ends instead of its partition's thread writing them all.
+// active edges.  A hub partition can have thousands of units, so instead of its partition's thread writing
+// them all, the block's threads take equal ranges of consecutive units: a binary search over the chunk's
+// unit ends finds the partition of a range's first unit, and the rest follow by walking forward.
 __device__ void write_units(uint4 *list, uint32_t base, uint32_t q, uint32_t cnt, uint32_t beg, uint32_t tot, uint32_t ea,
                             uint32_t *s_beg, uint32_t *s_end, uint32_t *s_q, uint32_t *s_ea) {
     s_beg[threadIdx.x] = beg;
@@ -216,13 +222,18 @@ __device__ void write_units(uint4 *list, uint32_t base, uint32_t q, uint32_t cnt
     s_q[threadIdx.x] = q;
     s_ea[threadIdx.x] = ea;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < tot; i += blockDim.x) {
-        uint32_t lo = 0, hi = blockDim.x - 1;  // first thread whose units end after i
+    const uint32_t per = (tot + blockDim.x - 1) / blockDim.x;
+    const uint32_t i0 = threadIdx.x * per, i1 = min(tot, i0 + per);
+    if (i0 < i1) {
+        uint32_t lo = 0, hi = blockDim.x - 1;  // first thread whose units end after i0
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
-            if (s_end[mid] > i) hi = mid; else lo = mid + 1;
+            if (s_end[mid] > i0) hi = mid; else lo = mid + 1;
         }
-        list[base + i] = make_uint4(s_q[lo], i - s_beg[lo], s_end[lo] - s_beg[lo], s_ea[lo]);
+        for (uint32_t i = i0; i < i1; ++i) {
+            while (s_end[lo] <= i) ++lo;
+            list[base + i] = make_uint4(s_q[lo], i - s_beg[lo], s_end[lo] - s_beg[lo], s_ea[lo]);
+        }
     }
     __syncthreads();
 }
@@ -241,10 +252,24 @@ __device__ __forceinline__ uint8_t analytic_mode(uint64_t k, uint64_t Ep, uint64
     return pc <= sc ? kModePC : kModeSC;
 }
 
-__device__ __forceinline__ double mode_bytes(uint8_t m, uint64_t k, uint64_t Ep, uint64_t npng, uint64_t Va, uint64_t Ea) {
-    if (m == kModePC) return 4.0 * (double)(3 * npng + k + Ep);
-    if (m == kModeSC) return 4.0 * ((double)Va + 3.0 * (double)Ea + 2.0 * ((double)npng / (double)Ep) * (double)Ea);
-    return 0.0;
+// The PC bytes of Sec. 3.2 are an integer: summed exactly (FP64 arithmetic is scarce on this GPU)
+__device__ __forceinline__ unsigned long long pc_mode_bytes(uint64_t k, uint64_t Ep, uint64_t npng) {
+    return 4ull * (3 * npng + k + Ep);
+}
+// The SC bytes 4 (V_a + 3 E_a + 2 r^p E_a), r^p = n_png / E^p, in integers: a whole number of bytes and
+// two 32-bit digits of the fraction 8 rem / E^p (units of 2^-29 and 2^-61 bytes, rounded down), by long
+// division (n_png E_a < 2^64 since E_a <= E^p < 2^32 and n_png <= E^p)
+__device__ __forceinline__ unsigned long long sc_mode_bytes(uint32_t Ep, uint32_t npng, uint64_t Va, uint64_t Ea,
+                                                            unsigned long long *d1, unsigned long long *d2) {
+    const unsigned long long x = (unsigned long long)npng * Ea, qt = x / Ep, rm = x - qt * Ep;
+    *d1 = (rm << 32) / Ep;
+    *d2 = (((rm << 32) - *d1 * Ep) << 32) / Ep;
+    return 4ull * (Va + 3 * Ea) + 8ull * qt;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
 }
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -449,7 +474,7 @@ __global__ void k_task_stats(Params p) {
             for (int i = 0; i < kGatherWarps; ++i) { a += s_va[i]; b += s_ea[i]; }
             p.t_va[t] = a;
             p.t_ea[t] = b;
-            p.t_res[t] = t == 0 ? p.t_res0 : 0.0;  // a resumed run's first plan sees the saved L1 change
+            p.t_res[t] = t == 0 ? __double2ull_rn(p.t_res0 * kResOne) : 0ull;  // a resumed run's first plan sees the saved L1 change
             p.t_stamp[t] = p.epoch;
         }
         __syncthreads();
@@ -462,13 +487,17 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
     __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_ub[kPlanThreads], s_ue[kPlanThreads], s_uq[kPlanThreads], s_uea[kPlanThreads];
     __shared__ unsigned long long s_v[kPlanThreads / 32], s_e[kPlanThreads / 32], s_sv[kPlanThreads / 32],
-        s_se[kPlanThreads / 32];
-    __shared__ double s_r[kPlanThreads / 32], s_b[kPlanThreads / 32];
+        s_se[kPlanThreads / 32], s_bp[kPlanThreads / 32];
+    __shared__ unsigned long long s_r[kPlanThreads / 32];
+    __shared__ unsigned long long s_f1[kPlanThreads / 32], s_f2[kPlanThreads / 32];
+    __shared__ uint32_t s_ct[kPlanThreads + 1];  // the chunk's task offsets (col_task)
     __shared__ uint32_t s_pc[kPlanThreads / 32], s_sc[kPlanThreads / 32], s_nl[kPlanThreads / 32], s_fb[kPlanThreads / 32];
+    __shared__ uint32_t s_cva[kPlanThreads];
+    __shared__ unsigned long long s_cea[kPlanThreads];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t prev = p.epoch - 1;
-    unsigned long long tv = 0, te = 0, tsv = 0, tse = 0;
-    double tr = 0.0, tb = 0.0;
+    unsigned long long tv = 0, te = 0, tsv = 0, tse = 0, tbp = 0, tr = 0;  // tr: L1 change (fixed point)
+    unsigned long long tf1 = 0, tf2 = 0;  // fractions of the SC model bytes (whole bytes: in tbp)
     uint32_t npc = 0, nsc = 0, nnull = 0, nfb = 0, sc_base = 0, pc_base = 0;
 
     uint32_t all_base = 0;
@@ -477,15 +506,81 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         uint32_t q = base + threadIdx.x;
         uint8_t m = kModeNone;
         bool valid = q < p.k;
-        uint64_t Va = 0, Ea = 0, Ep = 0, np = 0;
+        uint64_t Va = 0, Ea = 0;
+        uint32_t Ep = 0, np = 0;  // loaded before the task statistics, widened where used
         float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        uint8_t pcs = 0;
         if (valid) {
-            double res = 0.0;
-            for (uint32_t t = p.col_task[q]; t < p.col_task[q + 1]; ++t)
-                if (p.t_stamp[t] == prev) { Va += p.t_va[t]; Ea += p.t_ea[t]; res += p.t_res[t]; }
             Ep = p.Ep[q];
             np = p.npng_p[q];
-            tv += Va; te += Ea; tr += res;
+            pcs = p.pc_state[q];
+        }
+        // V_a and E_a of the chunk's columns from the last iteration's gather-task statistics: the block
+        // takes the chunk's tasks (contiguous, dozens for a hub column) together, each thread a run of
+        // consecutive tasks with kPlanLoads loads in flight, and adds each column's share of its run into
+        // per-column shared counters (integers: exact in any order)
+        const uint32_t nq = min(blockDim.x, p.k - base);  // columns of the chunk
+        s_cva[threadIdx.x] = 0u;
+        s_cea[threadIdx.x] = 0ull;
+        if (threadIdx.x < nq) s_ct[threadIdx.x] = p.col_task[base + threadIdx.x];
+        if (threadIdx.x == 0) s_ct[nq] = p.col_task[base + nq];
+        __syncthreads();
+        {
+            const uint32_t tlo = s_ct[0], thi = s_ct[nq];
+            const uint32_t per = (thi - tlo + blockDim.x - 1) / blockDim.x;
+            const uint32_t r0 = tlo + threadIdx.x * per, r1 = min(thi, r0 + per);
+            // the column (within the chunk) of task r0: the last c with s_ct[c] <= r0
+            uint32_t c = 0;
+            if (r0 < r1) {
+                uint32_t lo = 0, hi = nq - 1;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (s_ct[mid] <= r0) lo = mid; else hi = mid - 1;
+                }
+                c = lo;
+            }
+            uint32_t cva = 0;
+            unsigned long long cea = 0;
+            for (uint32_t t = r0; t < r1; t += kPlanLoads) {
+                uint32_t st[kPlanLoads], va[kPlanLoads];
+                unsigned long long ea[kPlanLoads], rs[kPlanLoads];
+#pragma unroll
+                for (uint32_t u = 0; u < kPlanLoads; ++u) {
+                    const bool in = t + u < r1;
+                    st[u] = in ? __ldg(&p.t_stamp[t + u]) : ~prev;
+                    va[u] = in ? __ldg(&p.t_va[t + u]) : 0u;
+                    ea[u] = in ? __ldg(&p.t_ea[t + u]) : 0ull;
+                    rs[u] = in ? __ldg(&p.t_res[t + u]) : 0ull;
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < kPlanLoads; ++u) {
+                    if (t + u >= r1) break;
+                    while (s_ct[c + 1] <= t + u) {  // task t + u starts a later column: flush this one
+                        if (cva | cea) {
+                            atomicAdd(&s_cva[c], cva);
+                            atomicAdd(&s_cea[c], cea);
+                        }
+                        cva = 0;
+                        cea = 0;
+                        ++c;
+                    }
+                    if (st[u] == prev) {
+                        cva += va[u];
+                        cea += ea[u];
+                        tr += rs[u];
+                    }
+                }
+            }
+            if (cva | cea) {
+                atomicAdd(&s_cva[c], cva);
+                atomicAdd(&s_cea[c], cea);
+            }
+        }
+        __syncthreads();
+        Va = s_cva[threadIdx.x];
+        Ea = s_cea[threadIdx.x];
+        if (valid) {
+            tv += Va; te += Ea;
             if (Va == 0 || Ep == 0) m = kModeNone;
             else if (p.policy == GPOP_MODE_FORCE_SC) m = kModeSC;
             else if (p.policy == GPOP_MODE_FORCE_PC) m = kModePC;
@@ -507,7 +602,13 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         if (p.isg_w >= 2 && valid && q % p.isg_w != (p.iter - 1) % p.isg_w) m = kModeNone;
         if (valid) {
             p.mode[q] = m;
-            tb += mode_bytes(m, p.k, Ep, np, Va, Ea);
+            if (m == kModePC) tbp += pc_mode_bytes(p.k, Ep, np);
+            else if (m == kModeSC) {
+                unsigned long long d1, d2;
+                tbp += sc_mode_bytes(Ep, np, Va, Ea, &d1, &d2);
+                tf1 += d1;
+                tf2 += d2;
+            }
             if (Va > 0) p.gflag[q] = p.epoch;  // active partitions are gathered (reInit of Alg. 2)
             npc += (m == kModePC);
             nsc += (m == kModeSC);
@@ -515,7 +616,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
                 tsv += Va;
                 tse += Ea;
             }
-            uint8_t act = m == kModePC ? kActPC : (p.pc_state[q] ? kActNull : kActSkip);
+            uint8_t act = m == kModePC ? kActPC : (pcs ? kActNull : kActSkip);
             nnull += (act == kActNull);
             p.action[q] = act;
         }
@@ -532,46 +633,49 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         uint32_t total;
         const uint32_t nsc_u = (valid && m == kModeSC) ? nu : 0u;
         uint32_t off = block_excl_scan(nsc_u, s_warp, &total);
-        write_units(p.sc_list, sc_base, q, nsc_u, off, total, (uint32_t)Ea, s_ub, s_ue, s_uq, s_uea);
+        if (total) write_units(p.sc_list, sc_base, q, nsc_u, off, total, (uint32_t)Ea, s_ub, s_ue, s_uq, s_uea);
         sc_base += total;
         if (p.log_both) {
             const uint32_t nall_u = (valid && m != kModeNone) ? nu : 0u;
             uint32_t off2 = block_excl_scan(nall_u, s_warp, &total);
-            write_units(p.all_list, all_base, q, nall_u, off2, total, (uint32_t)Ea, s_ub, s_ue, s_uq, s_uea);
+            if (total) write_units(p.all_list, all_base, q, nall_u, off2, total, (uint32_t)Ea, s_ub, s_ue, s_uq, s_uea);
             all_base += total;
         }
     }
-    // deterministic block reductions (fixed tree order)
-    for (int o = 16; o > 0; o >>= 1) {
-        tv += __shfl_xor_sync(0xffffffffu, tv, o);
-        te += __shfl_xor_sync(0xffffffffu, te, o);
-        tsv += __shfl_xor_sync(0xffffffffu, tsv, o);
-        tse += __shfl_xor_sync(0xffffffffu, tse, o);
-        tr += __shfl_xor_sync(0xffffffffu, tr, o);
-        tb += __shfl_xor_sync(0xffffffffu, tb, o);
-        npc += __shfl_xor_sync(0xffffffffu, npc, o);
-        nsc += __shfl_xor_sync(0xffffffffu, nsc, o);
-        nnull += __shfl_xor_sync(0xffffffffu, nnull, o);
-        nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
-    }
+    // deterministic block reductions (fixed orders; integers exact)
+    tv = warp_sum_u64(tv);
+    te = warp_sum_u64(te);
+    tsv = warp_sum_u64(tsv);
+    tse = warp_sum_u64(tse);
+    tbp = warp_sum_u64(tbp);
+    tr = warp_sum_u64(tr);
+    tf1 = warp_sum_u64(tf1);
+    tf2 = warp_sum_u64(tf2);
+    npc = __reduce_add_sync(0xffffffffu, npc);
+    nsc = __reduce_add_sync(0xffffffffu, nsc);
+    nnull = __reduce_add_sync(0xffffffffu, nnull);
+    nfb = __reduce_add_sync(0xffffffffu, nfb);
     if (lane == 0) {
-        s_v[wid] = tv; s_e[wid] = te; s_r[wid] = tr; s_b[wid] = tb; s_sv[wid] = tsv; s_se[wid] = tse;
+        s_v[wid] = tv; s_e[wid] = te; s_r[wid] = tr; s_f1[wid] = tf1; s_f2[wid] = tf2; s_sv[wid] = tsv; s_se[wid] = tse; s_bp[wid] = tbp;
         s_pc[wid] = npc; s_sc[wid] = nsc; s_nl[wid] = nnull; s_fb[wid] = nfb;
     }
     __syncthreads();
     __shared__ uint32_t s_done;
     if (threadIdx.x == 0) {
-        unsigned long long a = 0, b = 0, sa = 0, sb = 0;
-        double r = 0.0, by = 0.0;
+        constexpr int kNw = kPlanThreads / 32;  // k_plan runs one block of kPlanThreads
+        unsigned long long a = 0, b = 0, sa = 0, sb = 0, bp = 0, rf = 0, f1 = 0, f2 = 0;
         uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            a += s_v[i]; b += s_e[i]; r += s_r[i]; by += s_b[i]; sa += s_sv[i]; sb += s_se[i];
+#pragma unroll 4
+        for (int i = 0; i < kNw; ++i) {
+            a += s_v[i]; b += s_e[i]; sa += s_sv[i]; sb += s_se[i]; bp += s_bp[i]; rf += s_r[i];
+            f1 += s_f1[i]; f2 += s_f2[i];
             c0 += s_pc[i]; c1 += s_sc[i]; c2 += s_nl[i]; c3 += s_fb[i];
         }
+        const double r = (double)rf * kResUnit;
         uint32_t done = (a == 0) || (p.iter > p.max_iters);
         if ((p.algo == ALG_PR || p.algo == ALG_PPR) && p.iter > 1 && r < p.tol) done = 1;
         Control c;
-        c.frontier_v = a; c.frontier_e = b; c.residual = r; c.model_bytes = by;
+        c.frontier_v = a; c.frontier_e = b; c.residual = r; c.model_bytes = (double)bp + (double)f1 * 0x1p-29 + (double)f2 * 0x1p-61;
         c.n_pc = c0; c.n_sc = c1; c.n_null = c2; c.done = done; c.n_fallback = c3; c.error = p.ctrl->error;
         c.n_sc_units = sc_base;
         p.pc_prefix[p.k] = pc_base;
@@ -579,8 +683,9 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
         c.sc_v = sa;
         c.sc_e = sb;
         *p.ctrl = c;
-        p.ctrl_snap[(p.iter - 1) & 1] = c;  // read by the host once the plan has finished
-        __threadfence_system();
+        // read by the host after it has synchronised with the stream (the kernel's completion makes
+        // the write visible)
+        p.ctrl_snap[(p.iter - 1) & 1] = c;
         for (int i = 0; i < 8; ++i) p.counters[i] = 0;
         p.counters[7] = all_base;  // LOG_BOTH: size of all_list
         s_done = done;
@@ -616,6 +721,20 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
                      smem_addr(dst)),
                  "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// L2 policy that marks the lines it touches as first to evict: for data read exactly once, so that it does
+// not push out lines prefetched for later use
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+    return pol;
+}
+// bulk_g2s with an L2 cache policy
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
                  : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
@@ -1203,6 +1322,7 @@ __device__ void pc_producer(const Params &p, PcSlot *slots, uint64_t *full, uint
     const bool pc_skip = p.pc_skip != 0;
     uint32_t issued = 0;  // blocks staged so far: buffer issued % nbuf, use issued / nbuf
     bool ok = true;
+    const uint64_t pol = l2_evict_first_policy();
     for (uint32_t n = 0; ok; ++n) {  // n: tasks handed over
         const uint32_t ts = n & 1;
         PcSlot &sl = slots[ts];
@@ -1272,7 +1392,8 @@ __device__ void pc_producer(const Params &p, PcSlot *slots, uint64_t *full, uint
             }
             char *dst = reinterpret_cast<char *>(stage + b * kStageWords);
             // the block's bin runs (row-major source slot, length, offset in the block; multiples of 4 values,
-            // so 16-byte aligned), eight descriptor loads in flight per lane
+            // so 16-byte aligned), eight descriptor loads in flight per lane; the values are read once, so
+            // their L2 lines go first (the consumers' entries prefetched into L2 stay)
             for (uint32_t r = r0; r < r1; r += 32 * 8) {
                 uint4 run[8];
 #pragma unroll
@@ -1283,9 +1404,9 @@ __device__ void pc_producer(const Params &p, PcSlot *slots, uint64_t *full, uint
 #pragma unroll
                 for (uint32_t u = 0; u < 8; ++u)
                     if (r + u * 32 + (uint32_t)lane < r1)
-                        bulk_g2s(dst + (size_t)run[u].z * kB,
-                                 reinterpret_cast<const char *>(p.pdata) + (size_t)run[u].x * kB, run[u].y * kB,
-                                 &full[b]);
+                        bulk_g2s_hint(dst + (size_t)run[u].z * kB,
+                                      reinterpret_cast<const char *>(p.pdata) + (size_t)run[u].x * kB, run[u].y * kB,
+                                      &full[b], pol);
             }
         }
     }
@@ -1300,8 +1421,8 @@ __device__ void pc_producer(const Params &p, PcSlot *slots, uint64_t *full, uint
 // Consumer warp w of k_gather_pc: for every task, folds its entries of each active block (those of its
 // destination range [D_w, D_w+1), the same in every block of the task, cut at build time so that no two
 // warps ever touch one destination) into the shared column accumulator, round by round, with the next
-// round's entries already loading into registers and its entries of the blocks two ahead being fetched
-// into L2; then all consumers write the column's result (or the task's partial vector) and reset the
+// round's entries already loading into registers and its entries of the next block being fetched into
+// L2; then all consumers write the column's result (or the task's partial vector) and reset the
 // accumulator.
 template <int ALGO, bool B16>
 __device__ void pc_consumer(const Params &p, const PcSlot *slots, uint64_t *full, uint64_t *empty, uint64_t *tfull,
@@ -1331,8 +1452,9 @@ __device__ void pc_consumer(const Params &p, const PcSlot *slots, uint64_t *full
                 if (c.s < c.e) break;
             }
         };
-        // this warp's entries (and SSSP weights) of active block j, bulk-prefetched into L2 two blocks
-        // ahead of their fold (the entries are 16-byte aligned and padded to whole 16-entry groups)
+        // this warp's entries (and SSSP weights) of active block j, bulk-prefetched into L2 one block ahead
+        // of their fold (the entries are 16-byte aligned and padded to whole 16-entry groups); further
+        // ahead, the stream of other reads evicts part of them before use
         auto prefetch_block = [&](uint32_t j) {
             if (lane == 0 && j < na) {
                 const uint32_t i = sl.blist[j], s = sl.sp[i * kSp + w], e = sl.sp[i * kSp + w + 1];
@@ -1343,14 +1465,13 @@ __device__ void pc_consumer(const Params &p, const PcSlot *slots, uint64_t *full
             }
         };
         prefetch_block(0);
-        prefetch_block(1);
         Cur c{0, 0, 0};
         seek(c);
         uint4 R[4];
         if (c.j < na) pc_load_round(p.pe, c.s, min(c.e - c.s, kPcRound), lane, R);
         for (uint32_t j = 0; j < na; ++j, ++used) {
             const uint32_t b = used % nbuf;
-            prefetch_block(j + 2);
+            prefetch_block(j + 1);
             // every consumer waits for every block, so that none is ever more than nbuf blocks ahead
             if (ok && !__all_sync(0xffffffffu, mbar_wait(&full[b], (used / nbuf) & 1u, abort, &p.ctrl->error, kPcSpinLimit, kPcSleepNs))) ok = false;
             const uint32_t vals = smem_addr(stage + b * kStageWords);
@@ -1810,7 +1931,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
             for (int w = 0; w < kGatherWarps; ++w) { a += s_va[w]; b2 += s_ea[w]; r += s_res[w]; }
             p.t_va[t] = a;
             p.t_ea[t] = b2;
-            p.t_res[t] = r;
+            p.t_res[t] = __double2ull_rn(r * kResOne);
             p.t_stamp[t] = p.epoch;
             if (p.t_task) p.t_task[t] = globaltimer() - t0;
             s_last = 0;
@@ -1834,7 +1955,7 @@ struct RunBuffers {
     uint32_t *val = nullptr, *lvl = nullptr, *sval = nullptr, *bits = nullptr;
     uint32_t *t_va = nullptr, *t_stamp = nullptr;
     unsigned long long *t_ea = nullptr;
-    double *t_res = nullptr;
+    unsigned long long *t_res = nullptr;
     uint8_t *mode = nullptr, *action = nullptr, *sel_mode = nullptr;
     uint32_t *col_done = nullptr;
     uint32_t *gflag = nullptr, *gflag_pc = nullptr, *counters = nullptr;
