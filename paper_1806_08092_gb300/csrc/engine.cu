@@ -1596,9 +1596,18 @@ __global__ void __launch_bounds__(256) k_merge_pc(Params p) {
         const uint32_t *src = p.pc_part + (uint64_t)part0 * p.P + i;
         if (i + 4 <= wq) {
             uint4 r = make_uint4(O::identity(), O::identity(), O::identity(), O::identity());
-            for (uint32_t j = 0; j < nt; ++j) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(src + (uint64_t)j * p.P);
-                r = make_uint4(O::combine(r.x, v.x), O::combine(r.y, v.y), O::combine(r.z, v.z), O::combine(r.w, v.w));
+            // eight partial vectors' loads in flight, combined in task order
+            for (uint32_t j0 = 0; j0 < nt; j0 += 8) {
+                uint4 v[8];
+#pragma unroll
+                for (uint32_t u = 0; u < 8; ++u)
+                    v[u] = j0 + u < nt ? __ldcs(reinterpret_cast<const uint4 *>(src + (uint64_t)(j0 + u) * p.P))
+                                       : make_uint4(0, 0, 0, 0);
+#pragma unroll
+                for (uint32_t u = 0; u < 8; ++u)
+                    if (j0 + u < nt)
+                        r = make_uint4(O::combine(r.x, v[u].x), O::combine(r.y, v[u].y), O::combine(r.z, v[u].z),
+                                       O::combine(r.w, v[u].w));
             }
             *reinterpret_cast<uint4 *>(p.pc_sum + gq + i) = r;
         } else {
