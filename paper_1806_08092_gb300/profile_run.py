@@ -32,6 +32,7 @@ def main() -> None:
     g = gg.rmat(a.scale).with_weights(hi=255)
     root = int(gg.roots(g, 16)[a.root_index])
     G = gp.Graph.from_csr(g.row_ptr, g.col, g.weights, partition_size=a.partition)
+    print(json.dumps({"layout": G.info()}), flush=True)
     keys = ("iterations", "device_ms", "edges_scattered", "vertices_scattered", "sc_vertices_scattered",
             "sc_edges_scattered", "gathered_vertices", "model_bytes", "pc_partition_steps", "sc_partition_steps")
     for algo in a.algos.split(","):

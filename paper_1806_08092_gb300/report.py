@@ -1,6 +1,6 @@
 """Measurements of the synthetic configurations on one GPU, one JSON line per result.
 
-    python -m paper_1806_08092_gb300.report [--configs c1,c2,c3,c4,nibble,ablation,degree]
+    python -m paper_1806_08092_gb300.report [--configs c1,c2,c3,c4,c4_graphs,nibble,ablation,isg,degree]
 
 c1        PageRank, 10 iterations, d = 0.85, RMAT-16 (P = 1024): time and GTEPS = 10 E / t.  The graph
           and its bins fit in L2, so no HBM fraction is meaningful for it.
@@ -12,9 +12,12 @@ c3        PageRank to an L1 residual below 1e-9 on RMAT-24 and on a uniform rand
           same size and average degree, with FP32 and with BF16 bin messages: GTEPS = E x iterations / t
           and per-kernel times (the errors against the FP64 oracle come from the GPU tests).
 c4        RMAT-22 BFS from 64 sources: gpop_run_msbfs (two 32-source passes) against 64 single-source
-          gpop_run calls, TEPS = sum over sources of traversed edges / t, and the batching speedup; and
-          PPR from 256 seeds (alpha = 0.15, L1 change < 1e-9 or 100 iterations), one gpop_run per seed
-          (a 32-bit message holds one FP32 value, so seeds are not packed into one pass).
+          gpop_run calls, TEPS = sum over sources of traversed edges / t, and the batching speedup; PPR
+          from 256 seeds (alpha = 0.15, L1 change < 1e-9 or 100 iterations), one gpop_run per seed; and
+          the same 256 seeds through gpop_run_ppr_batch (32 seeds per message, P = 1024) with the
+          per-row error of three seeds against the FP64 oracle.
+c4_graphs 128 independent RMAT graphs (scales 10-18, edge factors 8-32): BFS on their disjoint union
+          (gpop_graph_build_union + gpop_run_bfs_union) against one gpop_run per graph.
 nibble    parallel Nibble (Alg. 4) on RMAT-24 from 16 seeds with Sec. 5's threshold eps = 1e-9, at most
           100 iterations: time, iterations, vertices with PR > 0 and edges scattered per seed.
 degree    time against average degree (Sec. 5, execution time vs degree): RMAT-26 (64 M vertices) from
@@ -23,6 +26,8 @@ degree    time against average degree (Sec. 5, execution time vs degree): RMAT-2
           on the symmetrised graph up to edge factor 16; with the PC / SC partition-steps of each run.
 ablation  RMAT-24 BFS and SSSP and symmetrised RMAT-24 CC with every partition forced to SC, forced to
           PC, and with Eq. (mode): time, iterations and the number of PC / SC partition-steps.
+isg       interleaved scatter-gather (Sec. 3.3) with 0 (bulk-synchronous), 2, 4 and 8 waves: SSSP on
+          RMAT-24 from 4 roots and CC on symmetrised RMAT-24, Eq. (mode) at BW_PC/BW_SC = 8/1.
 
 Times are CUDA-event device times of gpop_run (inputs resident on the GPU), median of three runs after
 a warm-up run unless stated.
