@@ -348,6 +348,13 @@ __device__ void select_partition(const Params &p, uint32_t q, uint32_t stamp, in
     if (lane == 0) p.sel_mode[q] = m;
 }
 
+// Programmatic dependent launch: the kernels of an iteration are launched so that each one's CTAs are
+// placed on the SMs as the CTAs of the one before it exit, instead of after the whole grid has retired.
+// Every one of them first waits until its predecessor in the stream has completed and its writes are
+// visible (griddepcontrol.wait; an immediate return for an ordinary launch).  None triggers its successor
+// early: successors placed while the predecessor still runs made an iteration slower.
+#define GPOP_GRID_DEP() asm volatile("griddepcontrol.wait;\n" ::: "memory")
+
 // Learned SC/PC choice for every partition (spec selector, Sec. 3.2's decision made by the MLP),
 // for the first iteration of a run: one warp per partition computes V_a and E_a from the initial
 // gather-task statistics (as k_plan does), the features and the forward pass, with the network staged
@@ -355,6 +362,7 @@ __device__ void select_partition(const Params &p, uint32_t q, uint32_t stamp, in
 // iterations get their choices from the tail of k_gather (the last task of each column to finish).
 constexpr int kSelectWarps = 8;
 __global__ void __launch_bounds__(32 * kSelectWarps) k_select(Params p) {
+    GPOP_GRID_DEP();
     __shared__ float s_w[GPOP_SELECTOR_PARAMS];
     for (int i = threadIdx.x; i < GPOP_SELECTOR_PARAMS; i += blockDim.x) s_w[i] = p.selector[i];
     __syncthreads();
@@ -484,6 +492,7 @@ __global__ void k_task_stats(Params p) {
 // --- plan: modes, actions, SC list, termination ------------------------------------------------
 
 __global__ void __launch_bounds__(kPlanThreads) k_plan(Params p) {
+    GPOP_GRID_DEP();
     __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_ub[kPlanThreads], s_ue[kPlanThreads], s_uq[kPlanThreads], s_uea[kPlanThreads];
     __shared__ unsigned long long s_v[kPlanThreads / 32], s_e[kPlanThreads / 32], s_sv[kPlanThreads / 32],
@@ -806,6 +815,7 @@ __device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
 // writes the 8 values of each group as two 16-byte stores.
 template <bool B16>
 __global__ void __launch_bounds__(kScatterPcThreads) k_scatter_pc(Params p) {
+    GPOP_GRID_DEP();
     extern __shared__ __align__(16) uint32_t s_val[];  // the partition's P message values (PC rows)
     __shared__ __align__(8) uint64_t s_bar;            // completion of the value copy
     __shared__ uint32_t s_task, s_ok;
@@ -915,6 +925,7 @@ __global__ void __launch_bounds__(kScatterPcThreads) k_scatter_pc(Params p) {
 // every scattered partition when a LOG_BOTH shadow pass times both modes), one warp per segment from the
 // frontier bits and the row offsets; the SC scatter's units find their edge ranges in these counts.
 __global__ void k_sc_segments(Params p) {
+    GPOP_GRID_DEP();
     const uint32_t nseg = (p.P + 1023) / 1024;
     const int lane = threadIdx.x & 31;
     const uint64_t nw = (uint64_t)p.k * nseg, step = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -952,6 +963,7 @@ __global__ void k_sc_segments(Params p) {
 // bump global cursors (zero at rest), and the last unit to finish publishes the counts and resets them.
 template <int ALGO, bool B16>
 __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
+    GPOP_GRID_DEP();
     extern __shared__ uint32_t s_cursor[];  // per sub-bin of the row: its next free slot (a partition of one unit)
                                             // or its first slot (a split partition, cursors in global memory)
     // the current segment's active vertices, ascending: exclusive prefix of their out-degrees, first
@@ -1570,6 +1582,9 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
         else stage[threadIdx.x * kStageWords + kPcPadIdx] = O::identity();
     }
     for (uint32_t i = threadIdx.x; i < p.P; i += kPcThreads) acc[i] = O::identity();
+    // the set-up above touches shared memory only, so it overlaps the end of the scatter; from here on
+    // the scatter's messages and the plan's counters are read
+    GPOP_GRID_DEP();
     const unsigned long long t_start = p.t_gpc ? globaltimer() : 0ull;
     __syncthreads();
     if (wid == kPcGatherWarps)
@@ -1585,6 +1600,7 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
 // reproducible) into pc_sum; one chunk per CTA, 16-byte accesses.
 template <int ALGO>
 __global__ void __launch_bounds__(256) k_merge_pc(Params p) {
+    GPOP_GRID_DEP();
     using O = Op<ALGO>;
     for (uint32_t it = blockIdx.x; it < p.nmerge; it += gridDim.x) {
         const uint2 m = p.pc_merge[it];  // column, first destination
@@ -1666,6 +1682,7 @@ __device__ __forceinline__ uint2 sc_pair(const Params &p, uint32_t j) {
 
 template <int ALGO, bool B16>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(Params p) {
+    GPOP_GRID_DEP();
     using O = Op<ALGO>;
     using A = ScAcc<ALGO>;
     __shared__ typename A::T s_acc[kGatherWidth];
@@ -2313,6 +2330,23 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         }
         nchain = 0;
     };
+    // launches an iteration kernel with programmatic stream serialisation (see GPOP_GRID_DEP); the first
+    // failed launch is kept in launch_err
+    cudaError_t launch_err = cudaSuccess;
+    auto launch_dep = [&](auto kernel, uint32_t grid, uint32_t block, size_t smem, const Params &kp) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(block);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, kp);
+        if (e != cudaSuccess && launch_err == cudaSuccess) launch_err = e;
+    };
     auto timed = [&](int kind, auto launch) {
         if (prof && nchain == 0) cudaEventRecord(kev[0], s);
         launch();
@@ -2329,9 +2363,9 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         const bool first_select = learned && it == 0;
         timed(0, [&] {
             if (first_select)
-                k_select<<<std::min<uint32_t>((g->k + kSelectWarps - 1) / kSelectWarps, 8u * g->num_sms),
-                           32 * kSelectWarps, 0, s>>>(pp);
-            k_plan<<<1, kPlanThreads, 0, s>>>(pp);
+                launch_dep(k_select, std::min<uint32_t>((g->k + kSelectWarps - 1) / kSelectWarps, 8u * g->num_sms),
+                           32 * kSelectWarps, 0, pp);
+            launch_dep(k_plan, 1, kPlanThreads, 0, pp);
         });
         if (prof && first_select) st.kernel_launches[0] += 1;  // k_select
     };
@@ -2339,7 +2373,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
     const int grid_seg = std::max(1, std::min((int)(((uint64_t)g->k * ((g->P + 1023) / 1024) + 7) / 8), 16 * g->num_sms));
     auto launch_work = [&](const Params &pp, const Control &c) -> cudaError_t {
         // per-segment active edges of the partitions the SC scatter (or the LOG_BOTH shadow) will visit
-        if (p.log_both || c.n_sc > 0) timed(2, [&] { k_sc_segments<<<grid_seg, 256, 0, s>>>(pp); });
+        if (p.log_both || c.n_sc > 0) timed(2, [&] { launch_dep(k_sc_segments, grid_seg, 256, 0, pp); });
         if (p.log_both) {
             // time both modes for every partition picked this iteration (shadow launches first:
             // the real SC scatter below rewrites the same bins with the same pairs)
@@ -2365,15 +2399,16 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         pgc.t_gpc = p.log_both ? rb->t_gpc : nullptr;
         pgc.pc_skip = c.n_pc < g->k;  // some partition is not PC: skip blocks whose sources all are not
         if (c.n_pc + c.n_null > 0)
-            timed(1, [&] { k_scatter_pc<B16><<<grid_pc, kScatterPcThreads, spc_smem, s>>>(pp); });
-        if (c.n_sc > 0) timed(2, [&] { k_scatter_sc<ALGO, B16><<<grid_sc, kScatterThreads, sc_smem, s>>>(ps); });
+            timed(1, [&] { launch_dep(k_scatter_pc<B16>, grid_pc, kScatterPcThreads, spc_smem, pp); });
+        if (c.n_sc > 0) timed(2, [&] { launch_dep(k_scatter_sc<ALGO, B16>, grid_sc, kScatterThreads, sc_smem, ps); });
         if (c.n_pc > 0) {
-            timed(4, [&] { k_gather_pc<ALGO, B16><<<grid_gh, kPcThreads, gpc_smem, s>>>(pgc); });
+            timed(4, [&] { launch_dep(k_gather_pc<ALGO, B16>, grid_gh, kPcThreads, gpc_smem, pgc); });
             if (g->nmerge)
-                timed(5, [&] { k_merge_pc<ALGO><<<std::min<uint32_t>(g->nmerge, 16u * g->num_sms), 256, 0, s>>>(pp); });
+                timed(5, [&] { launch_dep(k_merge_pc<ALGO>, std::min<uint32_t>(g->nmerge, 16u * g->num_sms), 256, 0, pp); });
         }
-        timed(3, [&] { k_gather<ALGO, B16><<<grid_ga, kGatherThreads, 0, s>>>(pg); });
-        return cudaGetLastError();
+        timed(3, [&] { launch_dep(k_gather<ALGO, B16>, grid_ga, kGatherThreads, 0, pg); });
+        const cudaError_t e = cudaGetLastError();
+        return launch_err != cudaSuccess ? launch_err : e;
     };
     // the plan's verdict on iteration iter: false when the loop stops (termination or error)
     auto take = [&](const Control &c) -> bool {
@@ -2402,7 +2437,7 @@ static gpop_status run_algo(Graph *g, RunBuffers *rb, const gpop_run_opts *o, cu
         p.iter = base + iter + 1;
         p.epoch = ++g->epoch;
         launch_plan(iter, p);
-        cudaError_t ce = cudaStreamSynchronize(s);
+        cudaError_t ce = launch_err != cudaSuccess ? launch_err : cudaStreamSynchronize(s);
         if (ce != cudaSuccess) { status = fail(GPOP_ERR_CUDA, std::string("plan: ") + cudaGetErrorString(ce)); break; }
         if (prof) resolve();
         const Control c = rb->h_ctrl[(base + iter) & 1];  // this plan's slot: (p.iter - 1) & 1
