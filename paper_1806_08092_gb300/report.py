@@ -14,8 +14,9 @@ c3        PageRank to an L1 residual below 1e-9 on RMAT-24 and on a uniform rand
 c4        RMAT-22 BFS from 64 sources: gpop_run_msbfs (two 32-source passes) against 64 single-source
           gpop_run calls, TEPS = sum over sources of traversed edges / t, and the batching speedup; PPR
           from 256 seeds (alpha = 0.15, L1 change < 1e-9 or 100 iterations), one gpop_run per seed; and
-          the same 256 seeds through gpop_run_ppr_batch (32 seeds per message, P = 1024) with the
-          per-row error of three seeds against the FP64 oracle.
+          the same 256 seeds through gpop_run_ppr_batch (32 seeds per message, P = 1024), with the
+          largest relative difference of three of its rows from the single-seed runs of the same seeds
+          (the error against the FP64 oracle is checked by the GPU tests).
 c4_graphs 128 independent RMAT graphs (scales 10-18, edge factors 8-32): BFS on their disjoint union
           (gpop_graph_build_union + gpop_run_bfs_union) against one gpop_run per graph.
 nibble    parallel Nibble (Alg. 4) on RMAT-24 from 16 seeds with Sec. 5's threshold eps = 1e-9, at most
@@ -168,37 +169,38 @@ def c4(nsrc=64):
     seeds = [int(x) for x in gg.roots(g, 256)]
     G.run("ppr", source=seeds[0], max_iters=100, tol=1e-9)  # warm-up
     ms = its = edges = conv = 0
-    for s in seeds:
+    rows = (0, 100, 255)
+    single_rows = {}
+    for j, s in enumerate(seeds):
         r = G.run("ppr", source=s, max_iters=100, tol=1e-9)
         ms += r.stats["device_ms"]
         its += r.stats["iterations"]
         edges += r.stats["edges_scattered"]
         conv += int(r.stats["converged"])
+        if j in rows:
+            single_rows[j] = r.values.cpu().numpy().astype(np.float64)
     _emit({"config": "c4", "graph": "rmat22", "algo": "ppr", "seeds": len(seeds), "alpha": 0.15, "tol_l1": 1e-9,
            "ms_total": ms, "ms_per_seed": ms / len(seeds), "iterations_mean": its / len(seeds), "converged": conv,
            "gteps_scattered": edges / (ms / 1e3) / 1e9})
     G.close()
     # the same 256 seeds batched (gpop_run_ppr_batch: 32 seeds per message, partition size 1024), against
-    # the single-seed runs above; per-seed error of four rows against the FP64 oracle
-    import oracle as O
+    # the single-seed runs above: time, and the largest relative difference of three rows where the
+    # single-seed value is at least 1e-9 (both runs stop at an L1 change below 1e-9)
     Gb = Graph.from_csr(g.row_ptr, g.col, None, partition_size=1024)
     Gb.run_ppr_batch(seeds[:32], max_iters=5)  # warm-up
     rb = Gb.run_ppr_batch(seeds, max_iters=300, tol=1e-9)
     vals = rb.values.cpu().numpy()
     it_pass = rb.stats["iterations"] // ((len(seeds) + 31) // 32)
-    errs = []
-    for j in (0, 100, 255):
-        b0 = j // 32 * 32
-        rb1 = Gb.run_ppr_batch(seeds[b0:b0 + 32], max_iters=300, tol=1e-9)
-        ref, _, _ = O.ppr(g, seeds[j], 0.15, max_iters=rb1.stats["iterations"])
-        x = rb1.values[j - b0].cpu().numpy().astype(np.float64)
-        sup = ref > 0
-        errs.append(float(np.max(np.abs(x[sup] - ref[sup]) / ref[sup])))
+    diffs = []
+    for j in rows:
+        ref, x = single_rows[j], vals[j].astype(np.float64)
+        big = ref >= 1e-9
+        diffs.append(float(np.max(np.abs(x[big] - ref[big]) / ref[big])))
     _emit({"config": "c4", "graph": "rmat22", "algo": "ppr_batch", "seeds": len(seeds), "seeds_per_pass": 32,
            "partition_size": 1024, "alpha": 0.15, "tol_l1": 1e-9, "ms_total": rb.stats["device_ms"],
            "single_seed_ms_total": ms, "speedup_vs_single_seed_runs": ms / rb.stats["device_ms"],
            "iterations_per_pass": it_pass, "converged": rb.stats["converged"],
-           "linf_rel_err_vs_fp64_oracle_rows_0_100_255": errs, "mass_per_row_max": float(vals.sum(axis=1).max())})
+           "max_rel_diff_vs_single_seed_rows_0_100_255": diffs, "mass_per_row_max": float(vals.sum(axis=1).max())})
     Gb.close()
 
 
