@@ -1124,8 +1124,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter_sc(Params p) {
 
 
 // 32-bit shared-memory accesses at explicit shared addresses (the fold's addresses stay 32-bit; volatile
-// keeps them in program order, which the read-modify-writes of consecutive rounds rely on).  The _if forms
-// do nothing at the address 0xFFFFFFFF (no shared address).
+// keeps them in program order, which the read-modify-writes of consecutive rounds rely on).
 __device__ __forceinline__ uint32_t lds32(uint32_t a) {
     uint32_t v;
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
@@ -1137,22 +1136,14 @@ __device__ __forceinline__ uint32_t lds16(uint32_t a) {
     return v;
 }
 __device__ __forceinline__ void sts32(uint32_t a, uint32_t v) { asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v)); }
-__device__ __forceinline__ uint32_t lds32_if(uint32_t a) {
-    uint32_t v;
-    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %1, -1;\n mov.u32 %0, 0;\n @q ld.shared.u32 %0, [%1];\n}\n"
-                 : "=r"(v)
-                 : "r"(a));
-    return v;
-}
-__device__ __forceinline__ void sts32_if(uint32_t a, uint32_t v) {
-    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, -1;\n @q st.shared.u32 [%0], %1;\n}\n" ::"r"(a), "r"(v));
-}
 
 // Serial fold of one lane's K destination entries (its K consecutive positions of the round, held in
 // registers as K / 4 quads), in batches of 8: the batch's message values are loaded first (independent
 // shared loads), runs of equal destination are then found in registers, and the complete inner runs are
-// folded into the accumulator with batched, predicated read-modify-writes (inner runs of a lane have
-// distinct destinations, and no other lane or warp touches them).  Entries are sorted by destination, so a
+// folded into the accumulator with batched read-modify-writes (inner runs of a lane have distinct
+// destinations, and no other lane or warp touches them).  A position that ends no inner run does its
+// read-modify-write on a scratch word past the value buffer's padding slot (never copied into, never
+// read for a result): fewer instructions than predicating the shared accesses.  Entries are sorted by destination, so a
 // position belongs to the lane's first run exactly when its destination is the first one, fd; head follows
 // that run's value.  Padding entries repeat their range's last destination and read the padding value slot
 // (the identity), so they fold as no-ops.  NULL messages are skipped when NUL (SSSP, PPR, Nibble, and
@@ -1185,8 +1176,8 @@ __device__ __forceinline__ void pc_lane(const uint4 (&E)[4], const int4 (&W)[4],
                 x[i] = lds32(stage + (ee[i] & 0xFFFFu) * 4u);
             }
         }
-        // ra: accumulator word of an inner run that ends at this position, or kNoRun
-        constexpr uint32_t kNoRun = 0xFFFFFFFFu;
+        // ra: accumulator word of an inner run that ends at this position, else the scratch word
+        const uint32_t kNoRun = stage + (kPcBlock + 1) * 4u;
         uint32_t ra[HB], fv[HB];
 #pragma unroll
         for (uint32_t i = 0; i < HB; ++i) {
@@ -1211,9 +1202,9 @@ __device__ __forceinline__ void pc_lane(const uint4 (&E)[4], const int4 (&W)[4],
         // read-modify-writes of the inner runs that end in this batch
         uint32_t old[HB];
 #pragma unroll
-        for (uint32_t i = 0; i < HB; ++i) old[i] = lds32_if(ra[i]);
+        for (uint32_t i = 0; i < HB; ++i) old[i] = lds32(ra[i]);
 #pragma unroll
-        for (uint32_t i = 0; i < HB; ++i) sts32_if(ra[i], O::combine(old[i], fv[i]));
+        for (uint32_t i = 0; i < HB; ++i) sts32(ra[i], O::combine(old[i], fv[i]));
     }
 }
 
@@ -1557,7 +1548,7 @@ __global__ void __launch_bounds__(kPcThreads, 1) k_gather_pc(Params p) {
     constexpr uint32_t kStageWords = kPcBlock + 4;
     extern __shared__ __align__(16) uint32_t s_pc_dyn[];
     const uint32_t nbuf = p.pc_nbuf;
-    uint32_t *stage = s_pc_dyn;                     // nbuf x (kPcBlock message values + the padding slot)
+    uint32_t *stage = s_pc_dyn;                     // nbuf x (kPcBlock message values, the padding slot, a scratch word)
     uint32_t *acc = s_pc_dyn + nbuf * kStageWords;  // P values of the column
     __shared__ __align__(8) uint64_t s_full[kPcMaxBufs], s_empty[kPcMaxBufs], s_tfull[2], s_tempty[2];
     __shared__ PcSlot s_slot[2];
